@@ -1,0 +1,173 @@
+"""Seeded synthetic CMP gathers and Radon-domain images.
+
+This module only draws inputs. It holds none of the transform's arithmetic,
+so both the oracle and the CUDA path may use it.
+
+Layouts follow the library: a gather is ``f[Nx][Nt]`` (time fastest), a
+Radon image is ``g[Nq][Ntau]`` (intercept time fastest). Everything is
+float64; callers cast.
+
+Events are hyperbolic reflections ``t = sqrt(tau0^2 + q0^2 x^2)`` carrying a
+Ricker wavelet ``r(t) = (1 - 2 pi^2 nu^2 t^2) exp(-pi^2 nu^2 t^2)`` (the
+CMP-gather model of the paper's Section 1 and Section 5 tests).
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+__all__ = [
+    "Geometry", "ricker", "rng_for", "hyperbolic_gather", "gaussian_gather",
+    "random_radon_image", "single_gather", "sweep_gather", "large_gather",
+    "band_limited_gather", "batch_geometries",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Geometry:
+    """Sampling of one gather and of its Radon image (physical units)."""
+    Nt: int
+    Nx: int
+    Ntau: int
+    Nq: int
+    dt: float
+    dx: float
+    qmin: float
+    qmax: float
+
+    @property
+    def T(self) -> float:
+        return (self.Nt - 1) * self.dt
+
+    @property
+    def X(self) -> float:
+        return (self.Nx - 1) * self.dx
+
+    @property
+    def dtau(self) -> float:
+        return self.T / (self.Ntau - 1)
+
+    def t(self) -> np.ndarray:
+        return np.arange(self.Nt) * self.dt
+
+    def x(self) -> np.ndarray:
+        return np.arange(self.Nx) * self.dx
+
+    def tau(self) -> np.ndarray:
+        return np.arange(self.Ntau) * self.dtau
+
+    def q(self) -> np.ndarray:
+        if self.Nq == 1:
+            return np.array([self.qmin])
+        return self.qmin + np.arange(self.Nq) * (self.qmax - self.qmin) / (self.Nq - 1)
+
+
+def rng_for(tag: int) -> np.random.Generator:
+    """PCG64 stream seeded by ``1604 + tag`` (one tag per workload)."""
+    return np.random.Generator(np.random.PCG64(1604 + int(tag)))
+
+
+def ricker(t: np.ndarray, nu: float) -> np.ndarray:
+    a = (np.pi * nu * t) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def hyperbolic_gather(geo: Geometry, tau0, q0, nu, amp) -> np.ndarray:
+    """Sum of Ricker events on hyperbolas ``t = sqrt(tau0^2 + q0^2 x^2)``."""
+    t = geo.t()[None, :]
+    x = geo.x()[:, None]
+    f = np.zeros((geo.Nx, geo.Nt))
+    for tz, qz, fz, az in zip(np.atleast_1d(tau0), np.atleast_1d(q0),
+                              np.atleast_1d(nu), np.atleast_1d(amp)):
+        arr = np.sqrt(tz * tz + (qz * x) ** 2)
+        f += az * ricker(t - arr, fz)
+    return f
+
+
+def gaussian_gather(geo: Geometry, a: float, b: float) -> np.ndarray:
+    """``exp(-a t^2 - b x^2)`` sampled on the gather grid."""
+    t = geo.t()[None, :]
+    x = geo.x()[:, None]
+    return np.exp(-a * t * t - b * x * x)
+
+
+def random_radon_image(geo: Geometry, tag: int) -> np.ndarray:
+    """Smooth random Radon-domain image (for adjoint and dot tests)."""
+    rng = rng_for(tag)
+    g = rng.standard_normal((geo.Nq, geo.Ntau))
+    # light smoothing along tau keeps it band-limited (3-tap binomial, twice)
+    for _ in range(2):
+        g[:, 1:-1] = 0.25 * g[:, :-2] + 0.5 * g[:, 1:-1] + 0.25 * g[:, 2:]
+    return g
+
+
+def single_gather(tag: int = 1, nu: float = 25.0) -> tuple[Geometry, np.ndarray]:
+    """Small gather: Nt=256 (dt=4 ms), Nx=64 offsets on [0,1.6] km,
+    Ntau=256, Nq=64 on q in [0.2,0.7] s/km, 8 Ricker events,
+    tau0~U[0.1,0.9] s, q0~U[0.25,0.65] s/km, amplitude N(0,1)."""
+    geo = Geometry(256, 64, 256, 64, 0.004, 1.6 / 63, 0.2, 0.7)
+    rng = rng_for(tag)
+    n = 8
+    tau0 = rng.uniform(0.1, 0.9, n)
+    q0 = rng.uniform(0.25, 0.65, n)
+    amp = rng.standard_normal(n)
+    return geo, hyperbolic_gather(geo, tau0, q0, np.full(n, nu), amp)
+
+
+def sweep_gather(N: int, tag: int = 2, n_events: int = 32,
+                 noise: float = 0.05, T: float = 2.0, X: float = 2.0,
+                 nu_range=(20.0, 40.0)) -> tuple[Geometry, np.ndarray]:
+    """Square gather N=Nt=Nx=Ntau=Nq on t in [0,T] s, x in [0,X] km,
+    q in [0.2,0.7] s/km; ``n_events`` Ricker events with
+    tau0~U[0.1,0.9T], q0~U[0.25,0.65], nu~U[nu_range], A~N(0,1),
+    plus Gaussian noise of ``noise`` times the clean RMS."""
+    geo = Geometry(N, N, N, N, T / (N - 1), X / (N - 1), 0.2, 0.7)
+    rng = rng_for(tag * 100003 + N)
+    tau0 = rng.uniform(0.1, 0.9 * T, n_events)
+    q0 = rng.uniform(0.25, 0.65, n_events)
+    nu = rng.uniform(nu_range[0], nu_range[1], n_events)
+    amp = rng.standard_normal(n_events)
+    f = hyperbolic_gather(geo, tau0, q0, nu, amp)
+    if noise > 0:
+        rms = float(np.sqrt(np.mean(f * f)))
+        f = f + noise * rms * rng.standard_normal(f.shape)
+    return geo, f
+
+
+def band_limited_gather(geo: Geometry, tag: int, n_events: int = 8,
+                        nu: float = 12.0) -> np.ndarray:
+    """Events with a low-frequency Ricker on any geometry (no noise)."""
+    rng = rng_for(tag)
+    T = geo.T
+    tau0 = rng.uniform(0.1 * T, 0.85 * T, n_events)
+    q0 = rng.uniform(0.25, 0.65, n_events)
+    amp = rng.standard_normal(n_events)
+    return hyperbolic_gather(geo, tau0, q0, np.full(n_events, nu), amp)
+
+
+def large_gather(N: int = 4096, tag: int = 5, n_events: int = 64,
+                 T: float = 2.0, X: float = 2.0) -> tuple[Geometry, np.ndarray]:
+    """Large square gather with primaries and their first multiples
+    (events at 2*tau0 with the same q0)."""
+    geo = Geometry(N, N, N, N, T / (N - 1), X / (N - 1), 0.2, 0.7)
+    rng = rng_for(tag * 100003 + N)
+    npri = n_events // 2
+    tau0 = rng.uniform(0.1, 0.45 * T, npri)
+    q0 = rng.uniform(0.25, 0.65, npri)
+    nu = rng.uniform(20.0, 40.0, npri)
+    amp = rng.standard_normal(npri)
+    f = hyperbolic_gather(geo, tau0, q0, nu, amp)
+    f += hyperbolic_gather(geo, 2 * tau0, q0, nu, -0.5 * amp)
+    return geo, f
+
+
+def batch_geometries(n: int, tag: int = 4) -> list[Geometry]:
+    """Uneven batch: Nt~U{500..3000} (dt=4 ms), Nx~U{60..480} (dx=25 m),
+    Nq=Nx, Ntau=Nt, q in [0.2,0.7] s/km."""
+    rng = rng_for(tag)
+    out = []
+    for _ in range(n):
+        Nt = int(rng.integers(500, 3001))
+        Nx = int(rng.integers(60, 481))
+        out.append(Geometry(Nt, Nx, Nt, Nx, 0.004, 0.025, 0.2, 0.7))
+    return out
