@@ -1,0 +1,360 @@
+"""Benchmark: forward + adjoint hyperbolic Radon transforms per second.
+
+Workload: the 2048x2048 gather of the size sweep (Nt = Nx = Ntau = Nq = 2048,
+T = 2 s, X = 2 km, q in [0.2, 0.7] s/km, 32 Ricker events 20-40 Hz plus 5 %
+noise), default method parameters. One step = radon_fwd then radon_adj on
+device-resident data (the pair one iteration of Eq. (18) needs). L2 is
+flushed (a 256 MiB write) before every timed step; only the step itself is
+timed, with CUDA events on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank runs its own gather
+(independent replicas, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N = 2048
+WORKLOAD = ("sweep gather 2048x2048 (Nt=Nx=Ntau=Nq=2048, T=2 s, X=2 km, q in [0.2,0.7] s/km, "
+            "32 Ricker events 20-40 Hz + 5% noise), forward + adjoint")
+METRIC = "fwd+adj hyperbolic Radon transforms/s at N=2048 (rel L2<=1e-2) vs GPU direct sum"
+UNIT = "transform pairs/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(tag_rank: int = 0):
+    import synth
+    geo, f = synth.sweep_gather(N, tag=2, noise=0.05)
+    return geo, f
+
+
+def cpu_baseline(geo, f, target_s: float = 12.0):
+    """The FP64 direct-summation oracle on the host cores, on a bounded sample
+    of outputs (forward) and gather points (adjoint), scaled to pairs/s."""
+    from oracle import direct
+    direct.build()
+    rng = np.random.default_rng(1)
+    g_img = np.zeros((geo.Nq, geo.Ntau))
+    n = 4096
+    while True:
+        ii = rng.integers(0, geo.Ntau, n)
+        li = rng.integers(0, geo.Nq, n)
+        jj = rng.integers(0, geo.Nt, n)
+        kk = rng.integers(0, geo.Nx, n)
+        t0 = time.perf_counter()
+        direct.fwd_points(f, geo.dt, geo.dx, geo.tau(), geo.q(), ii, li)
+        t1 = time.perf_counter()
+        direct.adj_points(g_img + 1.0, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q(), jj, kk)
+        t2 = time.perf_counter()
+        if t2 - t0 > target_s / 4 or n >= 1 << 22:
+            break
+        n *= 4
+    t_fwd_full = (t1 - t0) * (geo.Ntau * geo.Nq) / n
+    t_adj_full = (t2 - t1) * (geo.Nt * geo.Nx) / n
+    return {"value": 1.0 / (t_fwd_full + t_adj_full), "unit": UNIT, "cores": direct.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 direct sum (oracle/direct.c, OpenMP) on {n} random outputs (forward) and "
+                      f"{n} random gather points (adjoint) of the 2048x2048 workload, extrapolated to "
+                      f"full transforms ({t2 - t0:.1f} s measured)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle on the host cores, each step a bounded sample."""
+    if rank != 0:
+        return
+    geo, f = make_workload()
+    from oracle import direct
+    direct.build()
+    rng = np.random.default_rng(7)
+    n = 1 << 14
+    g_img = np.ones((geo.Nq, geo.Ntau))
+
+    def step():
+        ii = rng.integers(0, geo.Ntau, n)
+        li = rng.integers(0, geo.Nq, n)
+        jj = rng.integers(0, geo.Nt, n)
+        kk = rng.integers(0, geo.Nx, n)
+        t0 = time.perf_counter()
+        direct.fwd_points(f, geo.dt, geo.dx, geo.tau(), geo.q(), ii, li)
+        t1 = time.perf_counter()
+        direct.adj_points(g_img, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q(), jj, kk)
+        t2 = time.perf_counter()
+        return (t1 - t0) * geo.Ntau * geo.Nq / n + (t2 - t1) * geo.Nt * geo.Nx / n
+
+    for _ in range(args.warmup):
+        step()
+    tot = sum(step() for _ in range(args.steps))
+    value = args.steps / tot
+    cores = direct.num_threads()
+    sample = (f"FP64 direct-sum oracle, {n} random outputs + {n} random gather points per step, "
+              f"extrapolated to full 2048^2 transforms")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-direct", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import paper_1604_07651_gb300 as hr
+    geo, f_np = make_workload(rank)
+    dev = torch.device("cuda", local)
+    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, device=local)
+    f = torch.tensor(f_np, dtype=torch.float32, device=dev)
+    g = torch.empty((geo.Nq, geo.Ntau), dtype=torch.float32, device=dev)
+    fa = torch.empty_like(f)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.forward(f, out=g)
+        plan.adjoint(g, out=fa)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: per-step CUDA events, L2 flushed before each step
+    plan.set_profiling(True)
+    plan.profile_read()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            starts[s].record(stream)
+            step()
+            ends[s].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    prof = plan.profile_read()
+    plan.set_profiling(False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # dominant kernel and its roofline
+    hbm, peak_kind = _peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    stages = {k: {"ms_per_launch": (v["ms"] / v["launches"]) if v["launches"] else 0.0,
+                  "launches_per_step": v["launches"] / args.steps,
+                  "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0,
+                  "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
+              for k, v in prof.items()}
+    launches = int(round(sum(v["launches"] for v in prof.values()) / args.steps)) * args.steps
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "flushed before each step (256 MiB write)",
+                   "method": {"sigma": plan.desc.sigma, "omega_c": plan.desc.omega_c,
+                              "tsplit": [plan.desc.tsplit[i] for i in range(plan.desc.n_tsplit)],
+                              "n_qsplit": plan.desc.n_qsplit},
+                   "lattices": [(p["Ntheta"], p["Nrho"], p["Ptheta"], p["Prho"]) for p in plan.pieces()]},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None},
+        "stages": stages,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    fh = torch.tensor(f_np, dtype=torch.float32).pin_memory()
+    gh = torch.empty((geo.Nq, geo.Ntau), dtype=torch.float32).pin_memory()
+    fah = torch.empty((geo.Nx, geo.Nt), dtype=torch.float32).pin_memory()
+    fd = torch.empty_like(f)
+
+    def e2e_step():
+        fd.copy_(fh, non_blocking=True)
+        plan.forward(fd, out=g)
+        plan.adjoint(g, out=fa)
+        gh.copy_(g, non_blocking=True)
+        fah.copy_(fa, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    result["e2e"] = {"value": world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                     "h2d_bytes_per_step": f.numel() * 4,
+                     "d2h_bytes_per_step": (g.numel() + fa.numel()) * 4}
+
+    if rank == 0:
+        # accuracy of this run's results against the FP64 oracle (sampled points)
+        from oracle import direct
+        direct.build()
+        rng = np.random.default_rng(2048)
+        ii = rng.integers(0, geo.Ntau, 4096)
+        li = rng.integers(0, geo.Nq, 4096)
+        plan.forward(f, out=g)
+        gnp = g.cpu().numpy()
+        ref = direct.fwd_points(f_np, geo.dt, geo.dx, geo.tau(), geo.q(), ii, li)
+        acc = {"fwd_rel_l2_vs_direct_sum_4096_points": float(np.linalg.norm(gnp[li, ii] - ref) / np.linalg.norm(ref))}
+        jj = rng.integers(0, geo.Nt, 4096)
+        kk = rng.integers(0, geo.Nx, 4096)
+        gsm = gnp.astype(np.float64)
+        plan.adjoint(torch.tensor(gsm, dtype=torch.float32, device=dev), out=fa)
+        refa = direct.adj_points(gsm, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q(), jj, kk)
+        fanp = fa.cpu().numpy()
+        acc["adj_rel_l2_vs_direct_sum_4096_points"] = float(np.linalg.norm(fanp[kk, jj] - refa) / np.linalg.norm(refa))
+        result["accuracy"] = acc
+
+        if not args.no_direct:
+            # the plain form: direct summation over hyperbolas on this GPU
+            dq = (geo.qmax - geo.qmin) / (geo.Nq - 1)
+            from paper_1604_07651_gb300 import direct_forward, direct_adjoint
+            for _ in range(1):
+                gd = direct_forward(f, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax)
+                direct_adjoint(gd, geo.Nt, geo.Nx, geo.dt, geo.dx, geo.qmin, geo.qmax)
+            torch.cuda.synchronize()
+            reps = 2
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                gd = direct_forward(f, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax)
+                direct_adjoint(gd, geo.Nt, geo.Nx, geo.dt, geo.dx, geo.qmin, geo.qmax)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            dms = a0.elapsed_time(a1) / reps
+            gdn = gd.cpu().numpy()
+            derr = float(np.linalg.norm(gdn[li, ii] - ref) / np.linalg.norm(ref))
+            result["gpu_direct_sum"] = {"value": 1e3 / dms, "unit": UNIT, "ms_per_pair": dms,
+                                        "fwd_rel_l2_vs_oracle": derr,
+                                        "speedup_of_log_polar": value / world / (1e3 / dms)}
+        if not args.no_cpu_baseline and world == 1:
+            result["cpu_baseline"] = cpu_baseline(geo, f_np)
+        print(json.dumps(result), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * hradon -- fast hyperbolic Radon transform on sm_103a (C ABI).
+ *
+ * Computes the hyperbolic Radon transform of a common-midpoint gather,
+ *
+ *     R_h f(tau, q) = int f( sqrt(tau^2 + q^2 x^2), x ) dx            (Eq. (1))
+ *                   = 2 int_0^inf f( sqrt(tau^2 + q^2 x^2), x ) dx   (Eq. (3)),
+ *
+ * and its adjoint (defined by <R_h f, g> = <f, R_h* g>, Eq. (16)) with the
+ * log-polar method of Nikitin, Andersson, Carlsson and Duchkov
+ * (arXiv:1604.07651, Sections 2-4): after the change of variables
+ * (s, y) = (t^2, x^2) the transform is a straight-line Radon transform, which
+ * becomes a convolution in log-polar coordinates (Eq. (6)-(7)) evaluated by
+ * cubic B-spline gridding, FFT and B-spline interpolation (Eq. (14)-(17)).
+ *
+ * Grids (physical units, any consistent set, e.g. s, km, s/km):
+ *   gather   f[k][j] = f(t_j, x_k),  t_j = j dt (j < Nt),  x_k = k dx (k < Nx)
+ *   image    g[l][i] = R f(tau_i, q_l), tau_i = tau0 + i dtau (i < Ntau),
+ *            q_l = qmin + l (qmax - qmin)/(Nq - 1) (l < Nq)
+ * Both arrays are row-major float32 with the time axis fastest:
+ * f is [Nx][Nt], g is [Nq][Ntau]. The gather is zero outside
+ * [0, (Nt-1)dt] x [0, (Nx-1)dx] (Eq. (11)).
+ *
+ * Ownership: every data pointer passed to radon_fwd / radon_adj /
+ * radon_direct_* is a device pointer owned by the caller, on the plan's
+ * device. The plan owns its tables, kernel spectra and work buffers
+ * (allocated by radon_plan_create*, freed by radon_plan_destroy). Outputs
+ * are overwritten, never accumulated. Calls are asynchronous on the given
+ * stream (a cudaStream_t passed as void*, NULL = the legacy default
+ * stream); no call in this header synchronises the host except plan
+ * creation. A plan may be used by one stream at a time.
+ *
+ * Errors: every function returns a radon_status and never aborts;
+ * radon_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef HRADON_H
+#define HRADON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RADON_OK = 0,
+    RADON_ERR_INVALID_ARG = 1, /* bad size, spacing, range, pointer or descriptor field */
+    RADON_ERR_OOM = 2,         /* device or host allocation failed */
+    RADON_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    RADON_ERR_UNSUPPORTED = 4  /* sizes beyond what the kernels handle (see radon_plan_create_ex) */
+} radon_status;
+
+typedef struct radon_plan_s* radon_plan;
+
+#define RADON_MAX_TSPLIT 8
+
+/*
+ * Problem and method parameters.
+ *   Nt, Nx, Ntau >= 2, Nq >= 1; dt, dx > 0; 0 <= qmin <= qmax (qmin < qmax if Nq > 1);
+ *   tau0 >= 0; dtau > 0 (0 selects (Nt-1) dt / (Ntau-1), i.e. tau on [0, T]).
+ *   sigma   : the log-polar sample spacing of Eq. (18) is divided by sigma (> 0).
+ *   omega_c : half-width, in cycles per lattice cell, of the frequency
+ *             rectangle L of Eq. (14) and (17) (0 < omega_c < 0.5).
+ *   tsplit  : split points of the time integral, Eq. (19), as fractions of
+ *             T = (Nt-1) dt in (0, 1); the split uses a smooth partition of
+ *             unity in t (raised cosine in log t over [b/1.25, 1.25 b]).
+ *   n_qsplit: number of slowness pieces (Section 5), >= 1; each gets its
+ *             own log-polar setup.
+ *   device  : CUDA device ordinal, or -1 for the calling thread's current device.
+ */
+typedef struct {
+    int Nt, Nx, Ntau, Nq;
+    double dt, dx;
+    double qmin, qmax;
+    double tau0, dtau;
+    double sigma, omega_c;
+    int n_tsplit;
+    double tsplit[RADON_MAX_TSPLIT];
+    int n_qsplit;
+    int device;
+} radon_desc;
+
+/* Geometry of one sub-problem of a plan (for tests and diagnostics). */
+typedef struct {
+    int jt_lo, jt_hi;        /* gather samples of the time piece */
+    int l_lo, l_hi;          /* output columns of the slowness piece */
+    double alpha, beta;      /* rotation and sector opening (Section 2.1) */
+    double a, O1, O2;        /* square side and centre (Section 2.1) */
+    double a_r, r_max;       /* radial extent of the lines meeting the data */
+    double dphi_rule, deta_rule; /* spacing of Eq. (18) */
+    double dtheta, drho, theta0, rho0;
+    int Ntheta, Nrho;        /* lattice, including two guard cells per side */
+    int Ptheta, Prho;        /* zero-padded FFT sizes */
+    int k1max, k2max;        /* frequency rectangle L in bins */
+    double theta_m;          /* kernel window |theta| <= theta_m */
+} radon_piece_info;
+
+/*
+ * Fill *d with the default method parameters for the given problem:
+ * tau0 = 0, dtau = (Nt-1) dt/(Ntau-1), sigma = 1.5, omega_c = 0.3,
+ * one time split at 0.4 T, one slowness piece, current device.
+ * Returns RADON_ERR_INVALID_ARG for a NULL d.
+ */
+radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau, int Nq, double dt,
+                             double dx, double qmin, double qmax);
+
+/*
+ * Plan for the grids above with qmin = 0 and default method parameters.
+ * Equivalent to radon_desc_init(&d, Nt, Nx, Ntau, Nq, dt, dx, 0, qmax) and
+ * radon_plan_create_ex(out, &d). Synchronous; runs FP64 plan-time kernels.
+ */
+radon_status radon_plan_create(radon_plan* out, int Nt, int Nx, int Ntau, int Nq, double dt,
+                               double dx, double qmax);
+
+/*
+ * Plan for an arbitrary descriptor. Computes every sub-problem's geometry
+ * in FP64 on the host (Sections 2.1, 2.2, 4), its kernel spectrum
+ * chi_L zeta_hat / B3_hat^2 with an FP64 quadrature on the device, and the
+ * lookup tables; allocates the work buffers. On failure *out is NULL.
+ * RADON_ERR_UNSUPPORTED if a lattice needs more shared memory per block
+ * than the device offers (FFT lengths above 12288 along rho or 6144 along
+ * theta on GB300).
+ */
+radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* d);
+
+/* Release everything the plan owns. NULL is accepted. Synchronises the plan's device. */
+radon_status radon_plan_destroy(radon_plan p);
+
+/*
+ * Forward transform: g = R_h f. f: device [Nx][Nt] float32 (read only),
+ * g: device [Nq][Ntau] float32 (overwritten). f and g must not overlap.
+ */
+radon_status radon_fwd(radon_plan p, const float* f, float* g, void* stream);
+
+/*
+ * Adjoint transform: f = R_h* g, the exact transpose of radon_fwd up to
+ * FP32 rounding. g: device [Nq][Ntau], f: device [Nx][Nt] (overwritten).
+ */
+radon_status radon_adj(radon_plan p, const float* g, float* f, void* stream);
+
+/* Number of sub-problems (time pieces x slowness pieces) of a plan. */
+radon_status radon_plan_num_pieces(radon_plan p, int* n);
+
+/* Geometry of sub-problem `piece` (0 <= piece < num_pieces). */
+radon_status radon_plan_piece_info(radon_plan p, int piece, radon_piece_info* info);
+
+/*
+ * Geometry of every sub-problem for a descriptor, computed on the host only
+ * (no device is touched): writes min(*npieces, max_infos) entries of infos
+ * (infos may be NULL when max_infos is 0) and sets *npieces to the total
+ * count, slowness-piece major as in a plan. Same checks as radon_plan_create_ex.
+ */
+radon_status radon_geometry(const radon_desc* d, int* npieces, radon_piece_info* infos,
+                            int max_infos);
+
+/* The descriptor the plan was built from (defaults resolved). */
+radon_status radon_plan_desc(radon_plan p, radon_desc* d);
+
+/* Device bytes owned by the plan. */
+radon_status radon_plan_device_bytes(radon_plan p, size_t* bytes);
+
+/*
+ * Direct summation over hyperbolas on the GPU (FP32), the O(N^3) comparator:
+ * Eq. (3) discretised as in the paper's reference (Section 5): Keys cubic
+ * interpolation in t, trapezoid in x. Same grids and layouts as above with
+ * q_l = qmin + l dq. Device pointers; asynchronous on stream.
+ */
+radon_status radon_direct_fwd(const float* f, float* g, int Nt, int Nx, int Ntau, int Nq,
+                              double dt, double dx, double tau0, double dtau, double qmin,
+                              double dq, void* stream);
+/* Its exact transpose. */
+radon_status radon_direct_adj(const float* g, float* f, int Nt, int Nx, int Ntau, int Nq,
+                              double dt, double dx, double tau0, double dtau, double qmin,
+                              double dq, void* stream);
+
+/*
+ * Per-stage timing (off by default). While enabled, every kernel launch of
+ * radon_fwd / radon_adj is bracketed by CUDA events recorded on the launch
+ * stream. Stages: 0 gridding + row FFT (forward), 1 column FFT*K*IFFT
+ * (forward), 2 inverse row FFT (forward), 3 output interpolation (forward),
+ * 4 output scatter + row FFT (adjoint), 5 column FFT*conj(K)*IFFT (adjoint),
+ * 6 inverse row FFT (adjoint), 7 gather of the samples (adjoint).
+ */
+#define RADON_NSTAGES 8
+radon_status radon_plan_set_profiling(radon_plan p, int enable);
+
+/*
+ * Totals since the last read: for each stage, the summed kernel time in ms,
+ * the number of launches, and the algorithmic bytes those launches must move
+ * (inputs read once plus outputs written once; lattice-sized intermediates
+ * counted at their stored size). Synchronises the recorded events, then
+ * resets the totals. Any output pointer may be NULL.
+ */
+radon_status radon_plan_profile_read(radon_plan p, double ms[RADON_NSTAGES],
+                                     long long launches[RADON_NSTAGES],
+                                     double bytes[RADON_NSTAGES]);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* radon_last_error(void);
+
+/* Library version string. */
+const char* radon_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HRADON_H */

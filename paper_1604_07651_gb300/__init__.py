@@ -1,0 +1,215 @@
+"""hradon: fast hyperbolic Radon transform (log-polar method) on sm_103a.
+
+Thin Python binding of the C ABI in ``include/hradon.h``. Every step of the
+transform runs in the library's CUDA kernels; PyTorch only provides device
+memory, streams and autograd. There is no CPU fallback: without a CUDA device
+or without the built library every call raises.
+
+    plan = Plan(Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax)      # geometry, kernel spectra
+    g = plan.forward(f)        # f: cuda float32 [Nx][Nt]  ->  g: [Nq][Ntau]
+    f2 = plan.adjoint(g)       # exact transpose (Eq. (16))
+    g = radon(f, plan)         # autograd op: backward is the adjoint
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import torch
+
+from . import _lib
+from ._lib import RadonError, RadonDesc, RadonPieceInfo
+
+__all__ = ["Plan", "radon", "radon_adjoint", "direct_forward", "direct_adjoint", "RadonError",
+           "HRadon"]
+
+
+def _stream_ptr(device: torch.device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check_tensor(t: torch.Tensor, shape, name: str, device: torch.device):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device != device or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 tensor on {device}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+class Plan:
+    """Plan of the log-polar hyperbolic Radon transform for one geometry.
+
+    Parameters mirror ``radon_desc``: gather ``Nt`` x ``Nx`` samples at
+    ``dt``, ``dx``; image ``Ntau`` x ``Nq`` with ``tau_i = tau0 + i*dtau``
+    (``dtau=0``: ``(Nt-1) dt/(Ntau-1)``) and ``q`` evenly on
+    ``[qmin, qmax]``; method parameters ``sigma``, ``omega_c``, ``tsplit``
+    (split points of Eq. (19) as fractions of T), ``n_qsplit``.
+    """
+
+    def __init__(self, Nt: int, Nx: int, Ntau: int, Nq: int, dt: float, dx: float,
+                 qmin: float = 0.0, qmax: float = 1.0, *, tau0: float = 0.0, dtau: float = 0.0,
+                 sigma: float | None = None, omega_c: float | None = None,
+                 tsplit: Sequence[float] | None = None, n_qsplit: int = 1,
+                 device: int | torch.device | None = None):
+        lib = _lib.load()
+        d = RadonDesc()
+        _lib.check(lib.radon_desc_init(ctypes.byref(d), Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax))
+        d.tau0, d.dtau, d.n_qsplit = tau0, dtau, n_qsplit
+        if sigma is not None:
+            d.sigma = sigma
+        if omega_c is not None:
+            d.omega_c = omega_c
+        if tsplit is not None:
+            ts = list(tsplit)
+            if len(ts) > _lib.MAX_TSPLIT:
+                raise ValueError(f"at most {_lib.MAX_TSPLIT} time splits")
+            d.n_tsplit = len(ts)
+            for i, v in enumerate(ts):
+                d.tsplit[i] = v
+        if device is None:
+            dev = torch.cuda.current_device()
+        else:
+            dev = torch.device(device).index if not isinstance(device, int) else device
+            dev = 0 if dev is None else dev
+        d.device = dev
+        self.device = torch.device("cuda", dev)
+        self._handle = ctypes.c_void_p()
+        _lib.check(lib.radon_plan_create_ex(ctypes.byref(self._handle), ctypes.byref(d)))
+        out = RadonDesc()
+        _lib.check(lib.radon_plan_desc(self._handle, ctypes.byref(out)))
+        self.desc = out
+        self.Nt, self.Nx, self.Ntau, self.Nq = Nt, Nx, Ntau, Nq
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_handle", None) is not None and self._handle.value:
+            _lib.load().radon_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- info ---------------------------------------------------------------
+    def pieces(self) -> list[dict]:
+        lib = _lib.load()
+        n = ctypes.c_int()
+        _lib.check(lib.radon_plan_num_pieces(self._handle, ctypes.byref(n)))
+        out = []
+        for p in range(n.value):
+            info = RadonPieceInfo()
+            _lib.check(lib.radon_plan_piece_info(self._handle, p, ctypes.byref(info)))
+            out.append({name: getattr(info, name) for name, _ in RadonPieceInfo._fields_})
+        return out
+
+    def device_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _lib.check(_lib.load().radon_plan_device_bytes(self._handle, ctypes.byref(v)))
+        return v.value
+
+    def set_profiling(self, enable: bool = True):
+        _lib.check(_lib.load().radon_plan_set_profiling(self._handle, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        """Per-stage kernel time (ms), launches and algorithmic bytes since the
+        last read (synchronises the recorded events)."""
+        n = _lib.NSTAGES
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        by = (ctypes.c_double * n)()
+        _lib.check(_lib.load().radon_plan_profile_read(self._handle, ms, cnt, by))
+        return {name: {"ms": ms[i], "launches": cnt[i], "bytes": by[i]}
+                for i, name in enumerate(_lib.STAGE_NAMES)}
+
+    # -- transforms ---------------------------------------------------------
+    def forward(self, f: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """g = R_h f on the current stream. f: [Nx][Nt] float32 on the plan's device."""
+        _check_tensor(f, (self.Nx, self.Nt), "f", self.device)
+        if out is None:
+            out = torch.empty((self.Nq, self.Ntau), dtype=torch.float32, device=self.device)
+        _check_tensor(out, (self.Nq, self.Ntau), "out", self.device)
+        _lib.check(_lib.load().radon_fwd(self._handle, ctypes.c_void_p(f.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device)))
+        return out
+
+    def adjoint(self, g: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """f = R_h* g on the current stream. g: [Nq][Ntau] float32 on the plan's device."""
+        _check_tensor(g, (self.Nq, self.Ntau), "g", self.device)
+        if out is None:
+            out = torch.empty((self.Nx, self.Nt), dtype=torch.float32, device=self.device)
+        _check_tensor(out, (self.Nx, self.Nt), "out", self.device)
+        _lib.check(_lib.load().radon_adj(self._handle, ctypes.c_void_p(g.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device)))
+        return out
+
+
+class HRadon(torch.autograd.Function):
+    """Autograd op of the linear operator R_h: the backward of the forward
+    transform is the adjoint transform (Eq. (16)); nothing is saved."""
+
+    @staticmethod
+    def forward(ctx, f, plan):
+        ctx.plan = plan
+        return plan.forward(f.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_g):
+        return ctx.plan.adjoint(grad_g.contiguous()), None
+
+
+class HRadonAdjoint(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, g, plan):
+        ctx.plan = plan
+        return plan.adjoint(g.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_f):
+        return ctx.plan.forward(grad_f.contiguous()), None
+
+
+def radon(f: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable forward transform."""
+    return HRadon.apply(f, plan)
+
+
+def radon_adjoint(g: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable adjoint transform."""
+    return HRadonAdjoint.apply(g, plan)
+
+
+def direct_forward(f: torch.Tensor, Ntau: int, Nq: int, dt: float, dx: float, qmin: float,
+                   qmax: float, tau0: float = 0.0, dtau: float = 0.0) -> torch.Tensor:
+    """Direct summation over hyperbolas on the GPU (the O(N^3) comparator)."""
+    Nx, Nt = f.shape
+    dtau = dtau if dtau > 0 else (Nt - 1) * dt / (Ntau - 1)
+    dq = (qmax - qmin) / (Nq - 1) if Nq > 1 else 0.0
+    _check_tensor(f, (Nx, Nt), "f", f.device)
+    g = torch.empty((Nq, Ntau), dtype=torch.float32, device=f.device)
+    _lib.check(_lib.load().radon_direct_fwd(ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                            Nt, Nx, Ntau, Nq, dt, dx, tau0, dtau, qmin, dq,
+                                            _stream_ptr(f.device)))
+    return g
+
+
+def direct_adjoint(g: torch.Tensor, Nt: int, Nx: int, dt: float, dx: float, qmin: float,
+                   qmax: float, tau0: float = 0.0, dtau: float = 0.0) -> torch.Tensor:
+    """Transpose of ``direct_forward``."""
+    Nq, Ntau = g.shape
+    dtau = dtau if dtau > 0 else (Nt - 1) * dt / (Ntau - 1)
+    dq = (qmax - qmin) / (Nq - 1) if Nq > 1 else 0.0
+    _check_tensor(g, (Nq, Ntau), "g", g.device)
+    f = torch.empty((Nx, Nt), dtype=torch.float32, device=g.device)
+    _lib.check(_lib.load().radon_direct_adj(ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+                                            Nt, Nx, Ntau, Nq, dt, dx, tau0, dtau, qmin, dq,
+                                            _stream_ptr(g.device)))
+    return f

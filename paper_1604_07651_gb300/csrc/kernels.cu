@@ -1,0 +1,585 @@
+// sm_103a kernels of the log-polar hyperbolic Radon transform and of the
+// direct-summation comparator.
+//
+// Forward, per sub-problem (Sections 2-4):
+//   k_scatter_samples  gridding of the gather samples onto the log-polar
+//                      lattice with cubic B-splines (Eq. (14)-(15)), one band
+//                      of lattice rows per CTA in shared memory, fused with the
+//                      real FFT of those rows (first half of Eq. (7)/(16));
+//   k_colconv          FFT along theta, product with the kernel spectrum
+//                      chi_L zeta_hat / B3_hat^2 (Eq. (16)-(17)), inverse FFT;
+//   k_rows_c2r         inverse real FFT of the rows -> B-spline coefficients;
+//   k_gather_radon     cubic B-spline interpolation at (phi, eta) = P2 S(tau^2,
+//                      q^2) (Eq. (17)), summed over the time pieces.
+// Adjoint (Eq. (16), Section 3): the same kernels with the roles exchanged:
+//   k_scatter_radon -> k_colconv (conjugate kernel) -> k_rows_c2r ->
+//   k_gather_samples.
+//
+// Lattice positions are computed in float-float where FP32 loses digits (see
+// hostdev.h); everything else is FP32. Shared-memory accumulation uses FP32
+// atomics, so the last bits of the forward gridding depend on the order in
+// which warps arrive.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace hr {
+
+__device__ __forceinline__ cf ldcf(const cf* p) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ ff ldff(const ff* p) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+
+// Block-cooperative Stockham FFT of `batch` sequences of length n stored
+// back to back in shared memory at a; b is a scratch buffer of the same size.
+// Returns the buffer that holds the result (a or b).
+template <int DIR>
+__device__ cf* block_fft(cf* a, cf* b, int n, int batch, const cf* __restrict__ tw,
+                         const FftPlan& fp) {
+    int Ns = 1;
+    for (int s = 0; s < fp.nst; ++s) {
+        const int R = fp.rad[s];
+        const int nb = n / R;
+        const int total = nb * batch;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int bb = idx / nb;
+            const int j = idx - bb * nb;
+            const cf* in = a + bb * n;
+            cf* out = b + bb * n;
+            if (R == 4)
+                stockham_butterfly<4>(in, out, n, Ns, j, tw, DIR);
+            else if (R == 2)
+                stockham_butterfly<2>(in, out, n, Ns, j, tw, DIR);
+            else
+                stockham_butterfly<3>(in, out, n, Ns, j, tw, DIR);
+        }
+        __syncthreads();
+        cf* t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// e^rho of output row i of a column: E0 + E1 i + E2 i^2 in float-float.
+__device__ __forceinline__ ff radon_e(const ff* E, int i) {
+    const float fi = (float)i;
+    ff t = ff_mul_f(ldff(E + 2), fi);
+    t = ff_add(t, ldff(E + 1));
+    t = ff_mul_f(t, fi);
+    return ff_add(t, ldff(E));
+}
+
+// Lattice rho-position of a point at distance e (float-float) from the
+// origin: nearest lattice line n from a rough log, then the exact offset
+// log(e / e^{rho_n}) = log1p((e - e^{rho_n}) / e^{rho_n}).
+__device__ __forceinline__ float rho_position(const PieceDev& P, ff e, const ff* Rtab,
+                                              float logscale) {
+    int n = __float2int_rn((logscale * __logf(e.hi) - P.rho0) * P.inv_drho);
+    n = min(max(n, 0), P.Nrho - 1);
+    const ff Rn = ldff(Rtab + n);
+    const float d = logscale * log1pf(ff_diff(e, Rn) / Rn.hi);
+    return (float)n + d * P.inv_drho;
+}
+
+// --------------------------------------------------------------------------
+// Row kernels: scatter into a band of lattice rows, then real FFT of the rows.
+// Shared memory: [R][Prho] floats (rows, viewed as [R][M] complex) plus
+// [R][M] complex scratch for the FFT.
+// --------------------------------------------------------------------------
+
+extern __shared__ __align__(16) float smem_f[];
+
+__device__ void rows_r2c_write(const PieceDev& P, int mb, int nrows, cf* __restrict__ spec) {
+    const int M = P.Prho / 2;
+    cf* rows = reinterpret_cast<cf*>(smem_f);
+    cf* tmp = rows + P.R * M;
+    cf* Z = block_fft<-1>(rows, tmp, M, nrows, P.twM, P.fftM);
+    const int nk = P.k2max + 1;
+    const int per_kb = nrows * P.CB;
+    const int total = P.nkb * per_kb;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int kb = idx / per_kb;
+        const int rem = idx - kb * per_kb;
+        const int m = rem / P.CB;
+        const int c = rem - m * P.CB;
+        const int k = kb * P.CB + c;
+        cf X = {0.f, 0.f};
+        if (k < nk) X = r2c_post(Z + m * M, M, k, P.twP);
+        spec[((size_t)kb * P.Ntheta + (mb + m)) * P.CB + c] = X;
+    }
+}
+
+__device__ __forceinline__ void zero_rows(const PieceDev& P) {
+    float4* p = reinterpret_cast<float4*>(smem_f);
+    const int n4 = P.R * P.Prho / 4;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Forward gridding (Eq. (15)) of the gather f[Nx][Nt] for one band of rows.
+__global__ void __launch_bounds__(512) k_scatter_samples(PieceDev P, const float* __restrict__ f,
+                                                         cf* __restrict__ spec) {
+    const int mb = blockIdx.x * P.R;
+    const int nrows = min(P.R, P.Ntheta - mb);
+    zero_rows(P);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int2* jr = P.jband + (size_t)blockIdx.x * P.Nx;
+    const ff cr = ldff(P.rowc + mb), sr = ldff(P.rows + mb);
+    for (int k = warp; k < P.Nx; k += nw) {
+        const int2 r = __ldg(jr + k);
+        if (r.x > r.y) continue;
+        const ff h = ldff(P.hk + k);
+        const float wk = __ldg(P.wk + k);
+        const float* fk = f + (size_t)k * P.Nt;
+        for (int j = r.x + lane; j <= r.y; j += 32) {
+            const ff lam = ldff(P.lam + j);
+            const float xth = (float)mb + angle_from(lam, h, cr, sr) * P.inv_dtheta;
+            const ff u2 = radius2(lam, h);
+            const float xrh = rho_position(P, u2, P.R2, 0.5f);
+            const float fm = floorf(xth), fn = floorf(xrh);
+            const int m0 = (int)fm - 1, n0 = (int)fn - 1;
+            if (n0 < 0 || n0 + 3 >= P.Nrho || m0 < 0 || m0 + 3 >= P.Ntheta) continue;
+            const float val = __ldg(fk + j) * __ldg(P.cj + j) * wk * rsqrtf(u2.hi);
+            float wt[4], wr[4];
+            b3_weights(xth - fm, wt);
+            b3_weights(xrh - fn, wr);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int m = m0 + a - mb;
+                if (m < 0 || m >= nrows) continue;
+                const float va = val * wt[a];
+                float* row = smem_f + m * P.Prho + n0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) atomicAdd(row + c, va * wr[c]);
+            }
+        }
+    }
+    __syncthreads();
+    rows_r2c_write(P, mb, nrows, spec);
+}
+
+// Adjoint of the output interpolation: scatter g[Nq][Ntau] of this slowness
+// piece's columns onto one band of rows (transpose of Eq. (17)).
+__global__ void __launch_bounds__(512) k_scatter_radon(PieceDev P, const float* __restrict__ g,
+                                                       cf* __restrict__ spec) {
+    const int mb = blockIdx.x * P.R;
+    const int nrows = min(P.R, P.Ntheta - mb);
+    zero_rows(P);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int2 lr = __ldg(P.lband + blockIdx.x);
+    for (int l = lr.x + warp; l <= lr.y; l += nw) {
+        const int lc = l - P.l_lo;
+        const int m0 = __ldg(P.colm0 + lc);
+        const float4 w4 = __ldg(P.colw + lc);
+        const float wt[4] = {w4.x, w4.y, w4.z, w4.w};
+        const float sc = __ldg(P.colscale + lc);
+        const ff* E = P.E + 3 * lc;
+        const float* gl = g + (size_t)l * P.Ntau;
+        for (int i = lane; i < P.Ntau; i += 32) {
+            const ff e = radon_e(E, i);
+            if (!(e.hi >= P.a_r && e.hi <= P.r_max)) continue;
+            const float xrh = rho_position(P, e, P.R1, 1.0f);
+            const float fn = floorf(xrh);
+            const int n0 = (int)fn - 1;
+            if (n0 < 0 || n0 + 3 >= P.Nrho) continue;
+            float wr[4];
+            b3_weights(xrh - fn, wr);
+            const float val = __ldg(gl + i) * sc;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int m = m0 + a - mb;
+                if (m < 0 || m >= nrows) continue;
+                const float va = val * wt[a];
+                float* row = smem_f + m * P.Prho + n0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) atomicAdd(row + c, va * wr[c]);
+            }
+        }
+    }
+    __syncthreads();
+    rows_r2c_write(P, mb, nrows, spec);
+}
+
+// --------------------------------------------------------------------------
+// Column pass: FFT along theta, product with K (or conj K), inverse FFT.
+// One block of CB spectrum columns per CTA; the blocked layout
+// [kb][m][CB] makes every load and store contiguous.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_colconv(PieceDev P, const cf* __restrict__ in,
+                                                 cf* __restrict__ out, int adjoint) {
+    const int kb = blockIdx.x;
+    const int CB = P.CB, Pt = P.Ptheta, Nth = P.Ntheta;
+    cf* A = reinterpret_cast<cf*>(smem_f);
+    cf* B = A + CB * Pt;
+    const cf* src = in + (size_t)kb * Nth * CB;
+    for (int idx = threadIdx.x; idx < Pt * CB; idx += blockDim.x) {
+        const int m = idx / CB, c = idx - m * CB;
+        A[c * Pt + m] = m < Nth ? ldcf(src + idx) : cf{0.f, 0.f};
+    }
+    __syncthreads();
+    cf* X = block_fft<-1>(A, B, Pt, CB, P.twT, P.fftT);
+    cf* Y = (X == A) ? B : A;
+    const int k1n = P.k1max + 1;
+    const cf* Kb = P.K + (size_t)kb * k1n * CB;
+    for (int idx = threadIdx.x; idx < Pt * CB; idx += blockDim.x) {
+        const int c = idx / Pt, k1 = idx - c * Pt;
+        const int kk = k1 <= Pt / 2 ? k1 : Pt - k1;
+        cf v = {0.f, 0.f};
+        if (kk < k1n) {
+            const cf kv = ldcf(Kb + kk * CB + c);
+            v = adjoint ? cmulc(X[idx], kv) : cmul(X[idx], kv);
+        }
+        X[idx] = v;
+    }
+    __syncthreads();
+    cf* Zr = block_fft<+1>(X, Y, Pt, CB, P.twT, P.fftT);
+    cf* dst = out + (size_t)kb * Nth * CB;
+    for (int idx = threadIdx.x; idx < Nth * CB; idx += blockDim.x) {
+        const int m = idx / CB, c = idx - m * CB;
+        dst[idx] = Zr[c * Pt + m];
+    }
+}
+
+// --------------------------------------------------------------------------
+// Inverse real FFT of a band of rows from the half spectrum (bins <= k2max,
+// the rest zero) into the real lattice P.lat[Ntheta][Nrho].
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_rows_c2r(PieceDev P, const cf* __restrict__ spec) {
+    const int mb = blockIdx.x * P.R;
+    const int nrows = min(P.R, P.Ntheta - mb);
+    const int M = P.Prho / 2;
+    cf* X = reinterpret_cast<cf*>(smem_f);
+    cf* tmp = X + P.R * M;
+    const int nk = P.k2max + 1;
+    for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
+        const int m = idx / M, k = idx - m * M;
+        cf v = {0.f, 0.f};
+        if (k < nk) {
+            const int kb = k / P.CB, c = k - kb * P.CB;
+            v = ldcf(spec + ((size_t)kb * P.Ntheta + (mb + m)) * P.CB + c);
+        }
+        X[idx] = v;
+    }
+    __syncthreads();
+    const int half = M / 2;
+    for (int idx = threadIdx.x; idx < nrows * (half + 1); idx += blockDim.x) {
+        const int m = idx / (half + 1), k = idx - m * (half + 1);
+        cf* row = X + m * M;
+        if (k == 0)
+            row[0] = c2r_pre_dc(row[0]);
+        else
+            c2r_pre_pair(row, M, k, P.twP);
+    }
+    __syncthreads();
+    cf* z = block_fft<+1>(X, tmp, M, nrows, P.twM, P.fftM);
+    const int Nr = P.Nrho;
+    for (int idx = threadIdx.x; idx < nrows * Nr; idx += blockDim.x) {
+        const int m = idx / Nr, n = idx - m * Nr;
+        const cf v = z[m * M + (n >> 1)];
+        P.lat[(size_t)(mb + m) * Nr + n] = (n & 1) ? v.y : v.x;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Gathers.
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ float taps16(const float* __restrict__ lat, int Nr, int m0, int n0,
+                                        const float wt[4], const float wr[4]) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const float* row = lat + (size_t)(m0 + a) * Nr + n0;
+        const float r = __ldg(row) * wr[0] + __ldg(row + 1) * wr[1] + __ldg(row + 2) * wr[2] +
+                        __ldg(row + 3) * wr[3];
+        s += wt[a] * r;
+    }
+    return s;
+}
+
+// Forward output interpolation (Eq. (17)) for the columns [l_lo, l_hi] of one
+// slowness piece, summed over its time pieces (pieces[0..np)).
+__global__ void __launch_bounds__(256) k_gather_radon(const PieceDev* __restrict__ pieces, int np,
+                                                      int l_lo, int ncol, int Ntau,
+                                                      float* __restrict__ g) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)ncol * Ntau) return;
+    const int lc = (int)(idx / Ntau);
+    const int i = (int)(idx - (long)lc * Ntau);
+    float acc = 0.f;
+    for (int p = 0; p < np; ++p) {
+        const PieceDev& P = pieces[p];
+        const ff e = radon_e(P.E + 3 * lc, i);
+        if (!(e.hi >= P.a_r && e.hi <= P.r_max)) continue;
+        const float xrh = rho_position(P, e, P.R1, 1.0f);
+        const float fn = floorf(xrh);
+        const int n0 = (int)fn - 1;
+        if (n0 < 0 || n0 + 3 >= P.Nrho) continue;
+        float wr[4];
+        b3_weights(xrh - fn, wr);
+        const float4 w4 = __ldg(P.colw + lc);
+        const float wt[4] = {w4.x, w4.y, w4.z, w4.w};
+        const int m0 = __ldg(P.colm0 + lc);
+        acc += __ldg(P.colscale + lc) * taps16(P.lat, P.Nrho, m0, n0, wt, wr);
+    }
+    g[(size_t)(l_lo + lc) * Ntau + i] = acc;
+}
+
+// Adjoint of the gridding (transpose of Eq. (15)): every gather sample reads
+// the 4x4 taps of each sub-problem that holds it.
+__global__ void __launch_bounds__(256) k_gather_samples(const PieceDev* __restrict__ pieces, int np,
+                                                        int Nt, int Nx, float* __restrict__ f) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)Nt * Nx) return;
+    const int k = (int)(idx / Nt);
+    const int j = (int)(idx - (long)k * Nt);
+    float acc = 0.f;
+    for (int p = 0; p < np; ++p) {
+        const PieceDev& P = pieces[p];
+        if (j < P.jt_lo || j > P.jt_hi || j < __ldg(P.jfirst + k)) continue;
+        const ff lam = ldff(P.lam + j);
+        const ff h = ldff(P.hk + k);
+        const float phia = P.alpha + atan2f(h.hi, lam.hi);
+        int mr = __float2int_rn((phia - P.theta0) * P.inv_dtheta);
+        mr = min(max(mr, 0), P.Ntheta - 1);
+        const float xth = (float)mr +
+                          angle_from(lam, h, ldff(P.rowc + mr), ldff(P.rows + mr)) * P.inv_dtheta;
+        const ff u2 = radius2(lam, h);
+        const float xrh = rho_position(P, u2, P.R2, 0.5f);
+        const float fm = floorf(xth), fn = floorf(xrh);
+        const int m0 = (int)fm - 1, n0 = (int)fn - 1;
+        if (n0 < 0 || n0 + 3 >= P.Nrho || m0 < 0 || m0 + 3 >= P.Ntheta) continue;
+        float wt[4], wr[4];
+        b3_weights(xth - fm, wt);
+        b3_weights(xrh - fn, wr);
+        const float w = __ldg(P.cj + j) * __ldg(P.wk + k) * rsqrtf(u2.hi);
+        acc += w * taps16(P.lat, P.Nrho, m0, n0, wt, wr);
+    }
+    f[idx] = acc;
+}
+
+// --------------------------------------------------------------------------
+// Plan time, FP64: zeta_hat as a quadrature written as a matrix product,
+// Z = A B with A[k1][n] = cos(2 pi theta_n w1) and B[n][k2] the complex
+// weights (real and imaginary parts as two matrices). 16x16 tiles.
+// --------------------------------------------------------------------------
+__global__ void k_zeta_gemm(const double* __restrict__ A, const double* __restrict__ Bre,
+                            const double* __restrict__ Bim, int n1, int nn, int n2,
+                            double* __restrict__ Zre, double* __restrict__ Zim) {
+    __shared__ double sA[16][17];
+    __shared__ double sR[16][17];
+    __shared__ double sI[16][17];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int row = blockIdx.y * 16 + ty;   // k1
+    const int col = blockIdx.x * 16 + tx;   // k2
+    double accr = 0.0, acci = 0.0;
+    for (int t0 = 0; t0 < nn; t0 += 16) {
+        const int ta = t0 + tx, tb = t0 + ty;
+        sA[ty][tx] = (row < n1 && ta < nn) ? A[(size_t)row * nn + ta] : 0.0;
+        sR[ty][tx] = (tb < nn && col < n2) ? Bre[(size_t)tb * n2 + col] : 0.0;
+        sI[ty][tx] = (tb < nn && col < n2) ? Bim[(size_t)tb * n2 + col] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            accr = fma(sA[ty][q], sR[q][tx], accr);
+            acci = fma(sA[ty][q], sI[q][tx], acci);
+        }
+        __syncthreads();
+    }
+    if (row < n1 && col < n2) {
+        Zre[(size_t)row * n2 + col] = accr;
+        Zim[(size_t)row * n2 + col] = acci;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Direct summation over hyperbolas on the GPU (FP32): the plain O(N^3)
+// comparator, Eq. (3) with the same discretisation as the paper's reference
+// (Keys cubic in t, trapezoid in x).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float keys_w(float s) {
+    s = fabsf(s);
+    if (s <= 1.f) return (1.5f * s - 2.5f) * s * s + 1.f;
+    if (s < 2.f) return ((-0.5f * s + 2.5f) * s - 4.f) * s + 2.f;
+    return 0.f;
+}
+
+__global__ void __launch_bounds__(256) k_direct_fwd(const float* __restrict__ f, float* __restrict__ g,
+                                                    int Nt, int Nx, int Ntau, float tau0_dt,
+                                                    float dtau_dt, float qmin_dx_dt, float dq_dx_dt,
+                                                    float two_dx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = blockIdx.y;
+    if (i >= Ntau) return;
+    const float tt = tau0_dt + dtau_dt * (float)i;      // tau / dt
+    const float qq = qmin_dx_dt + dq_dx_dt * (float)l;  // q dx / dt
+    const float tt2 = tt * tt, qq2 = qq * qq;
+    float acc = 0.f;
+    for (int k = 0; k < Nx; ++k) {
+        const float p = sqrtf(tt2 + qq2 * (float)k * (float)k);  // t / dt
+        const float fl = floorf(p);
+        const int j0 = (int)fl;
+        const float s = p - fl;
+        const float* tr = f + (size_t)k * Nt;
+        float v = 0.f;
+        if (j0 - 1 >= 0 && j0 + 2 < Nt) {
+            v = __ldg(tr + j0 - 1) * keys_w(s + 1.f) + __ldg(tr + j0) * keys_w(s) +
+                __ldg(tr + j0 + 1) * keys_w(s - 1.f) + __ldg(tr + j0 + 2) * keys_w(s - 2.f);
+        } else {
+#pragma unroll
+            for (int d = -1; d <= 2; ++d) {
+                const int jj = j0 + d;
+                if (jj >= 0 && jj < Nt) v += __ldg(tr + jj) * keys_w(s - (float)d);
+            }
+        }
+        acc += (k == 0 || k == Nx - 1) ? 0.5f * v : v;
+    }
+    g[(size_t)l * Ntau + i] = two_dx * acc;
+}
+
+__global__ void __launch_bounds__(256) k_direct_adj(const float* __restrict__ g, float* __restrict__ f,
+                                                    int Nt, int Nx, int Ntau, int Nq, float tau0_dt,
+                                                    float dtau_dt, float qmin_dx_dt, float dq_dx_dt,
+                                                    float two_dx) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (j >= Nt) return;
+    const float kk = (float)k;
+    const float lo = fmaxf((float)(j - 2), 0.f), hi = (float)(j + 2);
+    float acc = 0.f;
+    for (int l = 0; l < Nq; ++l) {
+        const float qq = (qmin_dx_dt + dq_dx_dt * (float)l) * kk;   // q x / dt
+        const float qq2 = qq * qq;
+        const float hi2 = hi * hi - qq2;
+        if (hi2 < 0.f) continue;
+        const float lo2 = lo * lo - qq2;
+        const float tlo = lo2 > 0.f ? sqrtf(lo2) : 0.f;
+        const float thi = sqrtf(hi2);
+        int i0 = (int)floorf((tlo - tau0_dt) / dtau_dt) - 1;
+        int i1 = (int)ceilf((thi - tau0_dt) / dtau_dt) + 1;
+        i0 = max(i0, 0);
+        i1 = min(i1, Ntau - 1);
+        const float* gl = g + (size_t)l * Ntau;
+        for (int i = i0; i <= i1; ++i) {
+            const float tt = tau0_dt + dtau_dt * (float)i;
+            const float p = sqrtf(tt * tt + qq2);
+            acc += __ldg(gl + i) * keys_w(p - (float)j);
+        }
+    }
+    f[(size_t)k * Nt + j] = ((k == 0 || k == Nx - 1) ? 0.5f : 1.f) * two_dx * acc;
+}
+
+// --------------------------------------------------------------------------
+// Launchers
+// --------------------------------------------------------------------------
+static int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+size_t scatter_smem_bytes(const PieceDev& P) {
+    return (size_t)2 * P.R * P.Prho * sizeof(float);
+}
+
+size_t colconv_smem_bytes(const PieceDev& P) {
+    return (size_t)2 * P.CB * P.Ptheta * sizeof(cf);
+}
+
+int max_smem_optin() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+static int set_smem(const void* fn, size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+int launch_scatter_gather_rows(const PieceDev& P, const float* f, cf* spec, void* stream) {
+    const size_t sm = scatter_smem_bytes(P);
+    if (int e = set_smem((const void*)k_scatter_samples, sm)) return e;
+    k_scatter_samples<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, f, spec);
+    return check_launch();
+}
+
+int launch_scatter_radon_rows(const PieceDev& P, const float* g, cf* spec, void* stream) {
+    const size_t sm = scatter_smem_bytes(P);
+    if (int e = set_smem((const void*)k_scatter_radon, sm)) return e;
+    k_scatter_radon<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, g, spec);
+    return check_launch();
+}
+
+int launch_colconv(const PieceDev& P, const cf* in, cf* out, int adjoint, void* stream) {
+    const size_t sm = colconv_smem_bytes(P);
+    if (int e = set_smem((const void*)k_colconv, sm)) return e;
+    k_colconv<<<P.nkb, 512, sm, (cudaStream_t)stream>>>(P, in, out, adjoint);
+    return check_launch();
+}
+
+int launch_rows_c2r(const PieceDev& P, const cf* spec, void* stream) {
+    const size_t sm = scatter_smem_bytes(P);
+    if (int e = set_smem((const void*)k_rows_c2r, sm)) return e;
+    k_rows_c2r<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, spec);
+    return check_launch();
+}
+
+int launch_gather_radon(const PieceDev* pieces, int npieces, const PieceDev* dev_pieces, int l_lo,
+                        int l_hi, float* g, void* stream) {
+    (void)pieces;
+    const int ncol = l_hi - l_lo + 1;
+    const int Ntau = pieces[0].Ntau;
+    const long total = (long)ncol * Ntau;
+    const int bs = 256;
+    const long nb = (total + bs - 1) / bs;
+    k_gather_radon<<<(unsigned)nb, bs, 0, (cudaStream_t)stream>>>(dev_pieces, npieces, l_lo, ncol,
+                                                                 Ntau, g);
+    return check_launch();
+}
+
+int launch_gather_samples(const PieceDev* dev_pieces, int npieces, int Nt, int Nx, float* f,
+                          void* stream) {
+    const long total = (long)Nt * Nx;
+    const int bs = 256;
+    const long nb = (total + bs - 1) / bs;
+    k_gather_samples<<<(unsigned)nb, bs, 0, (cudaStream_t)stream>>>(dev_pieces, npieces, Nt, Nx, f);
+    return check_launch();
+}
+
+int launch_zeta_gemm(const double* A, const double* Bre, const double* Bim, int n1, int nn, int n2,
+                     double* Zre, double* Zim, void* stream) {
+    dim3 bs(16, 16);
+    dim3 gs((n2 + 15) / 16, (n1 + 15) / 16);
+    k_zeta_gemm<<<gs, bs, 0, (cudaStream_t)stream>>>(A, Bre, Bim, n1, nn, n2, Zre, Zim);
+    return check_launch();
+}
+
+int launch_direct_fwd(const float* f, float* g, int Nt, int Nx, int Ntau, int Nq, double dt,
+                      double dx, double tau0, double dtau, double qmin, double dq, void* stream) {
+    dim3 bs(256);
+    dim3 gs((Ntau + 255) / 256, Nq);
+    k_direct_fwd<<<gs, bs, 0, (cudaStream_t)stream>>>(
+        f, g, Nt, Nx, Ntau, (float)(tau0 / dt), (float)(dtau / dt), (float)(qmin * dx / dt),
+        (float)(dq * dx / dt), (float)(2.0 * dx));
+    return check_launch();
+}
+
+int launch_direct_adj(const float* g, float* f, int Nt, int Nx, int Ntau, int Nq, double dt,
+                      double dx, double tau0, double dtau, double qmin, double dq, void* stream) {
+    dim3 bs(256);
+    dim3 gs((Nt + 255) / 256, Nx);
+    k_direct_adj<<<gs, bs, 0, (cudaStream_t)stream>>>(
+        g, f, Nt, Nx, Ntau, Nq, (float)(tau0 / dt), (float)(dtau / dt), (float)(qmin * dx / dt),
+        (float)(dq * dx / dt), (float)(2.0 * dx));
+    return check_launch();
+}
+
+}  // namespace hr

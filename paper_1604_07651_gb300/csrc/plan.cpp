@@ -1,0 +1,1039 @@
+// Host side of hradon: descriptor checks, the FP64 geometry of every
+// sub-problem (Sections 2.1, 2.2 and 4 of the paper), the plan-time tables,
+// the kernel spectra and the C ABI of include/hradon.h.
+//
+// Built with -ffp-contract=off so that the FP64 geometry rounds the same way
+// on every host architecture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hradon.h"
+#include "internal.h"
+
+using namespace hr;
+
+namespace {
+
+thread_local std::string g_err;
+
+radon_status fail(radon_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+const double kPi = 3.14159265358979323846;
+const double kTOverlap = 1.25;   // half-width ratio of the time-partition transition bands
+const double kBetaMin = 1e-3;    // smallest angular opening of a sub-problem
+
+ff to_ff(double v) {
+    float hi = (float)v;
+    float lo = (float)(v - (double)hi);
+    return {hi, lo};
+}
+
+int fft_size(int n) {
+    long best = -1;
+    for (long p = 1; p < 2L * n + 2; p *= 2) {
+        for (long c : {p, 3 * p})
+            if (c >= n && (best < 0 || c < best)) best = c;
+    }
+    return (int)best;
+}
+
+FftPlan make_fft_plan(int n) {
+    FftPlan fp;
+    fp.n = n;
+    int rad[32];
+    fp.nst = fft_radices(n, rad);
+    for (int i = 0; i < fp.nst && i < 24; ++i) fp.rad[i] = rad[i];
+    return fp;
+}
+
+// Rising edge of the time partition at split b (raised cosine in log t).
+double t_edge(double tb, double b, double r) {
+    double u = std::log(std::max(tb, 1e-300) / b) / std::log(r);
+    u = std::min(1.0, std::max(-1.0, u));
+    return 0.5 * (1.0 + std::sin(0.5 * kPi * u));
+}
+
+// Accepted time split points (sorted, separated by the overlap bands).
+std::vector<double> accepted_splits(const radon_desc& d) {
+    std::vector<double> in(d.tsplit, d.tsplit + std::max(0, std::min(d.n_tsplit, RADON_MAX_TSPLIT)));
+    std::sort(in.begin(), in.end());
+    std::vector<double> bs;
+    const double r = kTOverlap;
+    for (double b : in) {
+        if (!(b > 0.0 && b < 1.0)) continue;
+        if (b * r >= 1.0) continue;
+        if (!bs.empty() && b / r < bs.back() * r) continue;
+        bs.push_back(b);
+    }
+    return bs;
+}
+
+struct TPiece { int lo, hi, idx; };
+
+std::vector<TPiece> time_pieces(const radon_desc& d, const std::vector<double>& bs) {
+    const double n = (double)(d.Nt - 1);
+    const double r = kTOverlap;
+    std::vector<TPiece> out;
+    const int np = (int)bs.size() + 1;
+    for (int p = 0; p < np; ++p) {
+        int lo = p == 0 ? 0 : (int)std::ceil(bs[p - 1] / r * n - 1e-9);
+        int hi = p == np - 1 ? d.Nt - 1 : (int)std::floor(bs[p] * r * n + 1e-9);
+        out.push_back({lo, hi, p});
+    }
+    return out;
+}
+
+double t_window(const std::vector<double>& bs, int p, double tb) {
+    const double r = kTOverlap;
+    double lo = p == 0 ? 1.0 : t_edge(tb, bs[p - 1], r);
+    double hi = p == (int)bs.size() ? 0.0 : t_edge(tb, bs[p], r);
+    return lo - hi;
+}
+
+std::vector<double> q_grid(const radon_desc& d) {
+    std::vector<double> q(d.Nq);
+    if (d.Nq == 1) {
+        q[0] = d.qmin;
+        return q;
+    }
+    const double dq = (d.qmax - d.qmin) / (d.Nq - 1);
+    for (int l = 0; l < d.Nq; ++l) q[l] = d.qmin + l * dq;
+    return q;
+}
+
+std::vector<std::pair<int, int>> slowness_pieces(const radon_desc& d) {
+    const double T = (d.Nt - 1) * d.dt, X = (d.Nx - 1) * d.dx;
+    std::vector<double> q = q_grid(d);
+    int n = std::max(1, d.n_qsplit);
+    if (n == 1 || d.Nq < 2) return {{0, d.Nq - 1}};
+    std::vector<double> psi(d.Nq);
+    for (int l = 0; l < d.Nq; ++l) {
+        double qb = q[l] * X / T;
+        psi[l] = std::atan(qb * qb);
+    }
+    const double lo = psi[0], hi = psi[d.Nq - 1];
+    std::vector<int> piece(d.Nq, 0);
+    for (int p = 1; p < n; ++p) {
+        double bnd = lo + (hi - lo) * p / n;
+        for (int l = 0; l < d.Nq; ++l)
+            if (psi[l] >= bnd) piece[l] += 1;
+    }
+    std::vector<std::pair<int, int>> out;
+    for (int p = 0; p < n; ++p) {
+        int a = -1, b = -1;
+        for (int l = 0; l < d.Nq; ++l)
+            if (piece[l] == p) {
+                if (a < 0) a = l;
+                b = l;
+            }
+        if (a >= 0) out.push_back({a, b});
+    }
+    return out;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double pp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1.0);
+            double dz = p1 / pp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+    std::sort(x.begin(), x.end());
+}
+
+double sinc4(double w) {
+    if (w == 0.0) return 1.0;
+    double s = std::sin(kPi * w) / (kPi * w);
+    return s * s * s * s;
+}
+
+double b3(double x) {
+    double ax = std::fabs(x);
+    if (ax < 1.0) return 2.0 / 3.0 - ax * ax + 0.5 * ax * ax * ax;
+    if (ax < 2.0) return (2.0 - ax) * (2.0 - ax) * (2.0 - ax) / 6.0;
+    return 0.0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+struct HostPiece {
+    int tpiece = 0, jt_lo = 0, jt_hi = 0, l_lo = 0, l_hi = 0;
+    double s0 = 0, s1 = 0, m_lo = 0, m_hi = 0, alpha = 0, beta = 0, a = 0, O1 = 0, O2 = 0;
+    double c_min = 0, k2 = 0, a_r = 0, r_max = 0, dphi_rule = 0, deta_rule = 0;
+    int n_theta = 0, n_rho = 0, Ntheta = 0, Nrho = 0, Ptheta = 0, Prho = 0, k1max = 0, k2max = 0;
+    double dtheta = 0, drho = 0, theta0 = 0, rho0 = 0, theta_m = 0;
+    std::vector<int> jfirst;
+    PieceDev dev{};
+};
+
+struct radon_plan_s {
+    radon_desc d{};
+    int device = 0;
+    std::vector<HostPiece> pieces;               // slowness-piece major
+    std::vector<std::pair<int, int>> qpieces;    // columns of each slowness piece
+    std::vector<int> qfirst, qcount;             // pieces of each slowness piece
+    PieceDev* dev_pieces = nullptr;
+    cf* spec1 = nullptr;
+    cf* spec2 = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    // per-stage timing
+    bool profiling = false;
+    struct Rec { int stage; cudaEvent_t a, b; double bytes; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+    size_t pool_next = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+radon_status dev_upload(radon_plan_s* p, const std::vector<T>& v, const T** out) {
+    void* ptr = nullptr;
+    size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RADON_ERR_OOM, "cudaMalloc of a plan table failed");
+    }
+    p->allocs.push_back(ptr);
+    p->bytes += bytes;
+    if (!v.empty() && cudaMemcpy(ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(RADON_ERR_CUDA, "cudaMemcpy of a plan table failed");
+    *out = (const T*)ptr;
+    return RADON_OK;
+}
+
+radon_status dev_alloc(radon_plan_s* p, size_t bytes, void** out) {
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RADON_ERR_OOM, "cudaMalloc of a plan buffer failed");
+    }
+    p->allocs.push_back(ptr);
+    p->bytes += bytes;
+    *out = ptr;
+    return RADON_OK;
+}
+
+radon_status check_desc(const radon_desc* d) {
+    if (!d) return fail(RADON_ERR_INVALID_ARG, "descriptor is NULL");
+    if (d->Nt < 2 || d->Nx < 2 || d->Ntau < 2 || d->Nq < 1)
+        return fail(RADON_ERR_INVALID_ARG, "need Nt, Nx, Ntau >= 2 and Nq >= 1");
+    if ((long)d->Nt * d->Nx > (1L << 30) || (long)d->Ntau * d->Nq > (1L << 30) || d->Nt > (1 << 20) ||
+        d->Ntau > (1 << 20))
+        return fail(RADON_ERR_UNSUPPORTED, "gather or image larger than 2^30 samples");
+    if (!(d->dt > 0) || !(d->dx > 0) || !std::isfinite(d->dt) || !std::isfinite(d->dx))
+        return fail(RADON_ERR_INVALID_ARG, "dt and dx must be positive and finite");
+    if (!(d->qmin >= 0) || !(d->qmax >= d->qmin) || !std::isfinite(d->qmax))
+        return fail(RADON_ERR_INVALID_ARG, "need 0 <= qmin <= qmax");
+    if (d->Nq > 1 && !(d->qmax > d->qmin))
+        return fail(RADON_ERR_INVALID_ARG, "need qmin < qmax when Nq > 1");
+    if (d->Nq == 1 && !(d->qmin > 0) && !(d->qmax > 0))
+        return fail(RADON_ERR_INVALID_ARG, "a single slowness column needs q > 0");
+    if (!(d->tau0 >= 0) || !std::isfinite(d->tau0) || !(d->dtau >= 0) || !std::isfinite(d->dtau))
+        return fail(RADON_ERR_INVALID_ARG, "need tau0 >= 0 and dtau >= 0");
+    if (!(d->sigma > 0) || !(d->sigma <= 16))
+        return fail(RADON_ERR_INVALID_ARG, "need 0 < sigma <= 16");
+    if (!(d->omega_c > 0) || !(d->omega_c < 0.5))
+        return fail(RADON_ERR_INVALID_ARG, "need 0 < omega_c < 0.5");
+    if (d->n_tsplit < 0 || d->n_tsplit > RADON_MAX_TSPLIT)
+        return fail(RADON_ERR_INVALID_ARG, "n_tsplit out of range");
+    if (d->n_qsplit < 1 || d->n_qsplit > 64)
+        return fail(RADON_ERR_INVALID_ARG, "need 1 <= n_qsplit <= 64");
+    return RADON_OK;
+}
+
+void map_T(const HostPiece& h, double s, double y, double& u1, double& u2) {
+    const double ca = std::cos(h.alpha), sa = std::sin(h.alpha);
+    const double ds = s - 0.5, dy = y - 0.5;
+    u1 = h.a * (ca * ds - sa * dy) + h.O1;
+    u2 = h.a * (sa * ds + ca * dy) + h.O2;
+}
+
+// Vertices of {(s,y) in [s0,s1]x[0,1] : s >= c + m y}.
+std::vector<std::pair<double, double>> clip_region(double s0, double s1, double c, double m) {
+    const double rect[4][2] = {{s0, 0.0}, {s1, 0.0}, {s1, 1.0}, {s0, 1.0}};
+    std::vector<std::pair<double, double>> out;
+    for (int i = 0; i < 4; ++i) {
+        const double* p = rect[i];
+        const double* r = rect[(i + 1) % 4];
+        double vp = p[0] - c - m * p[1], vr = r[0] - c - m * r[1];
+        if (vp >= 0) out.push_back({p[0], p[1]});
+        if ((vp >= 0) != (vr >= 0)) {
+            double t = vp / (vp - vr);
+            out.push_back({p[0] + t * (r[0] - p[0]), p[1] + t * (r[1] - p[1])});
+        }
+    }
+    return out;
+}
+
+// FP64 geometry of one sub-problem (same definitions as the paper's
+// Sections 2.1, 2.2 and 4; readings documented with the descriptor).
+radon_status make_geometry(const radon_desc& d, const TPiece& tp, std::pair<int, int> lq,
+                           HostPiece& h, std::vector<double>& phi_all) {
+    const double n_t = d.Nt - 1, n_x = d.Nx - 1;
+    const double T = n_t * d.dt, X = n_x * d.dx;
+    const std::vector<double> q = q_grid(d);
+    h.tpiece = tp.idx;
+    h.jt_lo = tp.lo;
+    h.jt_hi = tp.hi;
+    h.l_lo = lq.first;
+    h.l_hi = lq.second;
+    h.s0 = (tp.lo / n_t) * (tp.lo / n_t);
+    h.s1 = (tp.hi / n_t) * (tp.hi / n_t);
+    double qb_lo = q[lq.first] * X / T, qb_hi = q[lq.second] * X / T;
+    h.m_lo = qb_lo * qb_lo;
+    h.m_hi = qb_hi * qb_hi;
+    double psi_lo = std::atan(h.m_lo), psi_hi = std::atan(h.m_hi);
+    if (psi_hi - psi_lo < kBetaMin) {
+        double mid = std::max(0.5 * (psi_lo + psi_hi), 0.5 * kBetaMin);
+        psi_lo = mid - 0.5 * kBetaMin;
+        psi_hi = mid + 0.5 * kBetaMin;
+    }
+    h.beta = psi_hi - psi_lo;
+    h.alpha = 0.5 * (psi_hi + psi_lo);
+    {
+        const double s2a = std::sin(2 * h.alpha), sb = std::sin(h.beta), cb = std::cos(h.beta);
+        h.a = sb / std::sqrt(s2a * sb + cb * (s2a + sb) + 1.0);
+        const double th = std::tan(h.beta / 2);
+        h.O1 = h.a * std::sin(h.alpha + kPi / 4) / (std::sqrt(2.0) * th);
+        h.O2 = h.a * std::cos(h.alpha + kPi / 4) * th / std::sqrt(2.0);
+    }
+    // Mute with the smallest slowness of the whole problem.
+    const double taub_min = d.tau0 / T;
+    h.c_min = taub_min * taub_min;
+    const double qb0 = q[0] * X / T;
+    h.k2 = qb0 * qb0;
+    h.jfirst.assign(d.Nx, tp.hi + 1);
+    for (int k = 0; k < d.Nx; ++k) {
+        const double xb = k / n_x;
+        const double lim = h.c_min + h.k2 * (xb * xb);
+        for (int j = tp.lo; j <= tp.hi; ++j) {
+            const double tb = j / n_t;
+            if (tb * tb >= lim) {
+                h.jfirst[k] = j;
+                break;
+            }
+        }
+    }
+    // Inner and outer radius over the data region.
+    auto poly = clip_region(h.s0, h.s1, h.c_min, h.k2);
+    if (poly.empty()) return fail(RADON_ERR_INVALID_ARG, "a time piece lies entirely in the muted region");
+    double ar = 1e300, rmax = 0.0;
+    for (double th : {-h.beta / 2, h.beta / 2})
+        for (auto& v : poly) {
+            double u1, u2;
+            map_T(h, v.first, v.second, u1, u2);
+            ar = std::min(ar, u1 * std::cos(th) + u2 * std::sin(th));
+        }
+    for (auto& v : poly) {
+        double u1, u2;
+        map_T(h, v.first, v.second, u1, u2);
+        rmax = std::max(rmax, std::sqrt(u1 * u1 + u2 * u2));
+    }
+    if (!(ar > 0)) return fail(RADON_ERR_INVALID_ARG, "degenerate log-polar setup (inner radius <= 0)");
+    h.a_r = ar;
+    h.r_max = rmax;
+    // Spacing of Eq. (18) over every sample of the time piece.
+    const int nj = tp.hi - tp.lo + 1;
+    phi_all.assign((size_t)nj * d.Nx, 0.0);
+    std::vector<double> eta_prev(nj), eta_cur(nj);
+    double dphi = 0.0, deta = 0.0;
+    for (int k = 0; k < d.Nx; ++k) {
+        const double xb = k / n_x;
+        const double y = xb * xb;
+        double* ph = &phi_all[(size_t)k * nj];
+        for (int jj = 0; jj < nj; ++jj) {
+            const double tb = (tp.lo + jj) / n_t;
+            double u1, u2;
+            map_T(h, tb * tb, y, u1, u2);
+            ph[jj] = std::atan2(u2, u1);
+            eta_cur[jj] = 0.5 * std::log(u1 * u1 + u2 * u2);
+            if (jj > 0) {
+                dphi = std::max(dphi, std::fabs(ph[jj] - ph[jj - 1]));
+                deta = std::max(deta, std::fabs(eta_cur[jj] - eta_cur[jj - 1]));
+            }
+            if (k > 0) {
+                dphi = std::max(dphi, std::fabs(ph[jj] - phi_all[(size_t)(k - 1) * nj + jj]));
+                deta = std::max(deta, std::fabs(eta_cur[jj] - eta_prev[jj]));
+            }
+        }
+        std::swap(eta_prev, eta_cur);
+    }
+    if (!(dphi > 0) || !(deta > 0)) return fail(RADON_ERR_INVALID_ARG, "degenerate sample spacing");
+    h.dphi_rule = dphi;
+    h.deta_rule = deta;
+    h.n_theta = std::max(1, (int)std::ceil(d.sigma * h.beta / dphi - 1e-9));
+    const double L_rho = std::log(h.r_max) - std::log(h.a_r);
+    h.n_rho = std::max(1, (int)std::ceil(d.sigma * L_rho / deta - 1e-9));
+    h.dtheta = h.beta / h.n_theta;
+    h.drho = L_rho / h.n_rho;
+    h.theta0 = -h.beta / 2 - 2 * h.dtheta;
+    h.rho0 = std::log(h.a_r) - 2 * h.drho;
+    h.Ntheta = h.n_theta + 5;
+    h.Nrho = h.n_rho + 5;
+    h.theta_m = std::min((h.Ntheta - 1) * h.dtheta, std::acos(std::exp(-(h.Nrho - 1) * h.drho)));
+    const int Ka = (int)std::ceil(h.theta_m / h.dtheta - 1e-9);
+    const int Kr = (int)std::ceil(-std::log(std::cos(h.theta_m)) / h.drho - 1e-9);
+    h.Ptheta = fft_size(h.Ntheta + Ka);
+    h.Prho = fft_size(h.Nrho + Kr);
+    h.k1max = std::min((int)std::floor(d.omega_c * h.Ptheta), h.Ptheta / 2 - 1);
+    h.k2max = std::min((int)std::floor(d.omega_c * h.Prho), h.Prho / 2 - 1);
+    return RADON_OK;
+}
+
+// zeta_hat on the lattice's frequency grid (FP64 quadrature on the device),
+// divided twice by the B-spline symbol and normalised for the kernels' FFT
+// conventions; stored in the blocked layout [nkb][k1max+1][CB].
+radon_status kernel_spectrum(radon_plan_s* p, const HostPiece& h, int CB, int nkb,
+                             std::vector<cf>& Kout) {
+    const int n1 = h.k1max + 1, n2 = h.k2max + 1;
+    const double dw1 = 1.0 / (h.Ptheta * h.dtheta), dw2 = 1.0 / (h.Prho * h.drho);
+    const double lc_m = std::log(std::cos(h.theta_m));
+    const double cycles = h.k1max * dw1 * h.theta_m + h.k2max * dw2 * std::fabs(lc_m);
+    const int npan = (int)std::ceil(cycles) + 4;
+    std::vector<double> gx, gw;
+    gauss_legendre(20, gx, gw);
+    const int nn = npan * 20;
+    std::vector<double> th(nn), wt(nn);
+    for (int pn = 0; pn < npan; ++pn) {
+        const double e0 = h.theta_m * pn / npan, e1 = h.theta_m * (pn + 1) / npan;
+        const double hh = 0.5 * (e1 - e0), c = 0.5 * (e1 + e0);
+        for (int i = 0; i < 20; ++i) {
+            th[pn * 20 + i] = c + hh * gx[i];
+            wt[pn * 20 + i] = hh * gw[i];
+        }
+    }
+    std::vector<double> A((size_t)n1 * nn), Bre((size_t)nn * n2), Bim((size_t)nn * n2);
+    for (int k1 = 0; k1 < n1; ++k1)
+        for (int t = 0; t < nn; ++t) A[(size_t)k1 * nn + t] = std::cos(2 * kPi * th[t] * (k1 * dw1));
+    for (int t = 0; t < nn; ++t) {
+        const double ct = std::cos(th[t]);
+        const double l = std::log(ct);
+        const double base = wt[t] / ct;
+        for (int k2 = 0; k2 < n2; ++k2) {
+            const double ph = -2 * kPi * (k2 * dw2) * l;
+            Bre[(size_t)t * n2 + k2] = base * std::cos(ph);
+            Bim[(size_t)t * n2 + k2] = base * std::sin(ph);
+        }
+    }
+    double *dA = nullptr, *dR = nullptr, *dI = nullptr, *dZr = nullptr, *dZi = nullptr;
+    const size_t bA = A.size() * 8, bB = Bre.size() * 8, bZ = (size_t)n1 * n2 * 8;
+    if (cudaMalloc(&dA, bA) != cudaSuccess || cudaMalloc(&dR, bB) != cudaSuccess ||
+        cudaMalloc(&dI, bB) != cudaSuccess || cudaMalloc(&dZr, bZ) != cudaSuccess ||
+        cudaMalloc(&dZi, bZ) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dA); cudaFree(dR); cudaFree(dI); cudaFree(dZr); cudaFree(dZi);
+        return fail(RADON_ERR_OOM, "cudaMalloc of the kernel-spectrum work arrays failed");
+    }
+    radon_status st = RADON_OK;
+    std::vector<double> Zr((size_t)n1 * n2), Zi((size_t)n1 * n2);
+    if (cudaMemcpy(dA, A.data(), bA, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dR, Bre.data(), bB, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dI, Bim.data(), bB, cudaMemcpyHostToDevice) != cudaSuccess) {
+        st = fail(RADON_ERR_CUDA, "upload of the kernel-spectrum tables failed");
+    } else if (int e = launch_zeta_gemm(dA, dR, dI, n1, nn, n2, dZr, dZi, nullptr)) {
+        st = fail(RADON_ERR_CUDA, std::string("zeta quadrature launch failed: ") +
+                                      cudaGetErrorString((cudaError_t)e));
+    } else if (cudaMemcpy(Zr.data(), dZr, bZ, cudaMemcpyDeviceToHost) != cudaSuccess ||
+               cudaMemcpy(Zi.data(), dZi, bZ, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        st = fail(RADON_ERR_CUDA, "zeta quadrature failed");
+    }
+    cudaFree(dA); cudaFree(dR); cudaFree(dI); cudaFree(dZr); cudaFree(dZi);
+    if (st != RADON_OK) return st;
+    (void)p;
+    // Normalisation of the kernels' transforms: the row real FFT pair without
+    // its 1/2 factors gives 2 Prho, the unnormalised column pair Ptheta.
+    const double norm = 1.0 / (2.0 * h.Ptheta * h.Prho);
+    Kout.assign((size_t)nkb * n1 * CB, cf{0.f, 0.f});
+    for (int k1 = 0; k1 < n1; ++k1) {
+        const double s1 = sinc4((double)k1 / h.Ptheta);
+        for (int k2 = 0; k2 < n2; ++k2) {
+            const double s2 = sinc4((double)k2 / h.Prho);
+            const double den = (s1 * s2) * (s1 * s2);
+            const double zr = 2.0 * Zr[(size_t)k1 * n2 + k2], zi = 2.0 * Zi[(size_t)k1 * n2 + k2];
+            const int kb = k2 / CB, c = k2 % CB;
+            Kout[((size_t)kb * n1 + k1) * CB + c] = {(float)(zr / den * norm), (float)(zi / den * norm)};
+        }
+    }
+    return RADON_OK;
+}
+
+radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector<double>& bs,
+                                const std::vector<double>& phi_all, int smem_max) {
+    const radon_desc& d = p->d;
+    const double n_t = d.Nt - 1, n_x = d.Nx - 1;
+    const double T = n_t * d.dt, X = n_x * d.dx;
+    PieceDev& P = h.dev;
+    P.Ntheta = h.Ntheta;
+    P.Nrho = h.Nrho;
+    P.Ptheta = h.Ptheta;
+    P.Prho = h.Prho;
+    P.k1max = h.k1max;
+    P.k2max = h.k2max;
+    // rows per band and spectrum columns per block, bounded by shared memory
+    int R = 4;
+    while (R > 1 && (size_t)2 * R * h.Prho * sizeof(float) > (size_t)smem_max) --R;
+    if ((size_t)2 * R * h.Prho * sizeof(float) > (size_t)smem_max)
+        return fail(RADON_ERR_UNSUPPORTED, "row FFT length too large for shared memory");
+    int CB = 2;
+    while (CB > 1 && (size_t)2 * CB * h.Ptheta * sizeof(cf) > (size_t)smem_max) --CB;
+    if ((size_t)2 * CB * h.Ptheta * sizeof(cf) > (size_t)smem_max)
+        return fail(RADON_ERR_UNSUPPORTED, "column FFT length too large for shared memory");
+    P.R = R;
+    P.CB = CB;
+    P.nkb = (h.k2max + 1 + CB - 1) / CB;
+    P.nbands = (h.Ntheta + R - 1) / R;
+    P.theta0 = (float)h.theta0;
+    P.rho0 = (float)h.rho0;
+    P.inv_dtheta = (float)(1.0 / h.dtheta);
+    P.inv_drho = (float)(1.0 / h.drho);
+    P.alpha = (float)h.alpha;
+    P.Nt = d.Nt;
+    P.Nx = d.Nx;
+    P.jt_lo = h.jt_lo;
+    P.jt_hi = h.jt_hi;
+    P.Ntau = d.Ntau;
+    P.l_lo = h.l_lo;
+    P.l_hi = h.l_hi;
+    P.a_r = (float)h.a_r;
+    P.r_max = (float)h.r_max;
+    P.fftM = make_fft_plan(h.Prho / 2);
+    P.fftT = make_fft_plan(h.Ptheta);
+
+    const double ca = std::cos(h.alpha), sa = std::sin(h.alpha);
+    const double Oa = h.O1 * ca + h.O2 * sa;       // O . e_alpha
+    const double Op = -h.O1 * sa + h.O2 * ca;      // O . e_perp
+    std::vector<ff> lam(d.Nt), hk(d.Nx);
+    std::vector<float> cj(d.Nt, 0.f), wk(d.Nx);
+    for (int j = 0; j < d.Nt; ++j) {
+        const double tb = j / n_t;
+        lam[j] = to_ff(h.a * (tb * tb - 0.5) + Oa);
+        if (j >= h.jt_lo && j <= h.jt_hi) {
+            const double w = t_window(bs, h.tpiece, tb);
+            cj[j] = (float)(w * 2.0 * h.a * h.a * tb / (n_t * n_x * h.dtheta * h.drho));
+        }
+    }
+    for (int k = 0; k < d.Nx; ++k) {
+        const double xb = k / n_x;
+        hk[k] = to_ff(h.a * (xb * xb - 0.5) + Op);
+        wk[k] = (k == 0 || k == d.Nx - 1) ? 0.5f : 1.0f;
+    }
+    std::vector<ff> rowc(h.Ntheta), rows(h.Ntheta), R1(h.Nrho), R2(h.Nrho);
+    for (int m = 0; m < h.Ntheta; ++m) {
+        const double g = h.theta0 + m * h.dtheta - h.alpha;
+        rowc[m] = to_ff(std::cos(g));
+        rows[m] = to_ff(std::sin(g));
+    }
+    for (int n = 0; n < h.Nrho; ++n) {
+        const double rho = h.rho0 + n * h.drho;
+        R1[n] = to_ff(std::exp(rho));
+        R2[n] = to_ff(std::exp(2.0 * rho));
+    }
+    // candidate sample range of every band (from the FP64 angles, one sample of margin)
+    const int nj = h.jt_hi - h.jt_lo + 1;
+    std::vector<int2> jband((size_t)P.nbands * d.Nx, int2{1, 0});
+    for (int k = 0; k < d.Nx; ++k) {
+        const int jstart = std::max(h.jt_lo, h.jfirst[k]);
+        for (int j = jstart; j <= h.jt_hi; ++j) {
+            const double xth = (phi_all[(size_t)k * nj + (j - h.jt_lo)] - h.theta0) / h.dtheta;
+            const int fl = (int)std::floor(xth);
+            int b0 = (int)std::ceil((double)(fl - 1 - R) / R);
+            int b1 = (int)std::floor((double)(fl + 3) / R);
+            b0 = std::max(b0, 0);
+            b1 = std::min(b1, P.nbands - 1);
+            for (int b = b0; b <= b1; ++b) {
+                int2& r = jband[(size_t)b * d.Nx + k];
+                if (r.x > r.y) r = int2{j, j};
+                else {
+                    r.x = std::min(r.x, j);
+                    r.y = std::max(r.y, j);
+                }
+            }
+        }
+        for (int b = 0; b < P.nbands; ++b) {
+            int2& r = jband[(size_t)b * d.Nx + k];
+            if (r.x <= r.y) {
+                r.x = std::max(r.x - 1, jstart);
+                r.y = std::min(r.y + 1, h.jt_hi);
+            }
+        }
+    }
+    // output columns: theta taps, scale, e^rho polynomial; band column ranges
+    const std::vector<double> q = q_grid(d);
+    const int ncol = h.l_hi - h.l_lo + 1;
+    std::vector<float4> colw(ncol);
+    std::vector<int> colm0(ncol);
+    std::vector<float> colscale(ncol);
+    std::vector<ff> E(3 * (size_t)ncol);
+    std::vector<int2> lband(P.nbands, int2{1, 0});
+    const double dtau = d.dtau > 0 ? d.dtau : T / (d.Ntau - 1);
+    const double c0 = (d.tau0 / T) * (d.tau0 / T), c1 = 2.0 * (d.tau0 / T) * (dtau / T),
+                 c2 = (dtau / T) * (dtau / T);
+    for (int lc = 0; lc < ncol; ++lc) {
+        const double qb = q[h.l_lo + lc] * X / T;
+        const double m = qb * qb;
+        const double psi = std::atan(m);
+        const double theta = h.alpha - psi;
+        const double xth = (theta - h.theta0) / h.dtheta;
+        const double fl = std::floor(xth);
+        int m0 = (int)fl - 1;
+        m0 = std::min(std::max(m0, 0), h.Ntheta - 4);
+        const double fr = xth - (m0 + 1);
+        colm0[lc] = m0;
+        colw[lc] = make_float4((float)b3(fr + 1.0), (float)b3(fr), (float)b3(fr - 1.0), (float)b3(fr - 2.0));
+        colscale[lc] = (float)(2.0 * X * std::cos(psi) / h.a);
+        const double Acoef = h.a * std::cos(psi);
+        const double Bcoef = h.a * std::cos(psi) * (0.5 * m - 0.5) + h.O1 * std::cos(theta) +
+                             h.O2 * std::sin(theta);
+        E[3 * lc + 0] = to_ff(Acoef * c0 + Bcoef);
+        E[3 * lc + 1] = to_ff(Acoef * c1);
+        E[3 * lc + 2] = to_ff(Acoef * c2);
+        const int flc = m0 + 1;
+        int b0 = (int)std::ceil((double)(flc - 1 - R) / R);
+        int b1 = (int)std::floor((double)(flc + 3) / R);
+        b0 = std::max(b0, 0);
+        b1 = std::min(b1, P.nbands - 1);
+        for (int b = b0; b <= b1; ++b) {
+            int2& r = lband[b];
+            const int l = h.l_lo + lc;
+            if (r.x > r.y) r = int2{l, l};
+            else {
+                r.x = std::min(r.x, l);
+                r.y = std::max(r.y, l);
+            }
+        }
+    }
+    // twiddles
+    const int M = h.Prho / 2;
+    std::vector<cf> twM(M), twP(M + 1), twT(h.Ptheta);
+    for (int k = 0; k < M; ++k)
+        twM[k] = {(float)std::cos(-2 * kPi * k / M), (float)std::sin(-2 * kPi * k / M)};
+    for (int k = 0; k <= M; ++k)
+        twP[k] = {(float)std::cos(-2 * kPi * k / h.Prho), (float)std::sin(-2 * kPi * k / h.Prho)};
+    for (int k = 0; k < h.Ptheta; ++k)
+        twT[k] = {(float)std::cos(-2 * kPi * k / h.Ptheta), (float)std::sin(-2 * kPi * k / h.Ptheta)};
+    std::vector<cf> K;
+    if (radon_status s = kernel_spectrum(p, h, CB, P.nkb, K)) return s;
+
+    radon_status s = RADON_OK;
+    if ((s = dev_upload(p, lam, &P.lam)) || (s = dev_upload(p, cj, &P.cj)) ||
+        (s = dev_upload(p, h.jfirst, &P.jfirst)) || (s = dev_upload(p, hk, &P.hk)) ||
+        (s = dev_upload(p, wk, &P.wk)) || (s = dev_upload(p, jband, &P.jband)) ||
+        (s = dev_upload(p, lband, &P.lband)) || (s = dev_upload(p, rowc, &P.rowc)) ||
+        (s = dev_upload(p, rows, &P.rows)) || (s = dev_upload(p, R1, &P.R1)) ||
+        (s = dev_upload(p, R2, &P.R2)) || (s = dev_upload(p, E, (const ff**)&P.E)) ||
+        (s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
+        (s = dev_upload(p, colscale, &P.colscale)) || (s = dev_upload(p, K, &P.K)) ||
+        (s = dev_upload(p, twM, &P.twM)) || (s = dev_upload(p, twP, &P.twP)) ||
+        (s = dev_upload(p, twT, &P.twT)))
+        return s;
+    void* lat = nullptr;
+    if ((s = dev_alloc(p, (size_t)h.Ntheta * h.Nrho * sizeof(float), &lat))) return s;
+    P.lat = (float*)lat;
+    return RADON_OK;
+}
+
+void destroy_plan(radon_plan_s* p) {
+    if (!p) return;
+    for (void* a : p->allocs) cudaFree(a);
+    for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    delete p;
+}
+
+cudaEvent_t pool_event(radon_plan_s* p) {
+    if (p->pool_next == p->event_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        p->event_pool.push_back(e);
+    }
+    return p->event_pool[p->pool_next++];
+}
+
+// Runs one launch, bracketed by events when profiling is on.
+template <class F>
+int timed(radon_plan_s* p, int stage, double bytes, void* stream, F&& launch) {
+    if (!p->profiling) return launch();
+    cudaEvent_t a = pool_event(p), b = pool_event(p);
+    if (!a || !b) return launch();
+    cudaEventRecord(a, (cudaStream_t)stream);
+    int e = launch();
+    cudaEventRecord(b, (cudaStream_t)stream);
+    p->recs.push_back({stage, a, b, bytes});
+    return e;
+}
+
+// Algorithmic bytes of each stage of one sub-problem.
+double bytes_spectrum(const PieceDev& P) { return 8.0 * P.Ntheta * (P.k2max + 1); }
+double bytes_lattice(const PieceDev& P) { return 4.0 * P.Ntheta * P.Nrho; }
+double bytes_samples(const PieceDev& P) { return 4.0 * P.Nx * (P.jt_hi - P.jt_lo + 1); }
+double bytes_kernel(const PieceDev& P) { return 8.0 * (P.k1max + 1) * (P.k2max + 1); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau, int Nq, double dt,
+                                        double dx, double qmin, double qmax) {
+    if (!d) return fail(RADON_ERR_INVALID_ARG, "descriptor is NULL");
+    std::memset(d, 0, sizeof(*d));
+    d->Nt = Nt;
+    d->Nx = Nx;
+    d->Ntau = Ntau;
+    d->Nq = Nq;
+    d->dt = dt;
+    d->dx = dx;
+    d->qmin = qmin;
+    d->qmax = qmax;
+    d->tau0 = 0.0;
+    d->dtau = 0.0;
+    d->sigma = 1.5;
+    d->omega_c = 0.3;
+    d->n_tsplit = 1;
+    d->tsplit[0] = 0.4;
+    d->n_qsplit = 1;
+    d->device = -1;
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_plan_create(radon_plan* out, int Nt, int Nx, int Ntau, int Nq, double dt,
+                                          double dx, double qmax) {
+    radon_desc d;
+    radon_desc_init(&d, Nt, Nx, Ntau, Nq, dt, dx, 0.0, qmax);
+    return radon_plan_create_ex(out, &d);
+}
+
+extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* din) {
+    if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (radon_status s = check_desc(din)) return s;
+    radon_plan_s* p = new (std::nothrow) radon_plan_s();
+    if (!p) return fail(RADON_ERR_OOM, "host allocation failed");
+    p->d = *din;
+    radon_desc& d = p->d;
+    if (d.dtau <= 0) d.dtau = (d.Nt - 1) * d.dt / (d.Ntau - 1);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        delete p;
+        return fail(RADON_ERR_CUDA, "no CUDA device");
+    }
+    if (d.device < 0) {
+        cudaGetDevice(&p->device);
+        d.device = p->device;
+    } else if (d.device >= ndev) {
+        delete p;
+        return fail(RADON_ERR_INVALID_ARG, "device ordinal out of range");
+    } else {
+        p->device = d.device;
+    }
+    DeviceGuard guard(p->device);
+    const int smem_max = max_smem_optin();
+    const std::vector<double> bs = accepted_splits(d);
+    const std::vector<TPiece> tps = time_pieces(d, bs);
+    p->qpieces = slowness_pieces(d);
+    std::vector<double> phi_all;
+    for (auto& lq : p->qpieces) {
+        p->qfirst.push_back((int)p->pieces.size());
+        for (auto& tp : tps) {
+            HostPiece h;
+            radon_status s = make_geometry(d, tp, lq, h, phi_all);
+            if (s == RADON_OK) s = build_piece_tables(p, h, bs, phi_all, smem_max);
+            if (s != RADON_OK) {
+                destroy_plan(p);
+                return s;
+            }
+            p->pieces.push_back(std::move(h));
+        }
+        p->qcount.push_back((int)tps.size());
+    }
+    // shared spectrum buffers and the device copy of the piece descriptors
+    size_t spec = 0;
+    for (auto& h : p->pieces) spec = std::max(spec, (size_t)h.dev.nkb * h.dev.CB * h.dev.Ntheta);
+    void* a = nullptr;
+    radon_status s = RADON_OK;
+    if ((s = dev_alloc(p, spec * sizeof(cf), &a))) { destroy_plan(p); return s; }
+    p->spec1 = (cf*)a;
+    if ((s = dev_alloc(p, spec * sizeof(cf), &a))) { destroy_plan(p); return s; }
+    p->spec2 = (cf*)a;
+    std::vector<PieceDev> devs;
+    for (auto& h : p->pieces) devs.push_back(h.dev);
+    const PieceDev* dp = nullptr;
+    if ((s = dev_upload(p, devs, &dp))) { destroy_plan(p); return s; }
+    p->dev_pieces = const_cast<PieceDev*>(dp);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        destroy_plan(p);
+        return fail(RADON_ERR_CUDA, "plan creation failed on the device");
+    }
+    *out = p;
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_plan_destroy(radon_plan p) {
+    if (!p) return RADON_OK;
+    DeviceGuard guard(p->device);
+    cudaDeviceSynchronize();
+    destroy_plan(p);
+    return RADON_OK;
+}
+
+static radon_status cuda_status(int e, const char* what) {
+    if (e == 0) return RADON_OK;
+    return fail(RADON_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString((cudaError_t)e));
+}
+
+extern "C" radon_status radon_fwd(radon_plan p, const float* f, float* g, void* stream) {
+    if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
+    if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    DeviceGuard guard(p->device);
+    for (size_t qi = 0; qi < p->qpieces.size(); ++qi) {
+        const int first = p->qfirst[qi], count = p->qcount[qi];
+        for (int t = 0; t < count; ++t) {
+            const PieceDev& P = p->pieces[first + t].dev;
+            const double bs = bytes_spectrum(P);
+            if (radon_status s = cuda_status(
+                    timed(p, 0, bytes_samples(P) + bs, stream,
+                          [&] { return launch_scatter_gather_rows(P, f, p->spec1, stream); }),
+                    "gridding"))
+                return s;
+            if (radon_status s = cuda_status(
+                    timed(p, 1, 2 * bs + bytes_kernel(P), stream,
+                          [&] { return launch_colconv(P, p->spec1, p->spec2, 0, stream); }),
+                    "convolution"))
+                return s;
+            if (radon_status s = cuda_status(
+                    timed(p, 2, bs + bytes_lattice(P), stream,
+                          [&] { return launch_rows_c2r(P, p->spec2, stream); }),
+                    "inverse row FFT"))
+                return s;
+        }
+        std::vector<PieceDev> host(count);
+        double lat = 0;
+        for (int t = 0; t < count; ++t) {
+            host[t] = p->pieces[first + t].dev;
+            lat += bytes_lattice(host[t]);
+        }
+        const double gb = 4.0 * p->d.Ntau * (p->qpieces[qi].second - p->qpieces[qi].first + 1);
+        if (radon_status s = cuda_status(
+                timed(p, 3, lat + gb, stream,
+                      [&] {
+                          return launch_gather_radon(host.data(), count, p->dev_pieces + first,
+                                                     p->qpieces[qi].first, p->qpieces[qi].second, g,
+                                                     stream);
+                      }),
+                "interpolation"))
+            return s;
+    }
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* stream) {
+    if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
+    if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    DeviceGuard guard(p->device);
+    double lat = 0;
+    for (auto& h : p->pieces) {
+        const PieceDev& P = h.dev;
+        const double bs = bytes_spectrum(P);
+        lat += bytes_lattice(P);
+        const double gb = 4.0 * p->d.Ntau * (P.l_hi - P.l_lo + 1);
+        if (radon_status s = cuda_status(
+                timed(p, 4, gb + bs, stream, [&] { return launch_scatter_radon_rows(P, g, p->spec1, stream); }),
+                "adjoint interpolation"))
+            return s;
+        if (radon_status s = cuda_status(
+                timed(p, 5, 2 * bs + bytes_kernel(P), stream,
+                      [&] { return launch_colconv(P, p->spec1, p->spec2, 1, stream); }),
+                "adjoint convolution"))
+            return s;
+        if (radon_status s = cuda_status(
+                timed(p, 6, bs + bytes_lattice(P), stream, [&] { return launch_rows_c2r(P, p->spec2, stream); }),
+                "inverse row FFT"))
+            return s;
+    }
+    return cuda_status(timed(p, 7, lat + 4.0 * p->d.Nt * p->d.Nx, stream,
+                             [&] {
+                                 return launch_gather_samples(p->dev_pieces, (int)p->pieces.size(), p->d.Nt,
+                                                              p->d.Nx, f, stream);
+                             }),
+                       "adjoint gridding");
+}
+
+extern "C" radon_status radon_plan_num_pieces(radon_plan p, int* n) {
+    if (!p || !n) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
+    *n = (int)p->pieces.size();
+    return RADON_OK;
+}
+
+static void fill_info(const HostPiece& h, radon_piece_info* info) {
+    info->jt_lo = h.jt_lo;
+    info->jt_hi = h.jt_hi;
+    info->l_lo = h.l_lo;
+    info->l_hi = h.l_hi;
+    info->alpha = h.alpha;
+    info->beta = h.beta;
+    info->a = h.a;
+    info->O1 = h.O1;
+    info->O2 = h.O2;
+    info->a_r = h.a_r;
+    info->r_max = h.r_max;
+    info->dphi_rule = h.dphi_rule;
+    info->deta_rule = h.deta_rule;
+    info->dtheta = h.dtheta;
+    info->drho = h.drho;
+    info->theta0 = h.theta0;
+    info->rho0 = h.rho0;
+    info->Ntheta = h.Ntheta;
+    info->Nrho = h.Nrho;
+    info->Ptheta = h.Ptheta;
+    info->Prho = h.Prho;
+    info->k1max = h.k1max;
+    info->k2max = h.k2max;
+    info->theta_m = h.theta_m;
+}
+
+extern "C" radon_status radon_plan_piece_info(radon_plan p, int piece, radon_piece_info* info) {
+    if (!p || !info) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
+    if (piece < 0 || piece >= (int)p->pieces.size()) return fail(RADON_ERR_INVALID_ARG, "piece out of range");
+    fill_info(p->pieces[piece], info);
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_geometry(const radon_desc* din, int* npieces, radon_piece_info* infos,
+                                       int max_infos) {
+    if (!npieces) return fail(RADON_ERR_INVALID_ARG, "npieces is NULL");
+    if (radon_status s = check_desc(din)) return s;
+    radon_desc d = *din;
+    if (d.dtau <= 0) d.dtau = (d.Nt - 1) * d.dt / (d.Ntau - 1);
+    const std::vector<double> bs = accepted_splits(d);
+    const std::vector<TPiece> tps = time_pieces(d, bs);
+    std::vector<double> phi_all;
+    int n = 0;
+    for (auto& lq : slowness_pieces(d))
+        for (auto& tp : tps) {
+            HostPiece h;
+            if (radon_status s = make_geometry(d, tp, lq, h, phi_all)) return s;
+            if (infos && n < max_infos) fill_info(h, infos + n);
+            ++n;
+        }
+    *npieces = n;
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_plan_desc(radon_plan p, radon_desc* d) {
+    if (!p || !d) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
+    *d = p->d;
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_plan_device_bytes(radon_plan p, size_t* bytes) {
+    if (!p || !bytes) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
+    *bytes = p->bytes;
+    return RADON_OK;
+}
+
+static radon_status check_direct(const void* a, const void* b, int Nt, int Nx, int Ntau, int Nq, double dt,
+                                 double dx, double tau0, double dtau) {
+    if (!a || !b) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    if (Nt < 2 || Nx < 2 || Ntau < 1 || Nq < 1) return fail(RADON_ERR_INVALID_ARG, "bad sizes");
+    if (!(dt > 0) || !(dx > 0) || !(dtau > 0) || !(tau0 >= 0))
+        return fail(RADON_ERR_INVALID_ARG, "need dt, dx, dtau > 0 and tau0 >= 0");
+    if (Nq > 65535 || Nx > 65535) return fail(RADON_ERR_UNSUPPORTED, "Nq and Nx must be below 65536");
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_direct_fwd(const float* f, float* g, int Nt, int Nx, int Ntau, int Nq,
+                                         double dt, double dx, double tau0, double dtau, double qmin,
+                                         double dq, void* stream) {
+    if (radon_status s = check_direct(f, g, Nt, Nx, Ntau, Nq, dt, dx, tau0, dtau)) return s;
+    return cuda_status(launch_direct_fwd(f, g, Nt, Nx, Ntau, Nq, dt, dx, tau0, dtau, qmin, dq, stream),
+                       "direct summation");
+}
+
+extern "C" radon_status radon_direct_adj(const float* g, float* f, int Nt, int Nx, int Ntau, int Nq,
+                                         double dt, double dx, double tau0, double dtau, double qmin,
+                                         double dq, void* stream) {
+    if (radon_status s = check_direct(g, f, Nt, Nx, Ntau, Nq, dt, dx, tau0, dtau)) return s;
+    return cuda_status(launch_direct_adj(g, f, Nt, Nx, Ntau, Nq, dt, dx, tau0, dtau, qmin, dq, stream),
+                       "direct summation adjoint");
+}
+
+extern "C" radon_status radon_plan_set_profiling(radon_plan p, int enable) {
+    if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
+    p->profiling = enable != 0;
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_plan_profile_read(radon_plan p, double ms[RADON_NSTAGES],
+                                                long long launches[RADON_NSTAGES],
+                                                double bytes[RADON_NSTAGES]) {
+    if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
+    DeviceGuard guard(p->device);
+    double t[RADON_NSTAGES] = {0}, b[RADON_NSTAGES] = {0};
+    long long n[RADON_NSTAGES] = {0};
+    radon_status st = RADON_OK;
+    for (auto& r : p->recs) {
+        float v = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&v, r.a, r.b) != cudaSuccess) {
+            st = fail(RADON_ERR_CUDA, "reading a profiling event failed");
+            continue;
+        }
+        t[r.stage] += v;
+        b[r.stage] += r.bytes;
+        n[r.stage] += 1;
+    }
+    p->recs.clear();
+    p->pool_next = 0;
+    for (int i = 0; i < RADON_NSTAGES; ++i) {
+        if (ms) ms[i] = t[i];
+        if (launches) launches[i] = n[i];
+        if (bytes) bytes[i] = b[i];
+    }
+    return st;
+}
+
+extern "C" const char* radon_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* radon_version(void) { return "hradon 0.1 (sm_103a)"; }

@@ -1,0 +1,191 @@
+// Host check of the arithmetic the CUDA kernels use (csrc/hostdev.h):
+// Stockham FFT stages, the real-FFT packing pair, and the float-float lattice
+// positions. Compiled with g++ by tests/test_hostdev.py; prints "name value"
+// lines (errors) that the test compares with thresholds.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <random>
+#include <vector>
+
+#include "hostdev.h"
+
+using namespace hr;
+typedef std::complex<double> cd;
+
+static std::vector<cf> twiddles(int n) {
+    std::vector<cf> t(n);
+    for (int k = 0; k < n; ++k) t[k] = {(float)std::cos(-2 * M_PI * k / n), (float)std::sin(-2 * M_PI * k / n)};
+    return t;
+}
+
+// The device driver's stage loop, run sequentially.
+static std::vector<cf> fft_emul(std::vector<cf> a, int dir) {
+    const int n = (int)a.size();
+    int rad[32];
+    const int nst = fft_radices(n, rad);
+    std::vector<cf> b(n), tw = twiddles(n);
+    int Ns = 1;
+    for (int s = 0; s < nst; ++s) {
+        const int R = rad[s];
+        for (int j = 0; j < n / R; ++j) {
+            if (R == 4) stockham_butterfly<4>(a.data(), b.data(), n, Ns, j, tw.data(), dir);
+            else if (R == 2) stockham_butterfly<2>(a.data(), b.data(), n, Ns, j, tw.data(), dir);
+            else stockham_butterfly<3>(a.data(), b.data(), n, Ns, j, tw.data(), dir);
+        }
+        std::swap(a, b);
+        Ns *= R;
+    }
+    return a;
+}
+
+static double fft_error(int n, int dir, std::mt19937& rng) {
+    std::normal_distribution<double> N(0, 1);
+    std::vector<cf> x(n);
+    std::vector<cd> xd(n);
+    for (int i = 0; i < n; ++i) {
+        x[i] = {(float)N(rng), (float)N(rng)};
+        xd[i] = cd(x[i].x, x[i].y);
+    }
+    std::vector<cf> y = fft_emul(x, dir);
+    double num = 0, den = 0;
+    for (int k = 0; k < n; ++k) {
+        cd acc = 0;
+        for (int i = 0; i < n; ++i) acc += xd[i] * std::polar(1.0, dir * 2 * M_PI * (double)((long)k * i % n) / n);
+        num += std::norm(acc - cd(y[k].x, y[k].y));
+        den += std::norm(acc);
+    }
+    return std::sqrt(num / den);
+}
+
+// Real FFT through the packed complex FFT: returns max relative error of
+// X_mine / X_true - 2 (the kernels omit the factors 1/2).
+static double rfft_error(int P, std::mt19937& rng) {
+    std::normal_distribution<double> N(0, 1);
+    const int M = P / 2;
+    std::vector<double> x(P);
+    for (auto& v : x) v = N(rng);
+    std::vector<cf> z(M);
+    for (int n = 0; n < M; ++n) z[n] = {(float)x[2 * n], (float)x[2 * n + 1]};
+    std::vector<cf> Z = fft_emul(z, -1);
+    std::vector<cf> twP(M + 1);
+    for (int k = 0; k <= M; ++k) twP[k] = {(float)std::cos(-2 * M_PI * k / P), (float)std::sin(-2 * M_PI * k / P)};
+    double num = 0, den = 0;
+    for (int k = 0; k <= M / 2; ++k) {
+        cd acc = 0;
+        for (int n = 0; n < P; ++n) acc += x[n] * std::polar(1.0, -2 * M_PI * (double)((long)k * n % P) / P);
+        cf X = r2c_post(Z.data(), M, k, twP.data());
+        num += std::norm(cd(X.x, X.y) - 2.0 * acc);
+        den += std::norm(2.0 * acc);
+    }
+    return std::sqrt(num / den);
+}
+
+// Inverse: half spectrum with bins 0..kmax (X0 real) -> x; returns the error
+// of x_mine against P * irfft(X) (normalised inverse times P).
+static double irfft_error(int P, int kmax, std::mt19937& rng) {
+    std::normal_distribution<double> N(0, 1);
+    const int M = P / 2;
+    std::vector<cd> Xd(M + 1, 0.0);
+    for (int k = 0; k <= kmax; ++k) Xd[k] = cd(N(rng), k ? N(rng) : 0.0);
+    std::vector<cf> X(M);
+    for (int k = 0; k < M; ++k) X[k] = {(float)Xd[k].real(), (float)Xd[k].imag()};
+    std::vector<cf> twP(M + 1);
+    for (int k = 0; k <= M; ++k) twP[k] = {(float)std::cos(-2 * M_PI * k / P), (float)std::sin(-2 * M_PI * k / P)};
+    X[0] = c2r_pre_dc(X[0]);
+    for (int k = 1; k <= M / 2; ++k) c2r_pre_pair(X.data(), M, k, twP.data());
+    std::vector<cf> z = fft_emul(X, +1);
+    double num = 0, den = 0;
+    for (int n = 0; n < P; ++n) {
+        double acc = Xd[0].real();
+        for (int k = 1; k < M; ++k) acc += 2.0 * (Xd[k] * std::polar(1.0, 2 * M_PI * (double)((long)k * n % P) / P)).real();
+        const double mine = (n & 1) ? z[n >> 1].y : z[n >> 1].x;
+        num += (mine - acc) * (mine - acc);
+        den += acc * acc;
+    }
+    return std::sqrt(num / den);
+}
+
+static ff to_ff(double v) {
+    float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+}
+
+// Lattice positions of random points near the unit arc in float-float,
+// against FP64: max error in cells for spacing 1e-4.
+static void position_errors(std::mt19937& rng, double& eth, double& erh, double& erh_e) {
+    std::uniform_real_distribution<double> U(0, 1);
+    const double dcell = 1e-4;
+    eth = erh = erh_e = 0;
+    for (int it = 0; it < 200000; ++it) {
+        const double alpha = 0.2 + 0.4 * U(rng);
+        const double lam = 0.3 + 0.6 * U(rng), h = -0.3 + 0.5 * U(rng);
+        // reference row near the true angle
+        const double phi = alpha + std::atan2(h, lam);
+        const double theta0 = -0.3;
+        const int mr = (int)std::floor((phi - theta0) / dcell + 0.5) + (int)(7 * U(rng)) - 3;
+        const double g = theta0 + mr * dcell - alpha;
+        const float d = angle_from(to_ff(lam), to_ff(h), to_ff(std::cos(g)), to_ff(std::sin(g)));
+        const double xth = mr + d / dcell;
+        eth = std::max(eth, std::fabs(xth - (phi - theta0) / dcell));
+        // radius: eta = 0.5 log(lam^2 + h^2)
+        const ff u2 = radius2(to_ff(lam), to_ff(h));
+        const double eta = 0.5 * std::log(lam * lam + h * h);
+        const double rho0 = -0.9;
+        const int n = (int)std::floor((eta - rho0) / dcell + 0.5) + (int)(3 * U(rng)) - 1;
+        const ff Rn = to_ff(std::exp(2.0 * (rho0 + n * dcell)));
+        const float de = 0.5f * log1pf(ff_diff(u2, Rn) / Rn.hi);
+        erh = std::max(erh, std::fabs(n + de / dcell - (eta - rho0) / dcell));
+        // e^rho of an output: E0 + E1 i + E2 i^2
+        const double E0 = 0.4 + 0.2 * U(rng), E1 = 1e-5 * U(rng), E2 = 3e-7 * U(rng);
+        const int i = (int)(2048 * U(rng));
+        ff t = ff_mul_f(to_ff(E2), (float)i);
+        t = ff_add(t, to_ff(E1));
+        t = ff_mul_f(t, (float)i);
+        const ff e = ff_add(t, to_ff(E0));
+        const double ed = E0 + E1 * i + E2 * (double)i * i;
+        const double rho = std::log(ed);
+        const int n2 = (int)std::floor((rho - rho0) / dcell + 0.5);
+        const ff R1 = to_ff(std::exp(rho0 + n2 * dcell));
+        const float dr = log1pf(ff_diff(e, R1) / R1.hi);
+        erh_e = std::max(erh_e, std::fabs(n2 + dr / dcell - (rho - rho0) / dcell));
+    }
+}
+
+static double b3_error() {
+    double e = 0;
+    for (int i = 0; i <= 1000; ++i) {
+        const float f = i / 1000.0f;
+        float w[4];
+        b3_weights(f, w);
+        auto B3 = [](double x) {
+            x = std::fabs(x);
+            return x < 1 ? 2.0 / 3 - x * x + 0.5 * x * x * x : (x < 2 ? (2 - x) * (2 - x) * (2 - x) / 6 : 0.0);
+        };
+        for (int a = 0; a < 4; ++a) e = std::max(e, std::fabs(w[a] - B3(f + 1 - a)));
+        e = std::max(e, std::fabs((double)w[0] + w[1] + w[2] + w[3] - 1.0));
+    }
+    return e;
+}
+
+int main() {
+    std::mt19937 rng(1604);
+    double e = 0;
+    for (int n : {2, 3, 4, 6, 8, 12, 16, 24, 64, 96, 384, 512, 1536, 2048})
+        e = std::max(e, std::max(fft_error(n, -1, rng), fft_error(n, +1, rng)));
+    std::printf("fft_rel_l2 %.3e\n", e);
+    e = 0;
+    for (int P : {8, 12, 64, 96, 768, 1024}) e = std::max(e, rfft_error(P, rng));
+    std::printf("rfft_rel_l2 %.3e\n", e);
+    e = 0;
+    for (int P : {8, 12, 64, 96, 768, 1024}) e = std::max(e, irfft_error(P, P / 2 - 1, rng));
+    for (int P : {64, 768}) e = std::max(e, irfft_error(P, P / 5, rng));
+    std::printf("irfft_rel_l2 %.3e\n", e);
+    double eth, erh, erh_e;
+    position_errors(rng, eth, erh, erh_e);
+    std::printf("theta_cells %.3e\n", eth);
+    std::printf("rho_cells %.3e\n", erh);
+    std::printf("rho_out_cells %.3e\n", erh_e);
+    std::printf("b3_weights %.3e\n", b3_error());
+    return 0;
+}

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA log-polar path (through the C ABI) against the oracle.
+
+* against the FP64 log-polar oracle on the same lattices: relative L2 <= 1e-5
+  (forward and adjoint), lattice geometry identical;
+* against the FP64 direct summation over hyperbolas: relative L2 <= 1e-2 on
+  band-limited data (Section 5), also at 2048x2048 on sampled outputs;
+* inner-product test (Eq. (16)) to the paper's FP32 level, 1e-5;
+* the GPU direct-summation comparator against the oracle's direct sum.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import direct as odirect
+from oracle.logpolar import Desc, LogPolar
+
+pytestmark = pytest.mark.gpu
+
+PARITY_TOL = 1e-5    # FP32 CUDA path vs FP64 oracle on the same lattices
+METHOD_TOL = 1e-2    # log-polar vs direct summation, band-limited data
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def hr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_07651_gb300 as hr
+    return hr
+
+
+def _pair(hr, geo, sigma=1.5, omega_c=0.3, tsplit=(0.4,), nq=1, tau0=0.0, dtau=0.0):
+    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+                   tau0=tau0, dtau=dtau, sigma=sigma, omega_c=omega_c, tsplit=tsplit, n_qsplit=nq)
+    desc = Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+                tau0=tau0, dtau=dtau, sigma=sigma, omega_c=omega_c, tsplits=tuple(tsplit),
+                n_qsplit=nq)
+    return plan, desc
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+CASES = {
+    # name: (geometry, method kwargs)
+    "small_gather_256x64": (synth.Geometry(256, 64, 256, 64, 0.004, 1.6 / 63, 0.2, 0.7), {}),
+    "square_256": (synth.Geometry(256, 256, 256, 256, 2.0 / 255, 2.0 / 255, 0.2, 0.7), {}),
+    "ragged_333x150": (synth.Geometry(333, 150, 301, 77, 0.006, 0.013, 0.15, 0.65),
+                       dict(tsplit=(0.3, 0.6), nq=2)),
+    "qmin0_no_split": (synth.Geometry(200, 90, 180, 50, 0.005, 0.02, 0.0, 0.6), dict(tsplit=())),
+    "sigma2_wc025": (synth.Geometry(300, 120, 300, 120, 0.006, 0.015, 0.2, 0.7),
+                     dict(sigma=2.0, omega_c=0.25, tsplit=(0.3, 0.6))),
+    "tau0_offset": (synth.Geometry(256, 96, 200, 64, 0.004, 0.02, 0.2, 0.7),
+                    dict(tau0=0.2, dtau=0.004)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_geometry_matches_oracle(hr, name):
+    geo, kw = CASES[name]
+    plan, desc = _pair(hr, geo, **kw)
+    lp = LogPolar(desc)
+    gpu = {(p["jt_lo"], p["l_lo"]): p for p in plan.pieces()}
+    assert len(gpu) == len(lp.parts)
+    for part in lp.parts:
+        p = gpu[(part.jt_lo, part.l_lo)]
+        for k in ("jt_hi", "l_hi", "Ntheta", "Nrho", "k1max", "k2max"):
+            assert p[k] == getattr(part, k), k
+        assert p["Ptheta"] == part.P_theta and p["Prho"] == part.P_rho
+        for k in ("alpha", "beta", "a", "O1", "O2", "a_r", "r_max", "dtheta", "drho", "theta_m"):
+            assert abs(p[k] - getattr(part, k)) <= 1e-12 * max(1.0, abs(getattr(part, k))), k
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_forward_and_adjoint_match_logpolar_oracle(hr, name):
+    geo, kw = CASES[name]
+    plan, desc = _pair(hr, geo, **kw)
+    lp = LogPolar(desc)
+    f = synth.band_limited_gather(geo, 31, n_events=6, nu=10.0)
+    g_ref = lp.forward(f)
+    g = plan.forward(_cuda(f)).cpu().numpy()
+    assert _rel(g, g_ref) < PARITY_TOL
+    gg = synth.random_radon_image(geo, 32)
+    f_ref = lp.adjoint(gg)
+    fa = plan.adjoint(_cuda(gg)).cpu().numpy()
+    assert _rel(fa, f_ref) < PARITY_TOL
+
+
+def test_dot_test_fp32(hr):
+    """Eq. (16) in FP32: the paper reports O(1e-5)."""
+    geo = synth.Geometry(512, 256, 512, 256, 2.0 / 511, 2.0 / 255, 0.2, 0.7)
+    plan, _ = _pair(hr, geo, tsplit=(0.3, 0.6), nq=2)
+    rng = np.random.default_rng(9)
+    f = _cuda(rng.standard_normal((geo.Nx, geo.Nt)))
+    g = _cuda(rng.standard_normal((geo.Nq, geo.Ntau)))
+    lhs = torch.sum(plan.forward(f).double() * g.double()).item()
+    rhs = torch.sum(f.double() * plan.adjoint(g).double()).item()
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def test_matches_direct_sum_band_limited_512(hr, oracle_direct):
+    geo, f = synth.sweep_gather(512, noise=0.0, nu_range=(8.0, 12.0))
+    plan, _ = _pair(hr, geo)
+    g_or = oracle_direct.fwd(f, geo.dt, geo.dx, geo.tau(), geo.q())
+    g = plan.forward(_cuda(f)).cpu().numpy()
+    assert _rel(g, g_or) < METHOD_TOL
+
+
+def test_full_size_2048_sampled_against_direct_sum(hr, oracle_direct):
+    """The benchmark workload (2048^2 gather, 32 Ricker events 20-40 Hz, 5 %
+    noise, default method parameters): forward on 4096 sampled outputs and
+    adjoint on 4096 sampled gather points against the FP64 direct sum."""
+    geo, f = synth.sweep_gather(2048, noise=0.05)
+    plan, _ = _pair(hr, geo)
+    rng = np.random.default_rng(2048)
+    ii = rng.integers(0, geo.Ntau, 4096)
+    li = rng.integers(0, geo.Nq, 4096)
+    g = plan.forward(_cuda(f)).cpu().numpy()
+    ref = odirect.fwd_points(f, geo.dt, geo.dx, geo.tau(), geo.q(), ii, li)
+    assert _rel(g[li, ii], ref) < METHOD_TOL
+    # adjoint of a smooth image concentrated like a Radon image of events
+    gg = synth.random_radon_image(geo, 77)
+    fa = plan.adjoint(_cuda(gg)).cpu().numpy()
+    jj = rng.integers(0, geo.Nt, 4096)
+    kk = rng.integers(0, geo.Nx, 4096)
+    refa = odirect.adj_points(gg, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q(), jj, kk)
+    assert _rel(fa[kk, jj], refa) < METHOD_TOL
+
+
+def test_full_size_2048_against_logpolar_oracle(hr):
+    """Same workload, every output, against the FP64 log-polar oracle."""
+    geo, f = synth.sweep_gather(2048, noise=0.05)
+    plan, desc = _pair(hr, geo)
+    g_ref = LogPolar(desc).forward(f)
+    g = plan.forward(_cuda(f)).cpu().numpy()
+    assert _rel(g, g_ref) < PARITY_TOL
+
+
+def test_direct_sum_kernel_matches_oracle(hr, oracle_direct):
+    geo, f = synth.single_gather(1)
+    g = hr.direct_forward(_cuda(f), geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax).cpu().numpy()
+    g_or = oracle_direct.fwd(f, geo.dt, geo.dx, geo.tau(), geo.q())
+    assert _rel(g, g_or) < 1e-4
+    gg = synth.random_radon_image(geo, 4)
+    fa = hr.direct_adjoint(_cuda(gg), geo.Nt, geo.Nx, geo.dt, geo.dx, geo.qmin, geo.qmax).cpu().numpy()
+    f_or = oracle_direct.adj(gg, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q())
+    assert _rel(fa, f_or) < 1e-4
+
+
+def test_autograd_backward_is_adjoint_and_fd(hr):
+    geo = synth.Geometry(128, 64, 128, 48, 0.008, 0.03, 0.2, 0.7)
+    plan, _ = _pair(hr, geo)
+    f = _cuda(synth.band_limited_gather(geo, 5)).requires_grad_(True)
+    w = _cuda(synth.random_radon_image(geo, 6))
+    loss = torch.sum(hr.radon(f, plan) * w)
+    loss.backward()
+    np.testing.assert_allclose(f.grad.cpu().numpy(), plan.adjoint(w).cpu().numpy(), rtol=0, atol=1e-6)
+    # finite difference along a random direction (the operator is linear, so
+    # the FD quotient is exact up to FP32 rounding)
+    v = _cuda(np.random.default_rng(1).standard_normal((geo.Nx, geo.Nt)))
+    eps = 1e-2
+    with torch.no_grad():
+        lp = torch.sum(plan.forward(f + eps * v).double() * w.double())
+        lm = torch.sum(plan.forward(f - eps * v).double() * w.double())
+    fd = ((lp - lm) / (2 * eps)).item()
+    an = torch.sum(f.grad.double() * v.double()).item()
+    assert abs(fd - an) / abs(an) < 1e-3
+
+
+def test_errors_are_reported_not_fatal(hr):
+    geo = synth.Geometry(64, 32, 64, 16, 0.01, 0.05, 0.2, 0.7)
+    plan, _ = _pair(hr, geo)
+    with pytest.raises(ValueError):
+        plan.forward(torch.zeros((geo.Nx, geo.Nt + 1), device="cuda"))
+    from paper_1604_07651_gb300 import _lib
+    L = _lib.load()
+    assert L.radon_fwd(plan._handle, None, None, None) == 1
+    with pytest.raises(hr.RadonError):
+        hr.Plan(64, 32, 64, 16, 0.01, 0.05, 0.5, 0.2)
+    # the context is still usable afterwards
+    out = plan.forward(torch.zeros((geo.Nx, geo.Nt), device="cuda"))
+    assert float(out.abs().max()) == 0.0
+
+
+def test_edge_cases(hr, oracle_direct):
+    """Smallest gathers, a single slowness column, zero input."""
+    geo = synth.Geometry(8, 4, 8, 3, 0.1, 0.1, 0.2, 0.7)
+    plan, desc = _pair(hr, geo, tsplit=())
+    f = np.random.default_rng(3).standard_normal((geo.Nx, geo.Nt))
+    g_ref = LogPolar(desc).forward(f)
+    assert _rel(plan.forward(_cuda(f)).cpu().numpy(), g_ref) < PARITY_TOL
+    geo1 = synth.Geometry(64, 32, 64, 1, 0.01, 0.03, 0.4, 0.4)
+    plan1, desc1 = _pair(hr, geo1, tsplit=())
+    f1 = synth.band_limited_gather(geo1, 8)
+    assert _rel(plan1.forward(_cuda(f1)).cpu().numpy(), LogPolar(desc1).forward(f1)) < PARITY_TOL
+    z = plan1.forward(torch.zeros((geo1.Nx, geo1.Nt), device="cuda"))
+    assert float(z.abs().max()) == 0.0

@@ -1,0 +1,43 @@
+"""CPU checks of the arithmetic inside the CUDA kernels (csrc/hostdev.h),
+compiled for the host with g++: FFT stages against a direct DFT, the
+real-FFT packing against its definition, float-float lattice positions
+against FP64, and the cubic B-spline tap weights."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def results(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    exe = str(tmp_path_factory.mktemp("hd") / "hostdev_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off",
+                    "-I", os.path.join(ROOT, "paper_1604_07651_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "hostdev_check.cpp"), "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    return {k: float(v) for k, v in (line.split() for line in out.strip().splitlines())}
+
+
+def test_stockham_fft(results):
+    assert results["fft_rel_l2"] < 5e-7
+
+
+def test_real_fft_packing(results):
+    assert results["rfft_rel_l2"] < 5e-7
+    assert results["irfft_rel_l2"] < 5e-7
+
+
+def test_float_float_positions(results):
+    # lattice positions to well below 1e-5 cells (FP32 alone gives ~1e-4)
+    assert results["theta_cells"] < 3e-6
+    assert results["rho_cells"] < 3e-6
+    assert results["rho_out_cells"] < 3e-6
+
+
+def test_b3_weights(results):
+    assert results["b3_weights"] < 1e-6
