@@ -101,6 +101,22 @@ def random_radon_image(geo: Geometry, tag: int) -> np.ndarray:
     return g
 
 
+def smooth_radon_image(geo: Geometry, tag: int, n_blobs: int = 24,
+                       width_samples: float = 6.0) -> np.ndarray:
+    """Band-limited Radon-domain image: Gaussian blobs of about
+    ``width_samples`` samples in tau and q at random positions and signs."""
+    rng = rng_for(tag)
+    i = np.arange(geo.Ntau)[None, :]
+    l = np.arange(geo.Nq)[:, None]
+    sc = max(1.0, geo.Ntau / 256.0)
+    g = np.zeros((geo.Nq, geo.Ntau))
+    for _ in range(n_blobs):
+        ci, cl = rng.uniform(0.05, 0.95) * geo.Ntau, rng.uniform(0.0, 1.0) * geo.Nq
+        wi, wl = width_samples * sc, width_samples * max(1.0, geo.Nq / 256.0)
+        g += rng.standard_normal() * np.exp(-((i - ci) / wi) ** 2 - ((l - cl) / wl) ** 2)
+    return g
+
+
 def single_gather(tag: int = 1, nu: float = 25.0) -> tuple[Geometry, np.ndarray]:
     """Small gather: Nt=256 (dt=4 ms), Nx=64 offsets on [0,1.6] km,
     Ntau=256, Nq=64 on q in [0.2,0.7] s/km, 8 Ricker events,

@@ -125,8 +125,8 @@ def test_full_size_2048_sampled_against_direct_sum(hr, oracle_direct):
     g = plan.forward(_cuda(f)).cpu().numpy()
     ref = odirect.fwd_points(f, geo.dt, geo.dx, geo.tau(), geo.q(), ii, li)
     assert _rel(g[li, ii], ref) < METHOD_TOL
-    # adjoint of a smooth image concentrated like a Radon image of events
-    gg = synth.random_radon_image(geo, 77)
+    # adjoint of a band-limited Radon image (Gaussian blobs in tau and q)
+    gg = synth.smooth_radon_image(geo, 77)
     fa = plan.adjoint(_cuda(gg)).cpu().numpy()
     jj = rng.integers(0, geo.Nt, 4096)
     kk = rng.integers(0, geo.Nx, 4096)
