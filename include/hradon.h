@@ -195,6 +195,30 @@ radon_status radon_plan_profile_read(radon_plan p, double ms[RADON_NSTAGES],
                                      long long launches[RADON_NSTAGES],
                                      double bytes[RADON_NSTAGES]);
 
+/*
+ * Forward transform that allocates nothing, for callers that cannot call
+ * cudaMalloc when they run (a host framework that has reserved the whole
+ * device for its own pool, deployments with a fixed device footprint, loops
+ * that cannot take the device-wide synchronisation cudaMalloc/cudaFree can
+ * cause). The paper has no counterpart; this is a deployment variant of
+ * radon_fwd with the same arguments and the same result (up to FP32
+ * rounding order).
+ *
+ * Its work memory (spectra, lattices, piece descriptors) is a static device
+ * array of RADON_NOALLOC_MAX_BYTES that every GPU loading this library holds
+ * until the process exits; the plan's own work buffers are not used. Plans
+ * whose work memory exceeds it (2048^2 gathers with default parameters need
+ * about 50 MB) or that have more than 32 pieces are rejected with
+ * RADON_ERR_UNSUPPORTED and a message giving the bytes needed. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls on a device share the one array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and give wrong results; serialise them.
+ */
+#define RADON_NOALLOC_MAX_BYTES (32u << 20)
+radon_status radon_fwd_noalloc(radon_plan p, const float* f, float* g, void* stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* radon_last_error(void);
 

@@ -54,6 +54,7 @@ SIGNATURES = {
     "radon_plan_set_profiling": (_c_int, [_vp, _c_int]),
     "radon_plan_profile_read": (_c_int, [_vp, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(_c_double)]),
+    "radon_fwd_noalloc": (_c_int, [_vp, _vp, _vp, _vp]),
     "radon_last_error": (ctypes.c_char_p, []),
     "radon_version": (ctypes.c_char_p, []),
 }

@@ -1,7 +1,8 @@
 """Builds the in-tree shared library ``libhradon.so`` for sm_103a.
 
-Two translation units, compiled in parallel: ``csrc/kernels.cu`` with nvcc
-(``-gencode arch=compute_103a,code=sm_103a``) and ``csrc/plan.cpp`` with the
+Three translation units, compiled in parallel: ``csrc/kernels.cu`` and
+``csrc/noalloc.cu`` with nvcc (``-gencode arch=compute_103a,code=sm_103a``)
+and ``csrc/plan.cpp`` with the
 host compiler (``-ffp-contract=off`` keeps the FP64 geometry identical on
 x86-64 and aarch64 hosts). No torch, no cmake.
 """
@@ -51,11 +52,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(bdir, exist_ok=True)
     inc = ["-I", CSRC, "-I", INCLUDE, "-I", os.path.join(cuda, "include")]
     ko = os.path.join(bdir, "kernels.o")
+    no = os.path.join(bdir, "noalloc.o")
     po = os.path.join(bdir, "plan.o")
     kcmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
             "-Xcompiler", "-ffp-contract=off", *inc, "-c", os.path.join(CSRC, "kernels.cu"), "-o", ko]
     if ptxas_info:
         kcmd.insert(1, "-Xptxas=-v")
+    ncmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *inc, "-c",
+            os.path.join(CSRC, "noalloc.cu"), "-o", no]
     pcmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", *inc, "-c",
             os.path.join(CSRC, "plan.cpp"), "-o", po]
 
@@ -66,10 +70,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         if verbose or ptxas_info:
             sys.stderr.write(r.stdout + r.stderr)
 
-    with ThreadPoolExecutor(2) as ex:
-        list(ex.map(run, [kcmd, pcmd]))
+    with ThreadPoolExecutor(3) as ex:
+        list(ex.map(run, [kcmd, ncmd, pcmd]))
     tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc, *ARCH, "-shared", ko, po, "-o", tmp, "-L", os.path.join(cuda, "lib64"), "-lcudart"])
+    run([nvcc, *ARCH, "-shared", ko, no, po, "-o", tmp, "-L", os.path.join(cuda, "lib64"), "-lcudart"])
     os.replace(tmp, LIB)
     return LIB
 

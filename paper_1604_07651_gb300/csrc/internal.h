@@ -7,6 +7,8 @@
 
 #include "hostdev.h"
 
+struct radon_plan_s;  // defined in plan.cpp
+
 namespace hr {
 
 struct FftPlan {            // radix schedule of one FFT length
@@ -75,6 +77,15 @@ int launch_direct_fwd(const float* f, float* g, int Nt, int Nx, int Ntau, int Nq
 int launch_direct_adj(const float* g, float* f, int Nt, int Nx, int Ntau, int Nq, double dt,
                       double dx, double tau0, double dtau, double qmin, double dq, void* stream);
 size_t scatter_smem_bytes(const PieceDev& P);
+
+// Forward transform of a plan with every work buffer carved out of the
+// caller-given device area `work` (256-byte aligned, `bytes` long) instead of
+// the plan's own buffers; allocates nothing (plan.cpp). Return radon_status.
+int set_error(int status, const char* msg);   // records the thread's last error, returns status
+int plan_device(const radon_plan_s* p);
+int plan_forward_work_bytes(const radon_plan_s* p, size_t* bytes);
+int plan_forward_in_work(radon_plan_s* p, const float* f, float* g, void* work, size_t bytes,
+                         void* stream);
 size_t colconv_smem_bytes(const PieceDev& P);
 int max_smem_optin();
 

@@ -1037,3 +1037,89 @@ extern "C" radon_status radon_plan_profile_read(radon_plan p, double ms[RADON_NS
 extern "C" const char* radon_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char* radon_version(void) { return "hradon 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Forward transform on caller-given work memory (used by radon_fwd_noalloc in
+// noalloc.cu). Layout of the area: the device copies of the piece
+// descriptors, the two spectrum buffers, then one lattice per piece, each
+// 256-byte aligned. Every byte the kernels read there is written earlier in
+// the same call, so nothing has to be cleared.
+// ---------------------------------------------------------------------------
+namespace hr {
+
+namespace {
+const int kWorkMaxPieces = 32;
+size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t spec_elems(const radon_plan_s* p) {
+    size_t spec = 0;
+    for (auto& h : p->pieces) spec = std::max(spec, (size_t)h.dev.nkb * h.dev.CB * h.dev.Ntheta);
+    return spec;
+}
+}  // namespace
+
+int set_error(int status, const char* msg) { return fail((radon_status)status, msg); }
+
+int plan_device(const radon_plan_s* p) { return p->device; }
+
+int plan_forward_work_bytes(const radon_plan_s* p, size_t* bytes) {
+    if (!p || !bytes) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
+    size_t b = round256(p->pieces.size() * sizeof(PieceDev));
+    b += 2 * round256(spec_elems(p) * sizeof(cf));
+    for (auto& h : p->pieces) b += round256((size_t)h.dev.Ntheta * h.dev.Nrho * sizeof(float));
+    *bytes = b;
+    return RADON_OK;
+}
+
+int plan_forward_in_work(radon_plan_s* p, const float* f, float* g, void* work, size_t bytes,
+                         void* stream) {
+    if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
+    if (!f || !g || !work) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    const int np = (int)p->pieces.size();
+    if (np > kWorkMaxPieces)
+        return fail(RADON_ERR_UNSUPPORTED, "the static-work forward handles plans of at most 32 pieces");
+    size_t need = 0;
+    plan_forward_work_bytes(p, &need);
+    if (need > bytes)
+        return fail(RADON_ERR_UNSUPPORTED,
+                    "plan needs " + std::to_string(need) + " bytes of work memory, the area holds " +
+                        std::to_string(bytes));
+    char* base = (char*)work;
+    PieceDev* dpieces = (PieceDev*)base;
+    size_t off = round256(np * sizeof(PieceDev));
+    cf* s1 = (cf*)(base + off);
+    off += round256(spec_elems(p) * sizeof(cf));
+    cf* s2 = (cf*)(base + off);
+    off += round256(spec_elems(p) * sizeof(cf));
+    PieceDev local[kWorkMaxPieces];
+    for (int i = 0; i < np; ++i) {
+        local[i] = p->pieces[i].dev;
+        local[i].lat = (float*)(base + off);
+        off += round256((size_t)local[i].Ntheta * local[i].Nrho * sizeof(float));
+    }
+    DeviceGuard guard(p->device);
+    // pageable source: the copy is staged before the call returns
+    if (cudaMemcpyAsync(dpieces, local, np * sizeof(PieceDev), cudaMemcpyHostToDevice,
+                        (cudaStream_t)stream) != cudaSuccess)
+        return fail(RADON_ERR_CUDA, "copy of the piece descriptors failed");
+    for (size_t qi = 0; qi < p->qpieces.size(); ++qi) {
+        const int first = p->qfirst[qi], count = p->qcount[qi];
+        for (int t = 0; t < count; ++t) {
+            const PieceDev& P = local[first + t];
+            if (radon_status s = cuda_status(launch_scatter_gather_rows(P, f, s1, stream), "gridding"))
+                return s;
+            if (radon_status s = cuda_status(launch_colconv(P, s1, s2, 0, stream), "convolution"))
+                return s;
+            if (radon_status s = cuda_status(launch_rows_c2r(P, s2, stream), "inverse row FFT"))
+                return s;
+        }
+        if (radon_status s = cuda_status(launch_gather_radon(local + first, count, dpieces + first,
+                                                             p->qpieces[qi].first, p->qpieces[qi].second,
+                                                             g, stream),
+                                         "interpolation"))
+            return s;
+    }
+    return RADON_OK;
+}
+
+}  // namespace hr
