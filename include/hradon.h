@@ -98,7 +98,7 @@ typedef struct {
 /*
  * Fill *d with the default method parameters for the given problem:
  * tau0 = 0, dtau = (Nt-1) dt/(Ntau-1), sigma = 1.5, omega_c = 0.3,
- * one time split at 0.4 T, one slowness piece, current device.
+ * time splits at 0.25 T and 0.5 T, one slowness piece, current device.
  * Returns RADON_ERR_INVALID_ARG for a NULL d.
  */
 radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau, int Nq, double dt,

@@ -1,12 +1,8 @@
 // Pure arithmetic shared by the device kernels and by the host unit tests of
-// those kernels (compiled with g++ for the tests, nvcc for the library).
-//
-// * float-float ("double-single") helpers: lattice positions need about
-//   1e-6 cells out of several thousand, more than FP32 carries, so the few
-//   sums that lose digits are done as unevaluated pairs hi + lo of floats
-//   using error-free transformations (Dekker/Knuth TwoSum, FMA TwoProd).
-// * cubic B-spline tap weights (the B3 of Eq. (14)-(17)).
-// * one radix-r Stockham butterfly (the FFT of Eq. (7), (16)-(17)).
+// those kernels (compiled with g++ for the tests, nvcc for the library):
+// * cubic B-spline tap weights (the B3 of Eq. (14)-(17));
+// * one radix-r Stockham butterfly (the FFT of Eq. (7), (16)-(17));
+// * the packing of a real FFT into a complex FFT of half the length.
 #pragma once
 
 #include <math.h>
@@ -20,76 +16,7 @@
 
 namespace hr {
 
-struct ff { float hi, lo; };           // value = hi + lo, |lo| <= ulp(hi)/2
 struct cf { float x, y; };             // complex float
-
-HD float fma_(float a, float b, float c) {
-#if defined(__CUDA_ARCH__)
-    return __fmaf_rn(a, b, c);
-#else
-    return fmaf(a, b, c);
-#endif
-}
-
-// a + b exactly as hi + lo (Knuth TwoSum).
-HD ff two_sum(float a, float b) {
-    float s = a + b;
-    float bb = s - a;
-    float e = (a - (s - bb)) + (b - bb);
-    return {s, e};
-}
-
-// a * b exactly as hi + lo (FMA TwoProd).
-HD ff two_prod(float a, float b) {
-    float p = a * b;
-    return {p, fma_(a, b, -p)};
-}
-
-// (x) * (y) for float-float x, y; relative error ~2^-44.
-HD ff ff_mul(ff x, ff y) {
-    ff p = two_prod(x.hi, y.hi);
-    float lo = p.lo + (x.hi * y.lo + x.lo * y.hi);
-    return two_sum(p.hi, lo);
-}
-
-// float-float times an exactly representable float.
-HD ff ff_mul_f(ff x, float b) {
-    ff p = two_prod(x.hi, b);
-    return two_sum(p.hi, p.lo + x.lo * b);
-}
-
-HD ff ff_add(ff x, ff y) {
-    ff s = two_sum(x.hi, y.hi);
-    return two_sum(s.hi, s.lo + x.lo + y.lo);
-}
-
-// Squared radius |u|^2 = lam^2 + h^2 of a sample whose rotated-frame
-// coordinates are float-float, as float-float.
-HD ff radius2(ff lam, ff h) {
-    ff a = two_prod(lam.hi, lam.hi);
-    ff b = two_prod(h.hi, h.hi);
-    ff s = two_sum(a.hi, b.hi);
-    float lo = s.lo + a.lo + b.lo + 2.0f * (lam.hi * lam.lo + h.hi * h.lo);
-    return two_sum(s.hi, lo);
-}
-
-// x - y for float-float x, y that agree to within a factor of two: the
-// leading difference is exact (Sterbenz), so the result keeps full digits.
-HD float ff_diff(ff x, ff y) {
-    return (x.hi - y.hi) + (x.lo - y.lo);
-}
-
-// Angle of the vector (lam, h) measured from the direction (c, s), both in
-// float-float: atan2(c*h - s*lam, c*lam + s*h). The cross product is a small
-// difference of two large products and is formed from exact TwoProd pieces.
-HD float angle_from(ff lam, ff h, ff c, ff s) {
-    ff p1 = two_prod(c.hi, h.hi);
-    ff p2 = two_prod(s.hi, lam.hi);
-    float cross = (p1.hi - p2.hi) +
-                  ((p1.lo - p2.lo) + (c.hi * h.lo + c.lo * h.hi) - (s.hi * lam.lo + s.lo * lam.hi));
-    float dot = c.hi * lam.hi + s.hi * h.hi;
-    return atan2f(cross, dot);
-}
 
 // Cubic B-spline weights of the four taps i0 .. i0+3, i0 = floor(x) - 1,
 // at fractional part f = x - floor(x): B3(f+1), B3(f), B3(f-1), B3(f-2).

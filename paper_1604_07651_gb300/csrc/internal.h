@@ -17,6 +17,23 @@ struct FftPlan {            // radix schedule of one FFT length
     int rad[24];
 };
 
+// Lattice position of one gather sample, computed once per plan in FP64:
+// first taps (m0, n0) packed as (m0 << 16) | n0, fractional parts (ft, fr)
+// of the position in cells, and the sample weight w (zero when the sample is
+// muted or outside the sub-problem).
+struct __align__(16) SampleEnt { int mn; float ft, fr, w; };
+// Rho position of one output of a slowness column: first tap n0 (-1 when the
+// line misses the sub-problem's data) and fractional part fr.
+struct __align__(8) RadonEnt { int n0; float fr; };
+
+// FP64 geometry the plan-time table kernels need (by value).
+struct TableArgs {
+    double a, ca, sa, O1, O2, alpha;
+    double theta0, dtheta, rho0, drho, a_r, r_max;
+    double n_t, n_x, T, tau0, dtau;
+    int jt_lo, nj, Nx, Ntheta, Nrho, Ntau, ncol;
+};
+
 // Device-visible description of one sub-problem (one time piece of one
 // slowness piece). Passed to kernels by value.
 struct PieceDev {
@@ -27,28 +44,17 @@ struct PieceDev {
     int nkb;                // number of column blocks: ceil((k2max+1)/CB)
     int R;                  // lattice rows per band of the row kernels
     int nbands;
-    float theta0, rho0;     // lattice origin (approximate, for picking references)
-    float inv_dtheta, inv_drho;
-    float alpha;
     // samples of the gather
     int Nt, Nx;
-    int jt_lo, jt_hi;
+    int jt_lo, jt_hi, nj;   // nj = jt_hi - jt_lo + 1
     // output columns of the slowness piece
     int Ntau, l_lo, l_hi;
-    float a_r, r_max;       // lines with e^rho outside [a_r, r_max] miss the data
     // tables (device pointers)
-    const ff* lam;          // [Nt]   rotated-frame coordinate along e_alpha, per sample time
-    const float* cj;        // [Nt]   per-time weight: window * 2 a^2 tb / (n_t n_x dtheta drho)
-    const int* jfirst;      // [Nx]   first sample of each trace kept by the mute
-    const ff* hk;           // [Nx]   rotated-frame coordinate along e_perp, per trace
-    const float* wk;        // [Nx]   trapezoid weight in x
-    const int2* jband;      // [nbands][Nx] candidate sample range of each band
+    const SampleEnt* stab;  // [Nx][nj] position and weight of every sample of the piece
+    const RadonEnt* rtab;   // [ncol][Ntau] rho position of every output of the piece
+    const int* band_off;    // [nbands+1] offsets of each band's runs in `runs`
+    const int4* runs;       // (trace k, first sample j, count <= 64, 0): samples a band may touch
     const int2* lband;      // [nbands] candidate output-column range of each band
-    const ff* rowc;         // [Ntheta] cos(theta_m - alpha)
-    const ff* rows;         // [Ntheta] sin(theta_m - alpha)
-    const ff* R1;           // [Nrho] e^{rho_n}
-    const ff* R2;           // [Nrho] e^{2 rho_n}
-    const ff* E;            // [3 * ncol] e^rho(i) = E0 + E1 i + E2 i^2 per column
     const float4* colw;     // [ncol] theta tap weights of each column
     const int* colm0;       // [ncol] first theta tap of each column
     const float* colscale;  // [ncol] output scale 2 X cos(psi) / a
@@ -70,6 +76,9 @@ int launch_gather_radon(const PieceDev* pieces, int npieces, const PieceDev* dev
                         int l_lo, int l_hi, float* g, void* stream);
 int launch_gather_samples(const PieceDev* dev_pieces, int npieces, int Nt, int Nx,
                           float* f, void* stream);
+int launch_sample_table(const TableArgs& A, const double* cj, const double* wk, const int* jfirst,
+                        SampleEnt* out);
+int launch_radon_table(const TableArgs& A, const double* qb2, RadonEnt* out);
 int launch_zeta_gemm(const double* A, const double* Bre, const double* Bim, int n1, int nn,
                      int n2, double* Zre, double* Zim, void* stream);
 int launch_direct_fwd(const float* f, float* g, int Nt, int Nx, int Ntau, int Nq, double dt,

@@ -15,10 +15,11 @@
 //   k_scatter_radon -> k_colconv (conjugate kernel) -> k_rows_c2r ->
 //   k_gather_samples.
 //
-// Lattice positions are computed in float-float where FP32 loses digits (see
-// hostdev.h); everything else is FP32. Shared-memory accumulation uses FP32
-// atomics, so the last bits of the forward gridding depend on the order in
-// which warps arrive.
+// Lattice positions do not depend on the data: the plan computes them once in
+// FP64 (k_sample_table, k_radon_table) and stores first tap and fractional
+// part, so the transforms themselves are FP32 loads, B-spline weights and
+// sums. Shared-memory accumulation uses FP32 atomics, so the last bits of the
+// gridding depend on the order in which warps arrive.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -29,11 +30,6 @@ __device__ __forceinline__ cf ldcf(const cf* p) {
     float2 v = __ldg(reinterpret_cast<const float2*>(p));
     return {v.x, v.y};
 }
-__device__ __forceinline__ ff ldff(const ff* p) {
-    float2 v = __ldg(reinterpret_cast<const float2*>(p));
-    return {v.x, v.y};
-}
-
 // Block-cooperative Stockham FFT of `batch` sequences of length n stored
 // back to back in shared memory at a; b is a scratch buffer of the same size.
 // Returns the buffer that holds the result (a or b).
@@ -64,27 +60,6 @@ __device__ cf* block_fft(cf* a, cf* b, int n, int batch, const cf* __restrict__ 
         Ns *= R;
     }
     return a;
-}
-
-// e^rho of output row i of a column: E0 + E1 i + E2 i^2 in float-float.
-__device__ __forceinline__ ff radon_e(const ff* E, int i) {
-    const float fi = (float)i;
-    ff t = ff_mul_f(ldff(E + 2), fi);
-    t = ff_add(t, ldff(E + 1));
-    t = ff_mul_f(t, fi);
-    return ff_add(t, ldff(E));
-}
-
-// Lattice rho-position of a point at distance e (float-float) from the
-// origin: nearest lattice line n from a rough log, then the exact offset
-// log(e / e^{rho_n}) = log1p((e - e^{rho_n}) / e^{rho_n}).
-__device__ __forceinline__ float rho_position(const PieceDev& P, ff e, const ff* Rtab,
-                                              float logscale) {
-    int n = __float2int_rn((logscale * __logf(e.hi) - P.rho0) * P.inv_drho);
-    n = min(max(n, 0), P.Nrho - 1);
-    const ff Rn = ldff(Rtab + n);
-    const float d = logscale * log1pf(ff_diff(e, Rn) / Rn.hi);
-    return (float)n + d * P.inv_drho;
 }
 
 // --------------------------------------------------------------------------
@@ -121,7 +96,33 @@ __device__ __forceinline__ void zero_rows(const PieceDev& P) {
     for (int i = threadIdx.x; i < n4; i += blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+__device__ __forceinline__ void band_taps(int m0, int n0, int mb, int nrows, int Prho, float val,
+                                          const float wt[4], const float wr[4]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int m = m0 + a - mb;
+        if (m < 0 || m >= nrows) continue;
+        const float va = val * wt[a];
+        float* row = smem_f + m * Prho + n0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) atomicAdd(row + c, va * wr[c]);
+    }
+}
+
 // Forward gridding (Eq. (15)) of the gather f[Nx][Nt] for one band of rows.
+// The plan lists, per band, runs of at most 64 consecutive samples of one
+// trace that can reach the band; a warp takes a run, each lane two samples
+// (both loads issued before either is used).
+__device__ __forceinline__ void scatter_sample(const PieceDev& P, int4 e, float fv, int mb, int nrows) {
+    const float w = __int_as_float(e.w);
+    const int m0 = e.x >> 16, n0 = e.x & 0xffff;
+    if (w == 0.f || m0 + 3 < mb || m0 >= mb + nrows) return;
+    float wt[4], wr[4];
+    b3_weights(__int_as_float(e.y), wt);
+    b3_weights(__int_as_float(e.z), wr);
+    band_taps(m0, n0, mb, nrows, P.Prho, fv * w, wt, wr);
+}
+
 __global__ void __launch_bounds__(512) k_scatter_samples(PieceDev P, const float* __restrict__ f,
                                                          cf* __restrict__ spec) {
     const int mb = blockIdx.x * P.R;
@@ -129,43 +130,75 @@ __global__ void __launch_bounds__(512) k_scatter_samples(PieceDev P, const float
     zero_rows(P);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int2* jr = P.jband + (size_t)blockIdx.x * P.Nx;
-    const ff cr = ldff(P.rowc + mb), sr = ldff(P.rows + mb);
-    for (int k = warp; k < P.Nx; k += nw) {
-        const int2 r = __ldg(jr + k);
-        if (r.x > r.y) continue;
-        const ff h = ldff(P.hk + k);
-        const float wk = __ldg(P.wk + k);
+    const int r0 = __ldg(P.band_off + blockIdx.x), r1 = __ldg(P.band_off + blockIdx.x + 1);
+    for (int r = r0 + warp; r < r1; r += nw) {
+        const int4 run = __ldg(P.runs + r);
+        const int k = run.x, j = run.y + lane, n = run.z;
+        const int4* st = reinterpret_cast<const int4*>(P.stab + (size_t)k * P.nj - P.jt_lo);
         const float* fk = f + (size_t)k * P.Nt;
-        for (int j = r.x + lane; j <= r.y; j += 32) {
-            const ff lam = ldff(P.lam + j);
-            const float xth = (float)mb + angle_from(lam, h, cr, sr) * P.inv_dtheta;
-            const ff u2 = radius2(lam, h);
-            const float xrh = rho_position(P, u2, P.R2, 0.5f);
-            const float fm = floorf(xth), fn = floorf(xrh);
-            const int m0 = (int)fm - 1, n0 = (int)fn - 1;
-            if (n0 < 0 || n0 + 3 >= P.Nrho || m0 < 0 || m0 + 3 >= P.Ntheta) continue;
-            const float val = __ldg(fk + j) * __ldg(P.cj + j) * wk * rsqrtf(u2.hi);
-            float wt[4], wr[4];
-            b3_weights(xth - fm, wt);
-            b3_weights(xrh - fn, wr);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int m = m0 + a - mb;
-                if (m < 0 || m >= nrows) continue;
-                const float va = val * wt[a];
-                float* row = smem_f + m * P.Prho + n0;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) atomicAdd(row + c, va * wr[c]);
-            }
-        }
+        const bool a = lane < n, b = lane + 32 < n;
+        int4 e0 = make_int4(0, 0, 0, 0), e1 = e0;
+        float f0 = 0.f, f1 = 0.f;
+        if (a) { e0 = __ldg(st + j); f0 = __ldg(fk + j); }
+        if (b) { e1 = __ldg(st + j + 32); f1 = __ldg(fk + j + 32); }
+        if (a) scatter_sample(P, e0, f0, mb, nrows);
+        if (b) scatter_sample(P, e1, f1, mb, nrows);
     }
     __syncthreads();
     rows_r2c_write(P, mb, nrows, spec);
 }
 
+// One group of 32 consecutive outputs of a column (same theta taps; rho tap
+// n0 nondecreasing in the lane index) onto the band. When neighbouring lanes
+// share a first tap -- small intercept times put dozens of outputs in one
+// cell -- the lanes of each run of equal n0 are summed first with a
+// segmented warp scan and only the run's last lane adds to shared memory.
+__device__ __forceinline__ void scatter_column_group(int2 e, float v, int m0, const float wt[4],
+                                                     int mb, int nrows, int Prho, int lane) {
+    const unsigned FULL = 0xffffffffu;
+    const bool valid = e.x >= 0;
+    const int key = valid ? e.x : -1 - lane;
+    float wr[4] = {0.f, 0.f, 0.f, 0.f};
+    if (valid) b3_weights(__int_as_float(e.y), wr);
+    const int kprev = __shfl_up_sync(FULL, key, 1);
+    const bool head = lane == 0 || kprev != key;
+    if (!__any_sync(FULL, !head)) {
+        if (valid) band_taps(m0, e.x, mb, nrows, Prho, v, wt, wr);
+        return;
+    }
+    float s0 = v * wr[0], s1 = v * wr[1], s2 = v * wr[2], s3 = v * wr[3];
+    int h = head;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float t0 = __shfl_up_sync(FULL, s0, d), t1 = __shfl_up_sync(FULL, s1, d);
+        const float t2 = __shfl_up_sync(FULL, s2, d), t3 = __shfl_up_sync(FULL, s3, d);
+        const int th = __shfl_up_sync(FULL, h, d);
+        if (lane >= d && !h) {
+            s0 += t0;
+            s1 += t1;
+            s2 += t2;
+            s3 += t3;
+            h |= th;
+        }
+    }
+    const int knext = __shfl_down_sync(FULL, key, 1);
+    const bool tail = lane == 31 || knext != key;
+    if (valid && tail) {
+        const float sw[4] = {s0, s1, s2, s3};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int m = m0 + a - mb;
+            if (m < 0 || m >= nrows) continue;
+            float* row = smem_f + m * Prho + e.x;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) atomicAdd(row + c, wt[a] * sw[c]);
+        }
+    }
+}
+
 // Adjoint of the output interpolation: scatter g[Nq][Ntau] of this slowness
-// piece's columns onto one band of rows (transpose of Eq. (17)).
+// piece's columns onto one band of rows (transpose of Eq. (17)). Work items
+// are (column, block of 64 intercept times), two groups of 32 per item.
 __global__ void __launch_bounds__(512) k_scatter_radon(PieceDev P, const float* __restrict__ g,
                                                        cf* __restrict__ spec) {
     const int mb = blockIdx.x * P.R;
@@ -174,34 +207,24 @@ __global__ void __launch_bounds__(512) k_scatter_radon(PieceDev P, const float* 
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int2 lr = __ldg(P.lband + blockIdx.x);
-    for (int l = lr.x + warp; l <= lr.y; l += nw) {
+    const int nblk = (P.Ntau + 63) >> 6;
+    const int items = lr.y >= lr.x ? (lr.y - lr.x + 1) * nblk : 0;
+    for (int it = warp; it < items; it += nw) {
+        const int l = lr.x + it / nblk;
+        const int i = ((it % nblk) << 6) + lane;
         const int lc = l - P.l_lo;
+        const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * P.Ntau);
+        const float* gl = g + (size_t)l * P.Ntau;
+        int2 e0 = make_int2(-1, 0), e1 = e0;
+        float g0 = 0.f, g1 = 0.f;
+        if (i < P.Ntau) { e0 = __ldg(rt + i); g0 = __ldg(gl + i); }
+        if (i + 32 < P.Ntau) { e1 = __ldg(rt + i + 32); g1 = __ldg(gl + i + 32); }
         const int m0 = __ldg(P.colm0 + lc);
         const float4 w4 = __ldg(P.colw + lc);
         const float wt[4] = {w4.x, w4.y, w4.z, w4.w};
         const float sc = __ldg(P.colscale + lc);
-        const ff* E = P.E + 3 * lc;
-        const float* gl = g + (size_t)l * P.Ntau;
-        for (int i = lane; i < P.Ntau; i += 32) {
-            const ff e = radon_e(E, i);
-            if (!(e.hi >= P.a_r && e.hi <= P.r_max)) continue;
-            const float xrh = rho_position(P, e, P.R1, 1.0f);
-            const float fn = floorf(xrh);
-            const int n0 = (int)fn - 1;
-            if (n0 < 0 || n0 + 3 >= P.Nrho) continue;
-            float wr[4];
-            b3_weights(xrh - fn, wr);
-            const float val = __ldg(gl + i) * sc;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int m = m0 + a - mb;
-                if (m < 0 || m >= nrows) continue;
-                const float va = val * wt[a];
-                float* row = smem_f + m * P.Prho + n0;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) atomicAdd(row + c, va * wr[c]);
-            }
-        }
+        scatter_column_group(e0, g0 * sc, m0, wt, mb, nrows, P.Prho, lane);
+        scatter_column_group(e1, g1 * sc, m0, wt, mb, nrows, P.Prho, lane);
     }
     __syncthreads();
     rows_r2c_write(P, mb, nrows, spec);
@@ -219,9 +242,19 @@ __global__ void __launch_bounds__(512) k_colconv(PieceDev P, const cf* __restric
     cf* A = reinterpret_cast<cf*>(smem_f);
     cf* B = A + CB * Pt;
     const cf* src = in + (size_t)kb * Nth * CB;
-    for (int idx = threadIdx.x; idx < Pt * CB; idx += blockDim.x) {
-        const int m = idx / CB, c = idx - m * CB;
-        A[c * Pt + m] = m < Nth ? ldcf(src + idx) : cf{0.f, 0.f};
+    if (CB == 2) {
+        // one 16-byte load per lattice row: both columns of the block
+        for (int m = threadIdx.x; m < Pt; m += blockDim.x) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (m < Nth) v = __ldg(reinterpret_cast<const float4*>(src) + m);
+            A[m] = {v.x, v.y};
+            A[Pt + m] = {v.z, v.w};
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < Pt * CB; idx += blockDim.x) {
+            const int m = idx / CB, c = idx - m * CB;
+            A[c * Pt + m] = m < Nth ? ldcf(src + idx) : cf{0.f, 0.f};
+        }
     }
     __syncthreads();
     cf* X = block_fft<-1>(A, B, Pt, CB, P.twT, P.fftT);
@@ -241,9 +274,16 @@ __global__ void __launch_bounds__(512) k_colconv(PieceDev P, const cf* __restric
     __syncthreads();
     cf* Zr = block_fft<+1>(X, Y, Pt, CB, P.twT, P.fftT);
     cf* dst = out + (size_t)kb * Nth * CB;
-    for (int idx = threadIdx.x; idx < Nth * CB; idx += blockDim.x) {
-        const int m = idx / CB, c = idx - m * CB;
-        dst[idx] = Zr[c * Pt + m];
+    if (CB == 2) {
+        for (int m = threadIdx.x; m < Nth; m += blockDim.x) {
+            const cf a = Zr[m], b = Zr[Pt + m];
+            reinterpret_cast<float4*>(dst)[m] = make_float4(a.x, a.y, b.x, b.y);
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < Nth * CB; idx += blockDim.x) {
+            const int m = idx / CB, c = idx - m * CB;
+            dst[idx] = Zr[c * Pt + m];
+        }
     }
 }
 
@@ -258,14 +298,19 @@ __global__ void __launch_bounds__(512) k_rows_c2r(PieceDev P, const cf* __restri
     cf* X = reinterpret_cast<cf*>(smem_f);
     cf* tmp = X + P.R * M;
     const int nk = P.k2max + 1;
+    // zero the bins above k2max, then copy the stored ones in the blocked
+    // layout's order (contiguous rows of the band for each column block)
     for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
         const int m = idx / M, k = idx - m * M;
-        cf v = {0.f, 0.f};
-        if (k < nk) {
-            const int kb = k / P.CB, c = k - kb * P.CB;
-            v = ldcf(spec + ((size_t)kb * P.Ntheta + (mb + m)) * P.CB + c);
-        }
-        X[idx] = v;
+        if (k >= nk) X[idx] = cf{0.f, 0.f};
+    }
+    const int per_kb = nrows * P.CB;
+    for (int idx = threadIdx.x; idx < P.nkb * per_kb; idx += blockDim.x) {
+        const int kb = idx / per_kb;
+        const int rem = idx - kb * per_kb;
+        const int m = rem / P.CB, c = rem - m * P.CB;
+        const int k = kb * P.CB + c;
+        if (k < nk) X[m * M + k] = ldcf(spec + ((size_t)kb * P.Ntheta + mb) * P.CB + rem);
     }
     __syncthreads();
     const int half = M / 2;
@@ -312,24 +357,19 @@ __global__ void __launch_bounds__(256) k_gather_radon(const PieceDev* __restrict
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)ncol * Ntau) return;
     const int lc = (int)(idx / Ntau);
-    const int i = (int)(idx - (long)lc * Ntau);
     float acc = 0.f;
     for (int p = 0; p < np; ++p) {
         const PieceDev& P = pieces[p];
-        const ff e = radon_e(P.E + 3 * lc, i);
-        if (!(e.hi >= P.a_r && e.hi <= P.r_max)) continue;
-        const float xrh = rho_position(P, e, P.R1, 1.0f);
-        const float fn = floorf(xrh);
-        const int n0 = (int)fn - 1;
-        if (n0 < 0 || n0 + 3 >= P.Nrho) continue;
+        const int2 e = __ldg(reinterpret_cast<const int2*>(P.rtab + idx));
+        if (e.x < 0) continue;
         float wr[4];
-        b3_weights(xrh - fn, wr);
+        b3_weights(__int_as_float(e.y), wr);
         const float4 w4 = __ldg(P.colw + lc);
         const float wt[4] = {w4.x, w4.y, w4.z, w4.w};
         const int m0 = __ldg(P.colm0 + lc);
-        acc += __ldg(P.colscale + lc) * taps16(P.lat, P.Nrho, m0, n0, wt, wr);
+        acc += __ldg(P.colscale + lc) * taps16(P.lat, P.Nrho, m0, e.x, wt, wr);
     }
-    g[(size_t)(l_lo + lc) * Ntau + i] = acc;
+    g[(size_t)l_lo * Ntau + idx] = acc;
 }
 
 // Adjoint of the gridding (transpose of Eq. (15)): every gather sample reads
@@ -343,26 +383,75 @@ __global__ void __launch_bounds__(256) k_gather_samples(const PieceDev* __restri
     float acc = 0.f;
     for (int p = 0; p < np; ++p) {
         const PieceDev& P = pieces[p];
-        if (j < P.jt_lo || j > P.jt_hi || j < __ldg(P.jfirst + k)) continue;
-        const ff lam = ldff(P.lam + j);
-        const ff h = ldff(P.hk + k);
-        const float phia = P.alpha + atan2f(h.hi, lam.hi);
-        int mr = __float2int_rn((phia - P.theta0) * P.inv_dtheta);
-        mr = min(max(mr, 0), P.Ntheta - 1);
-        const float xth = (float)mr +
-                          angle_from(lam, h, ldff(P.rowc + mr), ldff(P.rows + mr)) * P.inv_dtheta;
-        const ff u2 = radius2(lam, h);
-        const float xrh = rho_position(P, u2, P.R2, 0.5f);
-        const float fm = floorf(xth), fn = floorf(xrh);
-        const int m0 = (int)fm - 1, n0 = (int)fn - 1;
-        if (n0 < 0 || n0 + 3 >= P.Nrho || m0 < 0 || m0 + 3 >= P.Ntheta) continue;
+        if (j < P.jt_lo || j > P.jt_hi) continue;
+        const int4 e = __ldg(reinterpret_cast<const int4*>(P.stab + (size_t)k * P.nj + (j - P.jt_lo)));
+        const float w = __int_as_float(e.w);
+        if (w == 0.f) continue;
         float wt[4], wr[4];
-        b3_weights(xth - fm, wt);
-        b3_weights(xrh - fn, wr);
-        const float w = __ldg(P.cj + j) * __ldg(P.wk + k) * rsqrtf(u2.hi);
-        acc += w * taps16(P.lat, P.Nrho, m0, n0, wt, wr);
+        b3_weights(__int_as_float(e.y), wt);
+        b3_weights(__int_as_float(e.z), wr);
+        acc += w * taps16(P.lat, P.Nrho, e.x >> 16, e.x & 0xffff, wt, wr);
     }
     f[idx] = acc;
+}
+
+// --------------------------------------------------------------------------
+// Plan time, FP64: lattice positions of every gather sample and of every
+// output (the maps P1 T of Eq. (10)/(14) and P2 S of Eq. (9)/(17)).
+// --------------------------------------------------------------------------
+__global__ void k_sample_table(TableArgs A, const double* __restrict__ cj, const double* __restrict__ wk,
+                               const int* __restrict__ jfirst, SampleEnt* __restrict__ out) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)A.nj * A.Nx) return;
+    const int k = (int)(idx / A.nj);
+    const int jl = (int)(idx - (long)k * A.nj);
+    const int j = A.jt_lo + jl;
+    const double tb = j / A.n_t, xb = k / A.n_x;
+    const double ds = tb * tb - 0.5, dy = xb * xb - 0.5;
+    const double u1 = A.a * (A.ca * ds - A.sa * dy) + A.O1;
+    const double u2 = A.a * (A.sa * ds + A.ca * dy) + A.O2;
+    const double r2 = u1 * u1 + u2 * u2;
+    const double xth = (atan2(u2, u1) - A.theta0) / A.dtheta;
+    const double xrh = (0.5 * log(r2) - A.rho0) / A.drho;
+    const double fm = floor(xth), fn = floor(xrh);
+    int m0 = (int)fm - 1, n0 = (int)fn - 1;
+    double w = (j >= jfirst[k]) ? cj[jl] * wk[k] / sqrt(r2) : 0.0;
+    if (m0 < 0 || m0 + 3 >= A.Ntheta || n0 < 0 || n0 + 3 >= A.Nrho) {
+        w = 0.0;
+        m0 = 0;
+        n0 = 0;
+    }
+    SampleEnt e;
+    e.mn = (m0 << 16) | n0;
+    e.ft = (float)(xth - fm);
+    e.fr = (float)(xrh - fn);
+    e.w = (float)w;
+    out[idx] = e;
+}
+
+__global__ void k_radon_table(TableArgs A, const double* __restrict__ qb2, RadonEnt* __restrict__ out) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)A.ncol * A.Ntau) return;
+    const int lc = (int)(idx / A.Ntau);
+    const int i = (int)(idx - (long)lc * A.Ntau);
+    const double m = qb2[lc];
+    const double psi = atan(m);
+    const double theta = A.alpha - psi;
+    const double tb = (A.tau0 + i * A.dtau) / A.T;
+    const double e = A.a * cos(psi) * (tb * tb - 0.5 + 0.5 * m) + A.O1 * cos(theta) + A.O2 * sin(theta);
+    RadonEnt r;
+    r.n0 = -1;
+    r.fr = 0.f;
+    if (e >= A.a_r && e <= A.r_max) {
+        const double xrh = (log(e) - A.rho0) / A.drho;
+        const double fn = floor(xrh);
+        const int n0 = (int)fn - 1;
+        if (n0 >= 0 && n0 + 3 < A.Nrho) {
+            r.n0 = n0;
+            r.fr = (float)(xrh - fn);
+        }
+    }
+    out[idx] = r;
 }
 
 // --------------------------------------------------------------------------
@@ -551,6 +640,19 @@ int launch_gather_samples(const PieceDev* dev_pieces, int npieces, int Nt, int N
     const int bs = 256;
     const long nb = (total + bs - 1) / bs;
     k_gather_samples<<<(unsigned)nb, bs, 0, (cudaStream_t)stream>>>(dev_pieces, npieces, Nt, Nx, f);
+    return check_launch();
+}
+
+int launch_sample_table(const TableArgs& A, const double* cj, const double* wk, const int* jfirst,
+                        SampleEnt* out) {
+    const long total = (long)A.nj * A.Nx;
+    k_sample_table<<<(unsigned)((total + 255) / 256), 256>>>(A, cj, wk, jfirst, out);
+    return check_launch();
+}
+
+int launch_radon_table(const TableArgs& A, const double* qb2, RadonEnt* out) {
+    const long total = (long)A.ncol * A.Ntau;
+    k_radon_table<<<(unsigned)((total + 255) / 256), 256>>>(A, qb2, out);
     return check_launch();
 }
 

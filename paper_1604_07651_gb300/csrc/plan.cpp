@@ -32,12 +32,6 @@ const double kPi = 3.14159265358979323846;
 const double kTOverlap = 1.25;   // half-width ratio of the time-partition transition bands
 const double kBetaMin = 1e-3;    // smallest angular opening of a sub-problem
 
-ff to_ff(double v) {
-    float hi = (float)v;
-    float lo = (float)(v - (double)hi);
-    return {hi, lo};
-}
-
 int fft_size(int n) {
     long best = -1;
     for (long p = 1; p < 2L * n + 2; p *= 2) {
@@ -524,53 +518,28 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.CB = CB;
     P.nkb = (h.k2max + 1 + CB - 1) / CB;
     P.nbands = (h.Ntheta + R - 1) / R;
-    P.theta0 = (float)h.theta0;
-    P.rho0 = (float)h.rho0;
-    P.inv_dtheta = (float)(1.0 / h.dtheta);
-    P.inv_drho = (float)(1.0 / h.drho);
-    P.alpha = (float)h.alpha;
     P.Nt = d.Nt;
     P.Nx = d.Nx;
     P.jt_lo = h.jt_lo;
     P.jt_hi = h.jt_hi;
+    P.nj = h.jt_hi - h.jt_lo + 1;
     P.Ntau = d.Ntau;
     P.l_lo = h.l_lo;
     P.l_hi = h.l_hi;
-    P.a_r = (float)h.a_r;
-    P.r_max = (float)h.r_max;
     P.fftM = make_fft_plan(h.Prho / 2);
     P.fftT = make_fft_plan(h.Ptheta);
 
-    const double ca = std::cos(h.alpha), sa = std::sin(h.alpha);
-    const double Oa = h.O1 * ca + h.O2 * sa;       // O . e_alpha
-    const double Op = -h.O1 * sa + h.O2 * ca;      // O . e_perp
-    std::vector<ff> lam(d.Nt), hk(d.Nx);
-    std::vector<float> cj(d.Nt, 0.f), wk(d.Nx);
-    for (int j = 0; j < d.Nt; ++j) {
-        const double tb = j / n_t;
-        lam[j] = to_ff(h.a * (tb * tb - 0.5) + Oa);
-        if (j >= h.jt_lo && j <= h.jt_hi) {
-            const double w = t_window(bs, h.tpiece, tb);
-            cj[j] = (float)(w * 2.0 * h.a * h.a * tb / (n_t * n_x * h.dtheta * h.drho));
-        }
+    // per-time weight (window, 2 a^2 tb, quadrature and B-spline normalisation)
+    // and trapezoid weights in x, both FP64 for the position-table kernel
+    std::vector<double> cj(P.nj), wk(d.Nx);
+    for (int jl = 0; jl < P.nj; ++jl) {
+        const double tb = (h.jt_lo + jl) / n_t;
+        const double w = t_window(bs, h.tpiece, tb);
+        cj[jl] = w * 2.0 * h.a * h.a * tb / (n_t * n_x * h.dtheta * h.drho);
     }
-    for (int k = 0; k < d.Nx; ++k) {
-        const double xb = k / n_x;
-        hk[k] = to_ff(h.a * (xb * xb - 0.5) + Op);
-        wk[k] = (k == 0 || k == d.Nx - 1) ? 0.5f : 1.0f;
-    }
-    std::vector<ff> rowc(h.Ntheta), rows(h.Ntheta), R1(h.Nrho), R2(h.Nrho);
-    for (int m = 0; m < h.Ntheta; ++m) {
-        const double g = h.theta0 + m * h.dtheta - h.alpha;
-        rowc[m] = to_ff(std::cos(g));
-        rows[m] = to_ff(std::sin(g));
-    }
-    for (int n = 0; n < h.Nrho; ++n) {
-        const double rho = h.rho0 + n * h.drho;
-        R1[n] = to_ff(std::exp(rho));
-        R2[n] = to_ff(std::exp(2.0 * rho));
-    }
-    // candidate sample range of every band (from the FP64 angles, one sample of margin)
+    for (int k = 0; k < d.Nx; ++k) wk[k] = (k == 0 || k == d.Nx - 1) ? 0.5 : 1.0;
+    // candidate sample range of every band (from the FP64 angles, one sample of margin:
+    // the device tables come from the same FP64 formulas)
     const int nj = h.jt_hi - h.jt_lo + 1;
     std::vector<int2> jband((size_t)P.nbands * d.Nx, int2{1, 0});
     for (int k = 0; k < d.Nx; ++k) {
@@ -578,8 +547,8 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
         for (int j = jstart; j <= h.jt_hi; ++j) {
             const double xth = (phi_all[(size_t)k * nj + (j - h.jt_lo)] - h.theta0) / h.dtheta;
             const int fl = (int)std::floor(xth);
-            int b0 = (int)std::ceil((double)(fl - 1 - R) / R);
-            int b1 = (int)std::floor((double)(fl + 3) / R);
+            int b0 = (int)std::ceil((double)(fl - R) / R);
+            int b1 = (int)std::floor((double)(fl + 2) / R);
             b0 = std::max(b0, 0);
             b1 = std::min(b1, P.nbands - 1);
             for (int b = b0; b <= b1; ++b) {
@@ -599,17 +568,26 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
             }
         }
     }
+    // runs of at most 64 samples of one trace, grouped by band
+    std::vector<int> band_off(P.nbands + 1, 0);
+    std::vector<int4> runs;
+    for (int b = 0; b < P.nbands; ++b) {
+        band_off[b] = (int)runs.size();
+        for (int k = 0; k < d.Nx; ++k) {
+            const int2 r = jband[(size_t)b * d.Nx + k];
+            for (int j = r.x; j <= r.y; j += 64) runs.push_back(int4{k, j, std::min(64, r.y - j + 1), 0});
+        }
+    }
+    band_off[P.nbands] = (int)runs.size();
     // output columns: theta taps, scale, e^rho polynomial; band column ranges
     const std::vector<double> q = q_grid(d);
     const int ncol = h.l_hi - h.l_lo + 1;
     std::vector<float4> colw(ncol);
     std::vector<int> colm0(ncol);
     std::vector<float> colscale(ncol);
-    std::vector<ff> E(3 * (size_t)ncol);
+    std::vector<double> qb2(ncol);
     std::vector<int2> lband(P.nbands, int2{1, 0});
     const double dtau = d.dtau > 0 ? d.dtau : T / (d.Ntau - 1);
-    const double c0 = (d.tau0 / T) * (d.tau0 / T), c1 = 2.0 * (d.tau0 / T) * (dtau / T),
-                 c2 = (dtau / T) * (dtau / T);
     for (int lc = 0; lc < ncol; ++lc) {
         const double qb = q[h.l_lo + lc] * X / T;
         const double m = qb * qb;
@@ -623,15 +601,10 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
         colm0[lc] = m0;
         colw[lc] = make_float4((float)b3(fr + 1.0), (float)b3(fr), (float)b3(fr - 1.0), (float)b3(fr - 2.0));
         colscale[lc] = (float)(2.0 * X * std::cos(psi) / h.a);
-        const double Acoef = h.a * std::cos(psi);
-        const double Bcoef = h.a * std::cos(psi) * (0.5 * m - 0.5) + h.O1 * std::cos(theta) +
-                             h.O2 * std::sin(theta);
-        E[3 * lc + 0] = to_ff(Acoef * c0 + Bcoef);
-        E[3 * lc + 1] = to_ff(Acoef * c1);
-        E[3 * lc + 2] = to_ff(Acoef * c2);
+        qb2[lc] = m;
         const int flc = m0 + 1;
-        int b0 = (int)std::ceil((double)(flc - 1 - R) / R);
-        int b1 = (int)std::floor((double)(flc + 3) / R);
+        int b0 = (int)std::ceil((double)(flc - R) / R);
+        int b1 = (int)std::floor((double)(flc + 2) / R);
         b0 = std::max(b0, 0);
         b1 = std::min(b1, P.nbands - 1);
         for (int b = b0; b <= b1; ++b) {
@@ -657,17 +630,53 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     if (radon_status s = kernel_spectrum(p, h, CB, P.nkb, K)) return s;
 
     radon_status s = RADON_OK;
-    if ((s = dev_upload(p, lam, &P.lam)) || (s = dev_upload(p, cj, &P.cj)) ||
-        (s = dev_upload(p, h.jfirst, &P.jfirst)) || (s = dev_upload(p, hk, &P.hk)) ||
-        (s = dev_upload(p, wk, &P.wk)) || (s = dev_upload(p, jband, &P.jband)) ||
-        (s = dev_upload(p, lband, &P.lband)) || (s = dev_upload(p, rowc, &P.rowc)) ||
-        (s = dev_upload(p, rows, &P.rows)) || (s = dev_upload(p, R1, &P.R1)) ||
-        (s = dev_upload(p, R2, &P.R2)) || (s = dev_upload(p, E, (const ff**)&P.E)) ||
+    if ((s = dev_upload(p, band_off, &P.band_off)) || (s = dev_upload(p, runs, &P.runs)) ||
+        (s = dev_upload(p, lband, &P.lband)) ||
         (s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
         (s = dev_upload(p, colscale, &P.colscale)) || (s = dev_upload(p, K, &P.K)) ||
         (s = dev_upload(p, twM, &P.twM)) || (s = dev_upload(p, twP, &P.twP)) ||
         (s = dev_upload(p, twT, &P.twT)))
         return s;
+    // position tables, FP64 on the device
+    TableArgs A;
+    A.a = h.a;
+    A.ca = std::cos(h.alpha);
+    A.sa = std::sin(h.alpha);
+    A.O1 = h.O1;
+    A.O2 = h.O2;
+    A.alpha = h.alpha;
+    A.theta0 = h.theta0;
+    A.dtheta = h.dtheta;
+    A.rho0 = h.rho0;
+    A.drho = h.drho;
+    A.a_r = h.a_r;
+    A.r_max = h.r_max;
+    A.n_t = n_t;
+    A.n_x = n_x;
+    A.T = T;
+    A.tau0 = d.tau0;
+    A.dtau = dtau;
+    A.jt_lo = h.jt_lo;
+    A.nj = P.nj;
+    A.Nx = d.Nx;
+    A.Ntheta = h.Ntheta;
+    A.Nrho = h.Nrho;
+    A.Ntau = d.Ntau;
+    A.ncol = ncol;
+    const double *dcj = nullptr, *dwk = nullptr, *dqb2 = nullptr;
+    const int* djf = nullptr;
+    void* tab = nullptr;
+    if ((s = dev_upload(p, cj, &dcj)) || (s = dev_upload(p, wk, &dwk)) ||
+        (s = dev_upload(p, h.jfirst, &djf)) || (s = dev_upload(p, qb2, &dqb2)))
+        return s;
+    if ((s = dev_alloc(p, (size_t)P.nj * d.Nx * sizeof(SampleEnt), &tab))) return s;
+    P.stab = (const SampleEnt*)tab;
+    if (int e = launch_sample_table(A, dcj, dwk, djf, (SampleEnt*)tab))
+        return fail(RADON_ERR_CUDA, std::string("position table: ") + cudaGetErrorString((cudaError_t)e));
+    if ((s = dev_alloc(p, (size_t)ncol * d.Ntau * sizeof(RadonEnt), &tab))) return s;
+    P.rtab = (const RadonEnt*)tab;
+    if (int e = launch_radon_table(A, dqb2, (RadonEnt*)tab))
+        return fail(RADON_ERR_CUDA, std::string("position table: ") + cudaGetErrorString((cudaError_t)e));
     void* lat = nullptr;
     if ((s = dev_alloc(p, (size_t)h.Ntheta * h.Nrho * sizeof(float), &lat))) return s;
     P.lat = (float*)lat;
@@ -731,8 +740,9 @@ extern "C" radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau,
     d->dtau = 0.0;
     d->sigma = 1.5;
     d->omega_c = 0.3;
-    d->n_tsplit = 1;
-    d->tsplit[0] = 0.4;
+    d->n_tsplit = 2;
+    d->tsplit[0] = 0.25;
+    d->tsplit[1] = 0.5;
     d->n_qsplit = 1;
     d->device = -1;
     return RADON_OK;

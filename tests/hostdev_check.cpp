@@ -1,6 +1,6 @@
 // Host check of the arithmetic the CUDA kernels use (csrc/hostdev.h):
-// Stockham FFT stages, the real-FFT packing pair, and the float-float lattice
-// positions. Compiled with g++ by tests/test_hostdev.py; prints "name value"
+// Stockham FFT stages, the real-FFT packing pair and the B-spline weights.
+// Compiled with g++ by tests/test_hostdev.py; prints "name value"
 // lines (errors) that the test compares with thresholds.
 #include <cmath>
 #include <complex>
@@ -106,52 +106,6 @@ static double irfft_error(int P, int kmax, std::mt19937& rng) {
     return std::sqrt(num / den);
 }
 
-static ff to_ff(double v) {
-    float hi = (float)v;
-    return {hi, (float)(v - (double)hi)};
-}
-
-// Lattice positions of random points near the unit arc in float-float,
-// against FP64: max error in cells for spacing 1e-4.
-static void position_errors(std::mt19937& rng, double& eth, double& erh, double& erh_e) {
-    std::uniform_real_distribution<double> U(0, 1);
-    const double dcell = 1e-4;
-    eth = erh = erh_e = 0;
-    for (int it = 0; it < 200000; ++it) {
-        const double alpha = 0.2 + 0.4 * U(rng);
-        const double lam = 0.3 + 0.6 * U(rng), h = -0.3 + 0.5 * U(rng);
-        // reference row near the true angle
-        const double phi = alpha + std::atan2(h, lam);
-        const double theta0 = -0.3;
-        const int mr = (int)std::floor((phi - theta0) / dcell + 0.5) + (int)(7 * U(rng)) - 3;
-        const double g = theta0 + mr * dcell - alpha;
-        const float d = angle_from(to_ff(lam), to_ff(h), to_ff(std::cos(g)), to_ff(std::sin(g)));
-        const double xth = mr + d / dcell;
-        eth = std::max(eth, std::fabs(xth - (phi - theta0) / dcell));
-        // radius: eta = 0.5 log(lam^2 + h^2)
-        const ff u2 = radius2(to_ff(lam), to_ff(h));
-        const double eta = 0.5 * std::log(lam * lam + h * h);
-        const double rho0 = -0.9;
-        const int n = (int)std::floor((eta - rho0) / dcell + 0.5) + (int)(3 * U(rng)) - 1;
-        const ff Rn = to_ff(std::exp(2.0 * (rho0 + n * dcell)));
-        const float de = 0.5f * log1pf(ff_diff(u2, Rn) / Rn.hi);
-        erh = std::max(erh, std::fabs(n + de / dcell - (eta - rho0) / dcell));
-        // e^rho of an output: E0 + E1 i + E2 i^2
-        const double E0 = 0.4 + 0.2 * U(rng), E1 = 1e-5 * U(rng), E2 = 3e-7 * U(rng);
-        const int i = (int)(2048 * U(rng));
-        ff t = ff_mul_f(to_ff(E2), (float)i);
-        t = ff_add(t, to_ff(E1));
-        t = ff_mul_f(t, (float)i);
-        const ff e = ff_add(t, to_ff(E0));
-        const double ed = E0 + E1 * i + E2 * (double)i * i;
-        const double rho = std::log(ed);
-        const int n2 = (int)std::floor((rho - rho0) / dcell + 0.5);
-        const ff R1 = to_ff(std::exp(rho0 + n2 * dcell));
-        const float dr = log1pf(ff_diff(e, R1) / R1.hi);
-        erh_e = std::max(erh_e, std::fabs(n2 + dr / dcell - (rho - rho0) / dcell));
-    }
-}
-
 static double b3_error() {
     double e = 0;
     for (int i = 0; i <= 1000; ++i) {
@@ -181,11 +135,6 @@ int main() {
     for (int P : {8, 12, 64, 96, 768, 1024}) e = std::max(e, irfft_error(P, P / 2 - 1, rng));
     for (int P : {64, 768}) e = std::max(e, irfft_error(P, P / 5, rng));
     std::printf("irfft_rel_l2 %.3e\n", e);
-    double eth, erh, erh_e;
-    position_errors(rng, eth, erh, erh_e);
-    std::printf("theta_cells %.3e\n", eth);
-    std::printf("rho_cells %.3e\n", erh);
-    std::printf("rho_out_cells %.3e\n", erh_e);
     std::printf("b3_weights %.3e\n", b3_error());
     return 0;
 }
