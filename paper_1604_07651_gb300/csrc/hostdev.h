@@ -10,8 +10,10 @@
 
 #if defined(__CUDACC__)
 #define HD __host__ __device__ __forceinline__
+#define HD_UNROLL _Pragma("unroll")
 #else
 #define HD inline
+#define HD_UNROLL
 #endif
 
 namespace hr {
@@ -28,6 +30,13 @@ HD void b3_weights(float f, float w[4]) {
     w[2] = (1.0f + 3.0f * f + 3.0f * f2 - 3.0f * f3) * (1.0f / 6.0f);
     w[3] = f3 * (1.0f / 6.0f);
 }
+
+// Shared-memory layout of every FFT buffer: element i of a sequence lives at
+// sw(i). XOR-ing the low four bits with the next four spreads the strided
+// stores of the first radix-16 stage (stride 16 elements) over all banks and
+// keeps contiguous accesses conflict-free. A permutation within each block of
+// 16 (and the identity below 16), so sw(i) < n for every length the FFT uses.
+HD int sw(int i) { return i ^ ((i >> 4) & 15); }
 
 HD cf cmul(cf a, cf b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 HD cf cmulc(cf a, cf b) { return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }  // a * conj(b)
@@ -71,43 +80,126 @@ HD void dft_small<3>(cf v[3], int dir) {
     v[2] = csub(m, id);
 }
 
-// One Stockham autosort butterfly (Govindaraju et al., SC'08 formulation):
-// stage of radix R with Ns = product of the radices already applied, for the
-// butterfly index j in [0, n/R). tw[k] = exp(-2 pi i k / n), k < n (the
-// forward twiddles; the inverse, dir = +1, uses their conjugates).
-template <int R>
-HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int j, const cf* tw, int dir) {
-    cf v[R];
-    int jm = j % Ns;
-    int step = n / (Ns * R);                 // twiddle index stride: k/(Ns R) = k*step/n
-    for (int r = 0; r < R; ++r) {
-        cf x = in[j + r * (n / R)];
-        int t = r * jm * step;               // < n
-        v[r] = r ? (dir < 0 ? cmul(x, tw[t]) : cmulc(x, tw[t])) : x;
+// cos(2 pi i / 16); with i a compile-time constant after unrolling, the
+// switch folds to a literal (no table in local memory).
+HD float cos16(int i) {
+    switch (i & 15) {
+        case 0: return 1.0f;
+        case 1: case 15: return 0.92387953251128674f;
+        case 2: case 14: return 0.70710678118654752f;
+        case 3: case 13: return 0.38268343236508977f;
+        case 4: case 12: return 0.0f;
+        case 5: case 11: return -0.38268343236508977f;
+        case 6: case 10: return -0.70710678118654752f;
+        case 7: case 9: return -0.92387953251128674f;
+        default: return -1.0f;
     }
-    dft_small<R>(v, dir);
-    int dst = (j / Ns) * Ns * R + jm;
-    for (int r = 0; r < R; ++r) out[dst + r * Ns] = v[r];
 }
 
-// Radix plan of n = 2^a 3^b: radices 4, then 2, then 3. Returns the number
-// of stages, or -1 if n has another prime factor.
+// exp(dir * 2 pi i k / N) for the in-register DFTs of size 8 and 16.
+template <int N>
+HD cf unit_root(int k, int dir) {
+    const int i = k * (16 / N);
+    return {cos16(i), dir * cos16(i - 4)};   // sin(x) = cos(x - pi/2)
+}
+
+// Size 8 as 2 x 4: inputs x[2 n1 + n2], X[k1 + 4 k2].
+template <>
+HD void dft_small<8>(cf v[8], int dir) {
+    cf e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft_small<4>(e, dir);
+    dft_small<4>(o, dir);
+HD_UNROLL
+    for (int k = 0; k < 4; ++k) {
+        const cf t = k ? cmul(o[k], unit_root<8>(k, dir)) : o[k];
+        v[k] = cadd(e[k], t);
+        v[k + 4] = csub(e[k], t);
+    }
+}
+
+// Size 16 as 4 x 4: Y[n2][k1] = DFT4 over n1 of x[4 n1 + n2], times
+// W16^(n2 k1), then X[k1 + 4 k2] = DFT4 over n2.
+template <>
+HD void dft_small<16>(cf v[16], int dir) {
+    cf y[4][4];
+HD_UNROLL
+    for (int n2 = 0; n2 < 4; ++n2) {
+HD_UNROLL
+        for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
+        dft_small<4>(y[n2], dir);
+    }
+HD_UNROLL
+    for (int k1 = 0; k1 < 4; ++k1) {
+        cf z[4];
+HD_UNROLL
+        for (int n2 = 0; n2 < 4; ++n2) z[n2] = (n2 * k1 != 0) ? cmul(y[n2][k1], unit_root<16>(n2 * k1, dir)) : y[n2][k1];
+        dft_small<4>(z, dir);
+HD_UNROLL
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+    }
+}
+
+// One Stockham autosort butterfly (Govindaraju et al., SC'08 formulation),
+// split in its two halves so that a caller can keep all loads of a stage
+// before all stores (in-place stages): stage of radix R with
+// Ns = product of the radices already applied, butterfly index j in
+// [0, n/R). tw[k] = exp(-2 pi i k / n), k < n (the forward twiddles; the
+// inverse, dir = +1, uses their conjugates).
+template <int R>
+HD void stockham_load(const cf* in, int n, int Ns, int j, const cf* tw, int dir, cf v[R]) {
+    const int jm = j & (Ns - 1);                // Ns is a power of two
+    const int step = n / (Ns * R);              // twiddle index stride
+HD_UNROLL
+    for (int r = 0; r < R; ++r) {
+        cf x = in[sw(j + r * (n / R))];
+        if (r) {
+            const cf w = tw[r * jm * step];     // < n
+            x = dir < 0 ? cmul(x, w) : cmulc(x, w);
+        }
+        v[r] = x;
+    }
+}
+
+template <int R>
+HD void stockham_store(cf* out, int Ns, int lgNs, int j, int dir, cf v[R]) {
+    dft_small<R>(v, dir);
+    const int jm = j & (Ns - 1);
+    const int dst = ((j >> lgNs) * R << lgNs) + jm;
+HD_UNROLL
+    for (int r = 0; r < R; ++r) out[sw(dst + r * Ns)] = v[r];
+}
+
+template <int R>
+HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int lgNs, int j, const cf* tw, int dir) {
+    cf v[R];
+    stockham_load<R>(in, n, Ns, j, tw, dir, v);
+    stockham_store<R>(out, Ns, lgNs, j, dir, v);
+}
+
+// Radix plan of n = 2^a 3^b (b <= 1): radix 16 while possible, one radix
+// 8, 4 or 2 for the remaining power of two, radix 3 last (so that every
+// stage sees a power-of-two Ns). Returns the number of stages, or -1 if n
+// has another prime factor or more than one factor 3.
 HD int fft_radices(int n, int rad[32]) {
     int k = 0;
-    while (n % 4 == 0) { rad[k++] = 4; n /= 4; }
-    while (n % 2 == 0) { rad[k++] = 2; n /= 2; }
-    while (n % 3 == 0) { rad[k++] = 3; n /= 3; }
-    return n == 1 ? k : -1;
+    int three = 0;
+    if (n % 3 == 0) { n /= 3; three = 1; }
+    if (n % 3 == 0) return -1;
+    while (n % 16 == 0) { rad[k++] = 16; n /= 16; }
+    if (n == 8 || n == 4 || n == 2) { rad[k++] = n; n = 1; }
+    if (n != 1) return -1;
+    if (three) rad[k++] = 3;
+    return k;
 }
 
 // Real FFT of length P = 2M through a complex FFT of length M of the packed
-// pairs z[n] = x[2n] + i x[2n+1] with transform Z. Unnormalised, without the
+// pairs z[n] = x[2n] + i x[2n+1] with transform Z (both in the sw layout). Unnormalised, without the
 // factors 1/2 (they are folded into the kernel spectrum):
 //   X[k] = (Z[k] + conj Z[M-k]) - i W^k (Z[k] - conj Z[M-k]),  W = exp(-2 pi i / P),
 // Z[M] = Z[0]. twP[k] = W^k.
 HD cf r2c_post(const cf* Z, int M, int k, const cf* twP) {
-    cf a = Z[k];
-    cf b = cconj(Z[k == 0 ? 0 : M - k]);
+    cf a = Z[sw(k)];
+    cf b = cconj(Z[sw(k == 0 ? 0 : M - k)]);
     cf e = cadd(a, b);
     cf o = cmul(twP[k], csub(a, b));
     return {e.x + o.y, e.y - o.x};          // e - i o
@@ -118,14 +210,14 @@ HD cf r2c_post(const cf* Z, int M, int k, const cf* twP) {
 //   E = X[k] + conj X[M-k],  O = W^-k (X[k] - conj X[M-k]).
 // W^-(M-k) = -W^k gives Z[M-k] from the same two values.
 HD void c2r_pre_pair(cf* X, int M, int k, const cf* twP) {
-    cf a = X[k], b = X[M - k];
+    cf a = X[sw(k)], b = X[sw(M - k)];
     cf w = twP[k];
     cf e1 = cadd(a, cconj(b));
     cf o1 = cmulc(csub(a, cconj(b)), w);     // (a - conj b) * conj(W^k)
     cf e2 = cadd(b, cconj(a));
     cf o2 = cmul(csub(b, cconj(a)), w);      // (b - conj a) * W^k, times -1 below
-    X[k] = {e1.x - o1.y, e1.y + o1.x};       // e1 + i o1
-    X[M - k] = {e2.x + o2.y, e2.y - o2.x};   // e2 + i (-o2)
+    X[sw(k)] = {e1.x - o1.y, e1.y + o1.x};       // e1 + i o1
+    X[sw(M - k)] = {e2.x + o2.y, e2.y - o2.x};   // e2 + i (-o2)
 }
 
 // k = 0 of the inverse: X[0] real part only (its imaginary part and X[M]

@@ -52,8 +52,10 @@ struct PieceDev {
     // tables (device pointers)
     const SampleEnt* stab;  // [Nx][nj] position and weight of every sample of the piece
     const RadonEnt* rtab;   // [ncol][Ntau] rho position of every output of the piece
-    const int* band_off;    // [nbands+1] offsets of each band's runs in `runs`
-    const int4* runs;       // (trace k, first sample j, count <= 64, 0): samples a band may touch
+    const int* order_s;     // [nbands] bands in decreasing sample work (launch order)
+    const int* order_r;     // [nbands] bands in decreasing output work (launch order)
+    const int* band_off;    // [nbands+1] offsets of each band's chunks in `runs`
+    const int4* runs;       // (trace k, first sample j, count <= 8, 0): samples a band may touch
     const int2* lband;      // [nbands] candidate output-column range of each band
     const float4* colw;     // [ncol] theta tap weights of each column
     const int* colm0;       // [ncol] first theta tap of each column

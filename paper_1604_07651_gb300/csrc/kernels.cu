@@ -30,51 +30,101 @@ __device__ __forceinline__ cf ldcf(const cf* p) {
     float2 v = __ldg(reinterpret_cast<const float2*>(p));
     return {v.x, v.y};
 }
-// Block-cooperative Stockham FFT of `batch` sequences of length n stored
-// back to back in shared memory at a; b is a scratch buffer of the same size.
-// Returns the buffer that holds the result (a or b).
-template <int DIR>
-__device__ cf* block_fft(cf* a, cf* b, int n, int batch, const cf* __restrict__ tw,
-                         const FftPlan& fp) {
-    int Ns = 1;
-    for (int s = 0; s < fp.nst; ++s) {
-        const int R = fp.rad[s];
-        const int nb = n / R;
-        const int total = nb * batch;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int bb = idx / nb;
-            const int j = idx - bb * nb;
-            const cf* in = a + bb * n;
-            cf* out = b + bb * n;
-            if (R == 4)
-                stockham_butterfly<4>(in, out, n, Ns, j, tw, DIR);
-            else if (R == 2)
-                stockham_butterfly<2>(in, out, n, Ns, j, tw, DIR);
-            else
-                stockham_butterfly<3>(in, out, n, Ns, j, tw, DIR);
+// One in-place Stockham stage of radix R over `nrows` sequences of length n
+// stored back to back in shared memory. Every thread first loads the inputs
+// of up to Q butterflies into registers, the block synchronises, then every
+// thread transforms and stores; so the stage can overwrite its own input.
+// Rows are processed in rounds of as many whole rows as blockDim.x * Q
+// butterflies cover (the plan guarantees n / R <= blockDim.x * Q).
+template <int R, int Q, int DIR>
+__device__ __forceinline__ void fft_stage(cf* buf, int n, int nrows, int Ns, int lgNs,
+                                          const cf* __restrict__ tw) {
+    const int nb = n / R;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int per_round = max(1, (nthr * Q) / nb);
+    const float inv_nb = 1.0f / (float)nb;
+    for (int r0 = 0; r0 < nrows; r0 += per_round) {
+        const int items = min(per_round, nrows - r0) * nb;
+        cf v[Q][R];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = tid + q * nthr;
+            if (idx < items) {
+                const int row = (int)(((float)idx + 0.5f) * inv_nb);
+                const int j = idx - row * nb;
+                stockham_load<R>(buf + (size_t)(r0 + row) * n, n, Ns, j, tw, DIR, v[q]);
+            }
         }
         __syncthreads();
-        cf* t = a;
-        a = b;
-        b = t;
-        Ns *= R;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = tid + q * nthr;
+            if (idx < items) {
+                const int row = (int)(((float)idx + 0.5f) * inv_nb);
+                const int j = idx - row * nb;
+                stockham_store<R>(buf + (size_t)(r0 + row) * n, Ns, lgNs, j, DIR, v[q]);
+            }
+        }
+        __syncthreads();
     }
-    return a;
+}
+
+// Block-cooperative in-place FFT of `nrows` sequences of length n
+// (unnormalised; DIR = -1 forward, +1 inverse). The radix plan is radix 16
+// stages, at most one radix 8, 4 or 2 stage, and at most one radix 3 stage
+// (fft_radices); written as straight-line code so that each stage keeps its
+// own small register footprint. Supported: n = 2^a <= 4096 and
+// n = 3 * 2^a <= 6144 with 512 threads.
+template <int DIR>
+__device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* __restrict__ tw,
+                                          const FftPlan& fp) {
+    int Ns = 1, lg = 0;
+    int s = 0;
+    for (; s < fp.nst && fp.rad[s] == 16; ++s) {
+        fft_stage<16, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+        Ns <<= 4;
+        lg += 4;
+    }
+    if (s < fp.nst && fp.rad[s] != 3) {
+        const int R = fp.rad[s];
+        const bool q1 = n / R <= (int)blockDim.x;
+        if (R == 8) {
+            if (q1) fft_stage<8, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+            else fft_stage<8, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        } else if (R == 4) {
+            if (q1) fft_stage<4, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+            else fft_stage<4, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        } else {
+            if (q1) fft_stage<2, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+            else fft_stage<2, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        }
+        Ns *= R;
+        lg = 31 - __clz(Ns);
+        ++s;
+    }
+    if (s < fp.nst) {
+        const int nb = n / 3;
+        if (nb <= (int)blockDim.x) fft_stage<3, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+        else if (nb <= 2 * (int)blockDim.x) fft_stage<3, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        else fft_stage<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);
+    }
 }
 
 // --------------------------------------------------------------------------
 // Row kernels: scatter into a band of lattice rows, then real FFT of the rows.
-// Shared memory: [R][Prho] floats (rows, viewed as [R][M] complex) plus
-// [R][M] complex scratch for the FFT.
+// Shared memory: [R][Prho] floats (rows, viewed as [R][M] complex); the FFT
+// works in place.
 // --------------------------------------------------------------------------
 
 extern __shared__ __align__(16) float smem_f[];
 
-__device__ void rows_r2c_write(const PieceDev& P, int mb, int nrows, cf* __restrict__ spec) {
+// Real sample n of a row buffer (stored as complex pairs in the sw layout).
+__device__ __forceinline__ int swr(int n) { return 2 * sw(n >> 1) + (n & 1); }
+
+__device__ __forceinline__ void rows_r2c_write(const PieceDev& P, int mb, int nrows, cf* __restrict__ spec) {
     const int M = P.Prho / 2;
-    cf* rows = reinterpret_cast<cf*>(smem_f);
-    cf* tmp = rows + P.R * M;
-    cf* Z = block_fft<-1>(rows, tmp, M, nrows, P.twM, P.fftM);
+    cf* Z = reinterpret_cast<cf*>(smem_f);
+    block_fft<-1>(Z, M, nrows, P.twM, P.fftM);
     const int nk = P.k2max + 1;
     const int per_kb = nrows * P.CB;
     const int total = P.nkb * per_kb;
@@ -103,46 +153,71 @@ __device__ __forceinline__ void band_taps(int m0, int n0, int mb, int nrows, int
         const int m = m0 + a - mb;
         if (m < 0 || m >= nrows) continue;
         const float va = val * wt[a];
-        float* row = smem_f + m * Prho + n0;
+        float* row = smem_f + m * Prho;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) atomicAdd(row + c, va * wr[c]);
+        for (int c = 0; c < 4; ++c) atomicAdd(row + swr(n0 + c), va * wr[c]);
     }
 }
 
 // Forward gridding (Eq. (15)) of the gather f[Nx][Nt] for one band of rows.
-// The plan lists, per band, runs of at most 64 consecutive samples of one
-// trace that can reach the band; a warp takes a run, each lane two samples
-// (both loads issued before either is used).
-__device__ __forceinline__ void scatter_sample(const PieceDev& P, int4 e, float fv, int mb, int nrows) {
-    const float w = __int_as_float(e.w);
-    const int m0 = e.x >> 16, n0 = e.x & 0xffff;
-    if (w == 0.f || m0 + 3 < mb || m0 >= mb + nrows) return;
-    float wt[4], wr[4];
-    b3_weights(__int_as_float(e.y), wt);
-    b3_weights(__int_as_float(e.z), wr);
-    band_taps(m0, n0, mb, nrows, P.Prho, fv * w, wt, wr);
+// The plan lists, per band, chunks of at most 8 consecutive samples of one
+// trace that can reach the band; each thread walks one chunk. Neighbouring
+// threads are 8 samples apart, so their 4x4 footprints rarely meet, and a
+// thread sums its samples in registers while their first tap (m0, n0) stays
+// the same, adding to shared memory only when it moves.
+__device__ __forceinline__ void flush_taps(int mn, int mb, int nrows, int Prho, const float acc[16]) {
+    if (mn < 0) return;
+    const int m0 = mn >> 16, n0 = mn & 0xffff;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int m = m0 + a - mb;
+        if (m < 0 || m >= nrows) continue;
+        float* row = smem_f + m * Prho;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) atomicAdd(row + swr(n0 + c), acc[4 * a + c]);
+    }
 }
 
-__global__ void __launch_bounds__(512) k_scatter_samples(PieceDev P, const float* __restrict__ f,
+__global__ void __launch_bounds__(512, 2) k_scatter_samples(const __grid_constant__ PieceDev P, const float* __restrict__ f,
                                                          cf* __restrict__ spec) {
-    const int mb = blockIdx.x * P.R;
+    const int band = __ldg(P.order_s + blockIdx.x);   // heaviest bands first
+    const int mb = band * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     zero_rows(P);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int r0 = __ldg(P.band_off + blockIdx.x), r1 = __ldg(P.band_off + blockIdx.x + 1);
-    for (int r = r0 + warp; r < r1; r += nw) {
-        const int4 run = __ldg(P.runs + r);
-        const int k = run.x, j = run.y + lane, n = run.z;
-        const int4* st = reinterpret_cast<const int4*>(P.stab + (size_t)k * P.nj - P.jt_lo);
-        const float* fk = f + (size_t)k * P.Nt;
-        const bool a = lane < n, b = lane + 32 < n;
-        int4 e0 = make_int4(0, 0, 0, 0), e1 = e0;
-        float f0 = 0.f, f1 = 0.f;
-        if (a) { e0 = __ldg(st + j); f0 = __ldg(fk + j); }
-        if (b) { e1 = __ldg(st + j + 32); f1 = __ldg(fk + j + 32); }
-        if (a) scatter_sample(P, e0, f0, mb, nrows);
-        if (b) scatter_sample(P, e1, f1, mb, nrows);
+    const int c0 = __ldg(P.band_off + band), c1 = __ldg(P.band_off + band + 1);
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const int4 ch = __ldg(P.runs + c);                 // (trace, first sample, count)
+        const int4* st = reinterpret_cast<const int4*>(P.stab + (size_t)ch.x * P.nj - P.jt_lo) + ch.y;
+        const float* fk = f + (size_t)ch.x * P.Nt + ch.y;
+        float acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+        int cur = -1;
+#pragma unroll 1
+        for (int t = 0; t < ch.z; ++t) {
+            const int4 e = __ldg(st + t);
+            const float w = __int_as_float(e.w);
+            const int m0 = e.x >> 16;
+            if (w == 0.f || m0 + 3 < mb || m0 >= mb + nrows) continue;
+            if (e.x != cur) {
+                flush_taps(cur, mb, nrows, P.Prho, acc);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+                cur = e.x;
+            }
+            float wt[4], wr[4];
+            b3_weights(__int_as_float(e.y), wt);
+            b3_weights(__int_as_float(e.z), wr);
+            const float v = __ldg(fk + t) * w;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float va = v * wt[a];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[4 * a + q] = fmaf(va, wr[q], acc[4 * a + q]);
+            }
+        }
+        flush_taps(cur, mb, nrows, P.Prho, acc);
     }
     __syncthreads();
     rows_r2c_write(P, mb, nrows, spec);
@@ -184,14 +259,14 @@ __device__ __forceinline__ void scatter_column_group(int2 e, float v, int m0, co
     const int knext = __shfl_down_sync(FULL, key, 1);
     const bool tail = lane == 31 || knext != key;
     if (valid && tail) {
-        const float sw[4] = {s0, s1, s2, s3};
+        const float sv[4] = {s0, s1, s2, s3};
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int m = m0 + a - mb;
             if (m < 0 || m >= nrows) continue;
-            float* row = smem_f + m * Prho + e.x;
+            float* row = smem_f + m * Prho;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) atomicAdd(row + c, wt[a] * sw[c]);
+            for (int c = 0; c < 4; ++c) atomicAdd(row + swr(e.x + c), wt[a] * sv[c]);
         }
     }
 }
@@ -199,14 +274,15 @@ __device__ __forceinline__ void scatter_column_group(int2 e, float v, int m0, co
 // Adjoint of the output interpolation: scatter g[Nq][Ntau] of this slowness
 // piece's columns onto one band of rows (transpose of Eq. (17)). Work items
 // are (column, block of 64 intercept times), two groups of 32 per item.
-__global__ void __launch_bounds__(512) k_scatter_radon(PieceDev P, const float* __restrict__ g,
+__global__ void __launch_bounds__(512, 2) k_scatter_radon(const __grid_constant__ PieceDev P, const float* __restrict__ g,
                                                        cf* __restrict__ spec) {
-    const int mb = blockIdx.x * P.R;
+    const int band = __ldg(P.order_r + blockIdx.x);   // heaviest bands first
+    const int mb = band * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     zero_rows(P);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int2 lr = __ldg(P.lband + blockIdx.x);
+    const int2 lr = __ldg(P.lband + band);
     const int nblk = (P.Ntau + 63) >> 6;
     const int items = lr.y >= lr.x ? (lr.y - lr.x + 1) * nblk : 0;
     for (int it = warp; it < items; it += nw) {
@@ -235,54 +311,55 @@ __global__ void __launch_bounds__(512) k_scatter_radon(PieceDev P, const float* 
 // One block of CB spectrum columns per CTA; the blocked layout
 // [kb][m][CB] makes every load and store contiguous.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_colconv(PieceDev P, const cf* __restrict__ in,
+__global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ PieceDev P, const cf* __restrict__ in,
                                                  cf* __restrict__ out, int adjoint) {
     const int kb = blockIdx.x;
     const int CB = P.CB, Pt = P.Ptheta, Nth = P.Ntheta;
     cf* A = reinterpret_cast<cf*>(smem_f);
-    cf* B = A + CB * Pt;
     const cf* src = in + (size_t)kb * Nth * CB;
     if (CB == 2) {
         // one 16-byte load per lattice row: both columns of the block
         for (int m = threadIdx.x; m < Pt; m += blockDim.x) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (m < Nth) v = __ldg(reinterpret_cast<const float4*>(src) + m);
-            A[m] = {v.x, v.y};
-            A[Pt + m] = {v.z, v.w};
+            A[sw(m)] = {v.x, v.y};
+            A[Pt + sw(m)] = {v.z, v.w};
         }
     } else {
         for (int idx = threadIdx.x; idx < Pt * CB; idx += blockDim.x) {
             const int m = idx / CB, c = idx - m * CB;
-            A[c * Pt + m] = m < Nth ? ldcf(src + idx) : cf{0.f, 0.f};
+            A[c * Pt + sw(m)] = m < Nth ? ldcf(src + idx) : cf{0.f, 0.f};
         }
     }
     __syncthreads();
-    cf* X = block_fft<-1>(A, B, Pt, CB, P.twT, P.fftT);
-    cf* Y = (X == A) ? B : A;
+    block_fft<-1>(A, Pt, CB, P.twT, P.fftT);
+    cf* X = A;
     const int k1n = P.k1max + 1;
     const cf* Kb = P.K + (size_t)kb * k1n * CB;
     for (int idx = threadIdx.x; idx < Pt * CB; idx += blockDim.x) {
         const int c = idx / Pt, k1 = idx - c * Pt;
         const int kk = k1 <= Pt / 2 ? k1 : Pt - k1;
+        const int pidx = c * Pt + sw(k1);
         cf v = {0.f, 0.f};
         if (kk < k1n) {
             const cf kv = ldcf(Kb + kk * CB + c);
-            v = adjoint ? cmulc(X[idx], kv) : cmul(X[idx], kv);
+            v = adjoint ? cmulc(X[pidx], kv) : cmul(X[pidx], kv);
         }
-        X[idx] = v;
+        X[pidx] = v;
     }
     __syncthreads();
-    cf* Zr = block_fft<+1>(X, Y, Pt, CB, P.twT, P.fftT);
+    block_fft<+1>(X, Pt, CB, P.twT, P.fftT);
+    const cf* Zr = X;
     cf* dst = out + (size_t)kb * Nth * CB;
     if (CB == 2) {
         for (int m = threadIdx.x; m < Nth; m += blockDim.x) {
-            const cf a = Zr[m], b = Zr[Pt + m];
+            const cf a = Zr[sw(m)], b = Zr[Pt + sw(m)];
             reinterpret_cast<float4*>(dst)[m] = make_float4(a.x, a.y, b.x, b.y);
         }
     } else {
         for (int idx = threadIdx.x; idx < Nth * CB; idx += blockDim.x) {
             const int m = idx / CB, c = idx - m * CB;
-            dst[idx] = Zr[c * Pt + m];
+            dst[idx] = Zr[c * Pt + sw(m)];
         }
     }
 }
@@ -291,18 +368,17 @@ __global__ void __launch_bounds__(512) k_colconv(PieceDev P, const cf* __restric
 // Inverse real FFT of a band of rows from the half spectrum (bins <= k2max,
 // the rest zero) into the real lattice P.lat[Ntheta][Nrho].
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_rows_c2r(PieceDev P, const cf* __restrict__ spec) {
+__global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ PieceDev P, const cf* __restrict__ spec) {
     const int mb = blockIdx.x * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int M = P.Prho / 2;
     cf* X = reinterpret_cast<cf*>(smem_f);
-    cf* tmp = X + P.R * M;
     const int nk = P.k2max + 1;
     // zero the bins above k2max, then copy the stored ones in the blocked
     // layout's order (contiguous rows of the band for each column block)
     for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
         const int m = idx / M, k = idx - m * M;
-        if (k >= nk) X[idx] = cf{0.f, 0.f};
+        if (k >= nk) X[m * M + sw(k)] = cf{0.f, 0.f};
     }
     const int per_kb = nrows * P.CB;
     for (int idx = threadIdx.x; idx < P.nkb * per_kb; idx += blockDim.x) {
@@ -310,7 +386,7 @@ __global__ void __launch_bounds__(512) k_rows_c2r(PieceDev P, const cf* __restri
         const int rem = idx - kb * per_kb;
         const int m = rem / P.CB, c = rem - m * P.CB;
         const int k = kb * P.CB + c;
-        if (k < nk) X[m * M + k] = ldcf(spec + ((size_t)kb * P.Ntheta + mb) * P.CB + rem);
+        if (k < nk) X[m * M + sw(k)] = ldcf(spec + ((size_t)kb * P.Ntheta + mb) * P.CB + rem);
     }
     __syncthreads();
     const int half = M / 2;
@@ -323,11 +399,12 @@ __global__ void __launch_bounds__(512) k_rows_c2r(PieceDev P, const cf* __restri
             c2r_pre_pair(row, M, k, P.twP);
     }
     __syncthreads();
-    cf* z = block_fft<+1>(X, tmp, M, nrows, P.twM, P.fftM);
+    block_fft<+1>(X, M, nrows, P.twM, P.fftM);
+    const cf* z = X;
     const int Nr = P.Nrho;
     for (int idx = threadIdx.x; idx < nrows * Nr; idx += blockDim.x) {
         const int m = idx / Nr, n = idx - m * Nr;
-        const cf v = z[m * M + (n >> 1)];
+        const cf v = z[m * M + sw(n >> 1)];
         P.lat[(size_t)(mb + m) * Nr + n] = (n & 1) ? v.y : v.x;
     }
 }
@@ -574,11 +651,11 @@ static int check_launch() {
 }
 
 size_t scatter_smem_bytes(const PieceDev& P) {
-    return (size_t)2 * P.R * P.Prho * sizeof(float);
+    return (size_t)P.R * P.Prho * sizeof(float);
 }
 
 size_t colconv_smem_bytes(const PieceDev& P) {
-    return (size_t)2 * P.CB * P.Ptheta * sizeof(cf);
+    return (size_t)P.CB * P.Ptheta * sizeof(cf);
 }
 
 int max_smem_optin() {

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -505,14 +506,27 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.Prho = h.Prho;
     P.k1max = h.k1max;
     P.k2max = h.k2max;
-    // rows per band and spectrum columns per block, bounded by shared memory
-    int R = 4;
-    while (R > 1 && (size_t)2 * R * h.Prho * sizeof(float) > (size_t)smem_max) --R;
-    if ((size_t)2 * R * h.Prho * sizeof(float) > (size_t)smem_max)
-        return fail(RADON_ERR_UNSUPPORTED, "row FFT length too large for shared memory");
+    // FFT lengths the in-place block FFT handles (512 threads): 2^a <= 4096, 3 * 2^a <= 6144
+    auto fft_ok = [](int n) { return (n % 3 == 0) ? n <= 6144 : n <= 4096; };
+    if (!fft_ok(h.Prho / 2) || !fft_ok(h.Ptheta))
+        return fail(RADON_ERR_UNSUPPORTED,
+                    "FFT length " + std::to_string(std::max(h.Prho / 2, h.Ptheta)) +
+                        " above the block FFT's limit (4096, or 6144 = 3*2048)");
+    // rows per band: 3 (more rows mean fewer, longer CTAs and worse balance;
+    // fewer mean more duplicated samples; 3 measured best on 2048^2 gathers)
+    int R = (int)std::min<size_t>(3, (size_t)smem_max / (h.Prho * sizeof(float)));
+    if (const char* env = std::getenv("HRADON_ROWS_PER_BAND")) {   // tuning knob
+        const int r = std::atoi(env);
+        if (r >= 1 && (size_t)r * h.Prho * sizeof(float) <= (size_t)smem_max) R = r;
+    }
+    if (R < 1) {
+        R = 1;
+        if ((size_t)h.Prho * sizeof(float) > (size_t)smem_max)
+            return fail(RADON_ERR_UNSUPPORTED, "row FFT length too large for shared memory");
+    }
     int CB = 2;
-    while (CB > 1 && (size_t)2 * CB * h.Ptheta * sizeof(cf) > (size_t)smem_max) --CB;
-    if ((size_t)2 * CB * h.Ptheta * sizeof(cf) > (size_t)smem_max)
+    while (CB > 1 && (size_t)CB * h.Ptheta * sizeof(cf) > (size_t)smem_max) --CB;
+    if ((size_t)CB * h.Ptheta * sizeof(cf) > (size_t)smem_max)
         return fail(RADON_ERR_UNSUPPORTED, "column FFT length too large for shared memory");
     P.R = R;
     P.CB = CB;
@@ -568,17 +582,25 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
             }
         }
     }
-    // runs of at most 64 samples of one trace, grouped by band
+    // chunks of at most 8 samples of one trace, grouped by band
     std::vector<int> band_off(P.nbands + 1, 0);
     std::vector<int4> runs;
     for (int b = 0; b < P.nbands; ++b) {
         band_off[b] = (int)runs.size();
         for (int k = 0; k < d.Nx; ++k) {
             const int2 r = jband[(size_t)b * d.Nx + k];
-            for (int j = r.x; j <= r.y; j += 64) runs.push_back(int4{k, j, std::min(64, r.y - j + 1), 0});
+            for (int j = r.x; j <= r.y; j += 8) runs.push_back(int4{k, j, std::min(8, r.y - j + 1), 0});
         }
     }
     band_off[P.nbands] = (int)runs.size();
+    // launch order: bands with the most samples first (the heaviest CTAs set
+    // the kernel's duration, so they should not start last)
+    std::vector<long> work_s(P.nbands, 0);
+    for (int b = 0; b < P.nbands; ++b)
+        for (int r = band_off[b]; r < band_off[b + 1]; ++r) work_s[b] += runs[r].z;
+    std::vector<int> order_s(P.nbands);
+    for (int b = 0; b < P.nbands; ++b) order_s[b] = b;
+    std::stable_sort(order_s.begin(), order_s.end(), [&](int x, int y) { return work_s[x] > work_s[y]; });
     // output columns: theta taps, scale, e^rho polynomial; band column ranges
     const std::vector<double> q = q_grid(d);
     const int ncol = h.l_hi - h.l_lo + 1;
@@ -617,6 +639,13 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
             }
         }
     }
+    std::vector<int> order_r(P.nbands);
+    for (int b = 0; b < P.nbands; ++b) order_r[b] = b;
+    std::stable_sort(order_r.begin(), order_r.end(), [&](int x, int y) {
+        const int wx = lband[x].y >= lband[x].x ? lband[x].y - lband[x].x + 1 : 0;
+        const int wy = lband[y].y >= lband[y].x ? lband[y].y - lband[y].x + 1 : 0;
+        return wx > wy;
+    });
     // twiddles
     const int M = h.Prho / 2;
     std::vector<cf> twM(M), twP(M + 1), twT(h.Ptheta);
@@ -631,6 +660,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
 
     radon_status s = RADON_OK;
     if ((s = dev_upload(p, band_off, &P.band_off)) || (s = dev_upload(p, runs, &P.runs)) ||
+        (s = dev_upload(p, order_s, &P.order_s)) || (s = dev_upload(p, order_r, &P.order_r)) ||
         (s = dev_upload(p, lband, &P.lband)) ||
         (s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
         (s = dev_upload(p, colscale, &P.colscale)) || (s = dev_upload(p, K, &P.K)) ||

@@ -19,24 +19,43 @@ static std::vector<cf> twiddles(int n) {
     return t;
 }
 
-// The device driver's stage loop, run sequentially.
-static std::vector<cf> fft_emul(std::vector<cf> a, int dir) {
+// The device driver's stage loop, run sequentially, on natural-order data
+// (converted to and from the swizzled shared-memory layout).
+static std::vector<cf> to_sw(const std::vector<cf>& x) {
+    std::vector<cf> y(x.size());
+    for (size_t i = 0; i < x.size(); ++i) y[sw((int)i)] = x[i];
+    return y;
+}
+static std::vector<cf> from_sw(const std::vector<cf>& y) {
+    std::vector<cf> x(y.size());
+    for (size_t i = 0; i < y.size(); ++i) x[i] = y[sw((int)i)];
+    return x;
+}
+
+static std::vector<cf> fft_emul_sw(std::vector<cf> a, int dir) {
     const int n = (int)a.size();
     int rad[32];
     const int nst = fft_radices(n, rad);
     std::vector<cf> b(n), tw = twiddles(n);
-    int Ns = 1;
+    int Ns = 1, lg = 0;
     for (int s = 0; s < nst; ++s) {
         const int R = rad[s];
         for (int j = 0; j < n / R; ++j) {
-            if (R == 4) stockham_butterfly<4>(a.data(), b.data(), n, Ns, j, tw.data(), dir);
-            else if (R == 2) stockham_butterfly<2>(a.data(), b.data(), n, Ns, j, tw.data(), dir);
-            else stockham_butterfly<3>(a.data(), b.data(), n, Ns, j, tw.data(), dir);
+            if (R == 16) stockham_butterfly<16>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
+            else if (R == 8) stockham_butterfly<8>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
+            else if (R == 4) stockham_butterfly<4>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
+            else if (R == 2) stockham_butterfly<2>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
+            else stockham_butterfly<3>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
         }
         std::swap(a, b);
         Ns *= R;
+        while ((1 << lg) < Ns) ++lg;
     }
     return a;
+}
+
+static std::vector<cf> fft_emul(const std::vector<cf>& a, int dir) {
+    return from_sw(fft_emul_sw(to_sw(a), dir));
 }
 
 static double fft_error(int n, int dir, std::mt19937& rng) {
@@ -67,7 +86,7 @@ static double rfft_error(int P, std::mt19937& rng) {
     for (auto& v : x) v = N(rng);
     std::vector<cf> z(M);
     for (int n = 0; n < M; ++n) z[n] = {(float)x[2 * n], (float)x[2 * n + 1]};
-    std::vector<cf> Z = fft_emul(z, -1);
+    std::vector<cf> Z = fft_emul_sw(to_sw(z), -1);
     std::vector<cf> twP(M + 1);
     for (int k = 0; k <= M; ++k) twP[k] = {(float)std::cos(-2 * M_PI * k / P), (float)std::sin(-2 * M_PI * k / P)};
     double num = 0, den = 0;
@@ -92,9 +111,10 @@ static double irfft_error(int P, int kmax, std::mt19937& rng) {
     for (int k = 0; k < M; ++k) X[k] = {(float)Xd[k].real(), (float)Xd[k].imag()};
     std::vector<cf> twP(M + 1);
     for (int k = 0; k <= M; ++k) twP[k] = {(float)std::cos(-2 * M_PI * k / P), (float)std::sin(-2 * M_PI * k / P)};
+    X = to_sw(X);
     X[0] = c2r_pre_dc(X[0]);
     for (int k = 1; k <= M / 2; ++k) c2r_pre_pair(X.data(), M, k, twP.data());
-    std::vector<cf> z = fft_emul(X, +1);
+    std::vector<cf> z = from_sw(fft_emul_sw(X, +1));
     double num = 0, den = 0;
     for (int n = 0; n < P; ++n) {
         double acc = Xd[0].real();
@@ -125,16 +145,28 @@ static double b3_error() {
 int main() {
     std::mt19937 rng(1604);
     double e = 0;
-    for (int n : {2, 3, 4, 6, 8, 12, 16, 24, 64, 96, 384, 512, 1536, 2048})
+    for (int n : {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 384, 512, 1024, 1536, 2048, 3072, 4096})
         e = std::max(e, std::max(fft_error(n, -1, rng), fft_error(n, +1, rng)));
     std::printf("fft_rel_l2 %.3e\n", e);
     e = 0;
-    for (int P : {8, 12, 64, 96, 768, 1024}) e = std::max(e, rfft_error(P, rng));
+    for (int P : {8, 12, 48, 64, 96, 768, 1024, 3072}) e = std::max(e, rfft_error(P, rng));
     std::printf("rfft_rel_l2 %.3e\n", e);
     e = 0;
-    for (int P : {8, 12, 64, 96, 768, 1024}) e = std::max(e, irfft_error(P, P / 2 - 1, rng));
+    for (int P : {8, 12, 48, 64, 96, 768, 1024, 3072}) e = std::max(e, irfft_error(P, P / 2 - 1, rng));
     for (int P : {64, 768}) e = std::max(e, irfft_error(P, P / 5, rng));
     std::printf("irfft_rel_l2 %.3e\n", e);
     std::printf("b3_weights %.3e\n", b3_error());
+    // the layout swizzle is a permutation of [0, n) for every FFT length used
+    int bad = 0;
+    for (int n = 1; n <= 6144; ++n) {
+        int rad[32];
+        if (fft_radices(n, rad) < 0 || (n % 3 == 0 ? n > 6144 : n > 4096)) continue;
+        std::vector<int> seen(n, 0);
+        for (int i = 0; i < n; ++i) {
+            const int p = sw(i);
+            if (p < 0 || p >= n || seen[p]++) ++bad;
+        }
+    }
+    std::printf("swizzle_violations %d\n", bad);
     return 0;
 }

@@ -33,3 +33,7 @@ def test_real_fft_packing(results):
 
 def test_b3_weights(results):
     assert results["b3_weights"] < 1e-6
+
+
+def test_shared_memory_swizzle_is_a_permutation(results):
+    assert results["swizzle_violations"] == 0
