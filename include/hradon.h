@@ -176,12 +176,13 @@ radon_status radon_direct_adj(const float* g, float* f, int Nt, int Nx, int Ntau
 /*
  * Per-stage timing (off by default). While enabled, every kernel launch of
  * radon_fwd / radon_adj is bracketed by CUDA events recorded on the launch
- * stream. Stages: 0 gridding + row FFT (forward), 1 column FFT*K*IFFT
- * (forward), 2 inverse row FFT (forward), 3 output interpolation (forward),
- * 4 output scatter + row FFT (adjoint), 5 column FFT*conj(K)*IFFT (adjoint),
- * 6 inverse row FFT (adjoint), 7 gather of the samples (adjoint).
+ * stream. Stages: 0 gridding (forward), 1 row FFT (forward), 2 column
+ * FFT*K*IFFT (forward), 3 inverse row FFT (forward), 4 output interpolation
+ * (forward), 5 output scatter + row FFT (adjoint), 6 column
+ * FFT*conj(K)*IFFT (adjoint), 7 inverse row FFT (adjoint), 8 gather of the
+ * samples (adjoint).
  */
-#define RADON_NSTAGES 8
+#define RADON_NSTAGES 9
 radon_status radon_plan_set_profiling(radon_plan p, int enable);
 
 /*

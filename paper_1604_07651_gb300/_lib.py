@@ -7,8 +7,8 @@ import os
 from . import build as _build
 
 MAX_TSPLIT = 8
-NSTAGES = 8
-STAGE_NAMES = ["grid_rowfft_fwd", "colconv_fwd", "rows_c2r_fwd", "interp_fwd",
+NSTAGES = 9
+STAGE_NAMES = ["grid_fwd", "rows_r2c_fwd", "colconv_fwd", "rows_c2r_fwd", "interp_fwd",
                "scatter_rowfft_adj", "colconv_adj", "rows_c2r_adj", "gather_adj"]
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 

@@ -52,10 +52,11 @@ struct PieceDev {
     // tables (device pointers)
     const SampleEnt* stab;  // [Nx][nj] position and weight of every sample of the piece
     const RadonEnt* rtab;   // [ncol][Ntau] rho position of every output of the piece
-    const int* order_s;     // [nbands] bands in decreasing sample work (launch order)
+    int ntr, ntc;           // lattice tiles of the forward gridding: rows, columns
+    int nunits;             // work units of the forward gridding
+    const int4* units;      // (tile, first chunk, end chunk, 0), heaviest first
+    const int4* chunks;     // (trace k, first sample j, count <= 8, 0), grouped by tile
     const int* order_r;     // [nbands] bands in decreasing output work (launch order)
-    const int* band_off;    // [nbands+1] offsets of each band's chunks in `runs`
-    const int4* runs;       // (trace k, first sample j, count <= 8, 0): samples a band may touch
     const int2* lband;      // [nbands] candidate output-column range of each band
     const float4* colw;     // [ncol] theta tap weights of each column
     const int* colm0;       // [ncol] first theta tap of each column
@@ -69,8 +70,13 @@ struct PieceDev {
     float* lat;             // [Ntheta][Nrho] real lattice (Q forward, G' adjoint)
 };
 
+// Lattice tile of the forward gridding (rows x columns of cells).
+constexpr int kTileRows = 16;
+constexpr int kTileCols = 128;
+
 // Launchers (kernels.cu)
-int launch_scatter_gather_rows(const PieceDev& P, const float* f, cf* spec, void* stream);
+int launch_grid_tiles(const PieceDev& P, const float* f, void* stream);
+int launch_rows_r2c(const PieceDev& P, cf* spec, void* stream);
 int launch_scatter_radon_rows(const PieceDev& P, const float* g, cf* spec, void* stream);
 int launch_colconv(const PieceDev& P, const cf* in, cf* out, int adjoint, void* stream);
 int launch_rows_c2r(const PieceDev& P, const cf* spec, void* stream);

@@ -2,10 +2,10 @@
 // direct-summation comparator.
 //
 // Forward, per sub-problem (Sections 2-4):
-//   k_scatter_samples  gridding of the gather samples onto the log-polar
-//                      lattice with cubic B-splines (Eq. (14)-(15)), one band
-//                      of lattice rows per CTA in shared memory, fused with the
-//                      real FFT of those rows (first half of Eq. (7)/(16));
+//   k_grid_tiles       gridding of the gather samples onto the log-polar
+//                      lattice with cubic B-splines (Eq. (14)-(15)), one tile
+//                      of lattice cells per CTA in shared memory;
+//   k_rows_r2c         real FFT of the lattice rows (first half of Eq. (7)/(16));
 //   k_colconv          FFT along theta, product with the kernel spectrum
 //                      chi_L zeta_hat / B3_hat^2 (Eq. (16)-(17)), inverse FFT;
 //   k_rows_c2r         inverse real FFT of the rows -> B-spline coefficients;
@@ -159,35 +159,41 @@ __device__ __forceinline__ void band_taps(int m0, int n0, int mb, int nrows, int
     }
 }
 
-// Forward gridding (Eq. (15)) of the gather f[Nx][Nt] for one band of rows.
-// The plan lists, per band, chunks of at most 8 consecutive samples of one
-// trace that can reach the band; each thread walks one chunk. Neighbouring
-// threads are 8 samples apart, so their 4x4 footprints rarely meet, and a
-// thread sums its samples in registers while their first tap (m0, n0) stays
-// the same, adding to shared memory only when it moves.
-__device__ __forceinline__ void flush_taps(int mn, int mb, int nrows, int Prho, const float acc[16]) {
+// Forward gridding (Eq. (15)) of the gather f[Nx][Nt] onto the lattice
+// P.lat (zeroed before). The plan lists, per tile of kTileRows x kTileCols
+// cells, chunks of at most 8 consecutive samples of one trace whose 4x4
+// footprint meets the tile, and cuts every tile's list into work units of at
+// most 256 chunks (sample density varies by two orders of magnitude over the
+// lattice, so units, not tiles, balance the CTAs). A CTA takes one unit, each
+// thread walks one chunk: neighbouring threads are 8 samples apart, so their
+// footprints rarely meet, and a thread sums its samples in registers while
+// their first tap (m0, n0) stays the same, adding to the shared tile only when
+// it moves. The tile's touched cells are then added to P.lat.
+__device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, float* tile, const float acc[16]) {
     if (mn < 0) return;
-    const int m0 = mn >> 16, n0 = mn & 0xffff;
+    const int m0 = (mn >> 16) - m_lo, n0 = (mn & 0xffff) - n_lo;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int m = m0 + a - mb;
-        if (m < 0 || m >= nrows) continue;
-        float* row = smem_f + m * Prho;
+        const int m = m0 + a;
+        if (m < 0 || m >= kTileRows) continue;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) atomicAdd(row + swr(n0 + c), acc[4 * a + c]);
+        for (int c = 0; c < 4; ++c) {
+            const int n = n0 + c;
+            if (n >= 0 && n < kTileCols) atomicAdd(tile + m * kTileCols + n, acc[4 * a + c]);
+        }
     }
 }
 
-__global__ void __launch_bounds__(512, 2) k_scatter_samples(const __grid_constant__ PieceDev P, const float* __restrict__ f,
-                                                         cf* __restrict__ spec) {
-    const int band = __ldg(P.order_s + blockIdx.x);   // heaviest bands first
-    const int mb = band * P.R;
-    const int nrows = min(P.R, P.Ntheta - mb);
-    zero_rows(P);
+__global__ void __launch_bounds__(256) k_grid_tiles(const __grid_constant__ PieceDev P,
+                                                    const float* __restrict__ f) {
+    __shared__ float tile[kTileRows * kTileCols];
+    const int4 u = __ldg(P.units + blockIdx.x);           // (tile, first chunk, end chunk)
+    const int ti = u.x / P.ntc, tj = u.x - ti * P.ntc;
+    const int m_lo = ti * kTileRows, n_lo = tj * kTileCols;
+    for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) tile[i] = 0.f;
     __syncthreads();
-    const int c0 = __ldg(P.band_off + band), c1 = __ldg(P.band_off + band + 1);
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        const int4 ch = __ldg(P.runs + c);                 // (trace, first sample, count)
+    for (int c = u.y + threadIdx.x; c < u.z; c += blockDim.x) {
+        const int4 ch = __ldg(P.chunks + c);               // (trace, first sample, count)
         const int4* st = reinterpret_cast<const int4*>(P.stab + (size_t)ch.x * P.nj - P.jt_lo) + ch.y;
         const float* fk = f + (size_t)ch.x * P.Nt + ch.y;
         float acc[16];
@@ -195,13 +201,12 @@ __global__ void __launch_bounds__(512, 2) k_scatter_samples(const __grid_constan
         for (int q = 0; q < 16; ++q) acc[q] = 0.f;
         int cur = -1;
 #pragma unroll 1
-        for (int t = 0; t < ch.z; ++t) {
-            const int4 e = __ldg(st + t);
+        for (int s = 0; s < ch.z; ++s) {
+            const int4 e = __ldg(st + s);
             const float w = __int_as_float(e.w);
-            const int m0 = e.x >> 16;
-            if (w == 0.f || m0 + 3 < mb || m0 >= mb + nrows) continue;
+            if (w == 0.f) continue;
             if (e.x != cur) {
-                flush_taps(cur, mb, nrows, P.Prho, acc);
+                flush_tile(cur, m_lo, n_lo, tile, acc);
 #pragma unroll
                 for (int q = 0; q < 16; ++q) acc[q] = 0.f;
                 cur = e.x;
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(512, 2) k_scatter_samples(const __grid_constan
             float wt[4], wr[4];
             b3_weights(__int_as_float(e.y), wt);
             b3_weights(__int_as_float(e.z), wr);
-            const float v = __ldg(fk + t) * w;
+            const float v = __ldg(fk + s) * w;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const float va = v * wt[a];
@@ -217,7 +222,26 @@ __global__ void __launch_bounds__(512, 2) k_scatter_samples(const __grid_constan
                 for (int q = 0; q < 4; ++q) acc[4 * a + q] = fmaf(va, wr[q], acc[4 * a + q]);
             }
         }
-        flush_taps(cur, mb, nrows, P.Prho, acc);
+        flush_tile(cur, m_lo, n_lo, tile, acc);
+    }
+    __syncthreads();
+    const int nr = min(kTileRows, P.Ntheta - m_lo), nc = min(kTileCols, P.Nrho - n_lo);
+    for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
+        const int m = i / kTileCols, n = i - m * kTileCols;
+        const float v = tile[i];
+        if (v != 0.f && m < nr && n < nc) atomicAdd(P.lat + (size_t)(m_lo + m) * P.Nrho + n_lo + n, v);
+    }
+}
+
+// Real FFT of a band of lattice rows (P.lat, zero-padded to Prho) into the
+// half spectrum (first half of Eq. (7)/(16)).
+__global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ PieceDev P, cf* __restrict__ spec) {
+    const int mb = blockIdx.x * P.R;
+    const int nrows = min(P.R, P.Ntheta - mb);
+    const int Pr = P.Prho, Nr = P.Nrho;
+    for (int idx = threadIdx.x; idx < nrows * Pr; idx += blockDim.x) {
+        const int m = idx / Pr, n = idx - m * Pr;
+        smem_f[m * Pr + swr(n)] = n < Nr ? P.lat[(size_t)(mb + m) * Nr + n] : 0.f;
     }
     __syncthreads();
     rows_r2c_write(P, mb, nrows, spec);
@@ -670,10 +694,17 @@ static int set_smem(const void* fn, size_t bytes) {
     return e == cudaSuccess ? 0 : (int)e;
 }
 
-int launch_scatter_gather_rows(const PieceDev& P, const float* f, cf* spec, void* stream) {
+int launch_grid_tiles(const PieceDev& P, const float* f, void* stream) {
+    cudaError_t e = cudaMemsetAsync(P.lat, 0, (size_t)P.Ntheta * P.Nrho * sizeof(float), (cudaStream_t)stream);
+    if (e != cudaSuccess) return (int)e;
+    if (P.nunits > 0) k_grid_tiles<<<P.nunits, 256, 0, (cudaStream_t)stream>>>(P, f);
+    return check_launch();
+}
+
+int launch_rows_r2c(const PieceDev& P, cf* spec, void* stream) {
     const size_t sm = scatter_smem_bytes(P);
-    if (int e = set_smem((const void*)k_scatter_samples, sm)) return e;
-    k_scatter_samples<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, f, spec);
+    if (int e = set_smem((const void*)k_rows_r2c, sm)) return e;
+    k_rows_r2c<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, spec);
     return check_launch();
 }
 

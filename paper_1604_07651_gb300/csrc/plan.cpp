@@ -494,6 +494,66 @@ radon_status kernel_spectrum(radon_plan_s* p, const HostPiece& h, int CB, int nk
     return RADON_OK;
 }
 
+// Tile lists of the forward gridding, built from the device's own position
+// table (copied back once) so that membership matches the kernel exactly:
+// for every tile, the chunks of at most 8 consecutive samples of one trace
+// whose 4x4 footprint meets it (along a trace the footprint moves
+// monotonically, so each trace meets a tile in one run of samples).
+radon_status build_tile_lists(radon_plan_s* p, const HostPiece& h, PieceDev& P) {
+    const int TR = kTileRows, TC = kTileCols;
+    P.ntr = (h.Ntheta + TR - 1) / TR;
+    P.ntc = (h.Nrho + TC - 1) / TC;
+    const int ntiles = P.ntr * P.ntc;
+    std::vector<SampleEnt> tab((size_t)P.nj * P.Nx);
+    if (cudaMemcpy(tab.data(), P.stab, tab.size() * sizeof(SampleEnt), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(RADON_ERR_CUDA, "reading back the position table failed");
+    std::vector<std::vector<int4>> runs(ntiles);
+    std::vector<int> last_k(ntiles, -1), last_j(ntiles, -2);
+    for (int k = 0; k < P.Nx; ++k) {
+        for (int jl = 0; jl < P.nj; ++jl) {
+            const SampleEnt& e = tab[(size_t)k * P.nj + jl];
+            if (e.w == 0.f) continue;
+            const int m0 = e.mn >> 16, n0 = e.mn & 0xffff;
+            const int j = P.jt_lo + jl;
+            for (int ti = m0 / TR; ti <= (m0 + 3) / TR && ti < P.ntr; ++ti)
+                for (int tj = n0 / TC; tj <= (n0 + 3) / TC && tj < P.ntc; ++tj) {
+                    const int t = ti * P.ntc + tj;
+                    if (last_k[t] == k && last_j[t] == j - 1 && runs[t].back().z < 8) {
+                        runs[t].back().z += 1;
+                    } else {
+                        runs[t].push_back(int4{k, j, 1, 0});
+                    }
+                    last_k[t] = k;
+                    last_j[t] = j;
+                }
+        }
+    }
+    // work units: every tile's chunks cut into pieces of at most 256 chunks
+    const int kUnit = 256;
+    std::vector<int4> flat, units;
+    std::vector<long> uwork;
+    for (int t = 0; t < ntiles; ++t) {
+        const int base = (int)flat.size();
+        flat.insert(flat.end(), runs[t].begin(), runs[t].end());
+        for (int c = 0; c < (int)runs[t].size(); c += kUnit) {
+            const int e = std::min((int)runs[t].size(), c + kUnit);
+            long w = 0;
+            for (int q = c; q < e; ++q) w += runs[t][q].z;
+            units.push_back(int4{t, base + c, base + e, 0});
+            uwork.push_back(w);
+        }
+    }
+    std::vector<int> order(units.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return uwork[x] > uwork[y]; });
+    std::vector<int4> sorted(units.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
+    P.nunits = (int)sorted.size();
+    radon_status s = RADON_OK;
+    if ((s = dev_upload(p, flat, &P.chunks)) || (s = dev_upload(p, sorted, &P.units))) return s;
+    return RADON_OK;
+}
+
 radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector<double>& bs,
                                 const std::vector<double>& phi_all, int smem_max) {
     const radon_desc& d = p->d;
@@ -552,55 +612,6 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
         cj[jl] = w * 2.0 * h.a * h.a * tb / (n_t * n_x * h.dtheta * h.drho);
     }
     for (int k = 0; k < d.Nx; ++k) wk[k] = (k == 0 || k == d.Nx - 1) ? 0.5 : 1.0;
-    // candidate sample range of every band (from the FP64 angles, one sample of margin:
-    // the device tables come from the same FP64 formulas)
-    const int nj = h.jt_hi - h.jt_lo + 1;
-    std::vector<int2> jband((size_t)P.nbands * d.Nx, int2{1, 0});
-    for (int k = 0; k < d.Nx; ++k) {
-        const int jstart = std::max(h.jt_lo, h.jfirst[k]);
-        for (int j = jstart; j <= h.jt_hi; ++j) {
-            const double xth = (phi_all[(size_t)k * nj + (j - h.jt_lo)] - h.theta0) / h.dtheta;
-            const int fl = (int)std::floor(xth);
-            int b0 = (int)std::ceil((double)(fl - R) / R);
-            int b1 = (int)std::floor((double)(fl + 2) / R);
-            b0 = std::max(b0, 0);
-            b1 = std::min(b1, P.nbands - 1);
-            for (int b = b0; b <= b1; ++b) {
-                int2& r = jband[(size_t)b * d.Nx + k];
-                if (r.x > r.y) r = int2{j, j};
-                else {
-                    r.x = std::min(r.x, j);
-                    r.y = std::max(r.y, j);
-                }
-            }
-        }
-        for (int b = 0; b < P.nbands; ++b) {
-            int2& r = jband[(size_t)b * d.Nx + k];
-            if (r.x <= r.y) {
-                r.x = std::max(r.x - 1, jstart);
-                r.y = std::min(r.y + 1, h.jt_hi);
-            }
-        }
-    }
-    // chunks of at most 8 samples of one trace, grouped by band
-    std::vector<int> band_off(P.nbands + 1, 0);
-    std::vector<int4> runs;
-    for (int b = 0; b < P.nbands; ++b) {
-        band_off[b] = (int)runs.size();
-        for (int k = 0; k < d.Nx; ++k) {
-            const int2 r = jband[(size_t)b * d.Nx + k];
-            for (int j = r.x; j <= r.y; j += 8) runs.push_back(int4{k, j, std::min(8, r.y - j + 1), 0});
-        }
-    }
-    band_off[P.nbands] = (int)runs.size();
-    // launch order: bands with the most samples first (the heaviest CTAs set
-    // the kernel's duration, so they should not start last)
-    std::vector<long> work_s(P.nbands, 0);
-    for (int b = 0; b < P.nbands; ++b)
-        for (int r = band_off[b]; r < band_off[b + 1]; ++r) work_s[b] += runs[r].z;
-    std::vector<int> order_s(P.nbands);
-    for (int b = 0; b < P.nbands; ++b) order_s[b] = b;
-    std::stable_sort(order_s.begin(), order_s.end(), [&](int x, int y) { return work_s[x] > work_s[y]; });
     // output columns: theta taps, scale, e^rho polynomial; band column ranges
     const std::vector<double> q = q_grid(d);
     const int ncol = h.l_hi - h.l_lo + 1;
@@ -659,8 +670,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     if (radon_status s = kernel_spectrum(p, h, CB, P.nkb, K)) return s;
 
     radon_status s = RADON_OK;
-    if ((s = dev_upload(p, band_off, &P.band_off)) || (s = dev_upload(p, runs, &P.runs)) ||
-        (s = dev_upload(p, order_s, &P.order_s)) || (s = dev_upload(p, order_r, &P.order_r)) ||
+    if ((s = dev_upload(p, order_r, &P.order_r)) ||
         (s = dev_upload(p, lband, &P.lband)) ||
         (s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
         (s = dev_upload(p, colscale, &P.colscale)) || (s = dev_upload(p, K, &P.K)) ||
@@ -703,6 +713,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.stab = (const SampleEnt*)tab;
     if (int e = launch_sample_table(A, dcj, dwk, djf, (SampleEnt*)tab))
         return fail(RADON_ERR_CUDA, std::string("position table: ") + cudaGetErrorString((cudaError_t)e));
+    if ((s = build_tile_lists(p, h, P))) return s;
     if ((s = dev_alloc(p, (size_t)ncol * d.Ntau * sizeof(RadonEnt), &tab))) return s;
     P.rtab = (const RadonEnt*)tab;
     if (int e = launch_radon_table(A, dqb2, (RadonEnt*)tab))
@@ -874,17 +885,22 @@ extern "C" radon_status radon_fwd(radon_plan p, const float* f, float* g, void* 
             const PieceDev& P = p->pieces[first + t].dev;
             const double bs = bytes_spectrum(P);
             if (radon_status s = cuda_status(
-                    timed(p, 0, bytes_samples(P) + bs, stream,
-                          [&] { return launch_scatter_gather_rows(P, f, p->spec1, stream); }),
+                    timed(p, 0, bytes_samples(P) + bytes_lattice(P), stream,
+                          [&] { return launch_grid_tiles(P, f, stream); }),
                     "gridding"))
                 return s;
             if (radon_status s = cuda_status(
-                    timed(p, 1, 2 * bs + bytes_kernel(P), stream,
+                    timed(p, 1, bytes_lattice(P) + bs, stream,
+                          [&] { return launch_rows_r2c(P, p->spec1, stream); }),
+                    "row FFT"))
+                return s;
+            if (radon_status s = cuda_status(
+                    timed(p, 2, 2 * bs + bytes_kernel(P), stream,
                           [&] { return launch_colconv(P, p->spec1, p->spec2, 0, stream); }),
                     "convolution"))
                 return s;
             if (radon_status s = cuda_status(
-                    timed(p, 2, bs + bytes_lattice(P), stream,
+                    timed(p, 3, bs + bytes_lattice(P), stream,
                           [&] { return launch_rows_c2r(P, p->spec2, stream); }),
                     "inverse row FFT"))
                 return s;
@@ -897,7 +913,7 @@ extern "C" radon_status radon_fwd(radon_plan p, const float* f, float* g, void* 
         }
         const double gb = 4.0 * p->d.Ntau * (p->qpieces[qi].second - p->qpieces[qi].first + 1);
         if (radon_status s = cuda_status(
-                timed(p, 3, lat + gb, stream,
+                timed(p, 4, lat + gb, stream,
                       [&] {
                           return launch_gather_radon(host.data(), count, p->dev_pieces + first,
                                                      p->qpieces[qi].first, p->qpieces[qi].second, g,
@@ -920,20 +936,20 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
         lat += bytes_lattice(P);
         const double gb = 4.0 * p->d.Ntau * (P.l_hi - P.l_lo + 1);
         if (radon_status s = cuda_status(
-                timed(p, 4, gb + bs, stream, [&] { return launch_scatter_radon_rows(P, g, p->spec1, stream); }),
+                timed(p, 5, gb + bs, stream, [&] { return launch_scatter_radon_rows(P, g, p->spec1, stream); }),
                 "adjoint interpolation"))
             return s;
         if (radon_status s = cuda_status(
-                timed(p, 5, 2 * bs + bytes_kernel(P), stream,
+                timed(p, 6, 2 * bs + bytes_kernel(P), stream,
                       [&] { return launch_colconv(P, p->spec1, p->spec2, 1, stream); }),
                 "adjoint convolution"))
             return s;
         if (radon_status s = cuda_status(
-                timed(p, 6, bs + bytes_lattice(P), stream, [&] { return launch_rows_c2r(P, p->spec2, stream); }),
+                timed(p, 7, bs + bytes_lattice(P), stream, [&] { return launch_rows_c2r(P, p->spec2, stream); }),
                 "inverse row FFT"))
             return s;
     }
-    return cuda_status(timed(p, 7, lat + 4.0 * p->d.Nt * p->d.Nx, stream,
+    return cuda_status(timed(p, 8, lat + 4.0 * p->d.Nt * p->d.Nx, stream,
                              [&] {
                                  return launch_gather_samples(p->dev_pieces, (int)p->pieces.size(), p->d.Nt,
                                                               p->d.Nx, f, stream);
@@ -1146,8 +1162,8 @@ int plan_forward_in_work(radon_plan_s* p, const float* f, float* g, void* work, 
         const int first = p->qfirst[qi], count = p->qcount[qi];
         for (int t = 0; t < count; ++t) {
             const PieceDev& P = local[first + t];
-            if (radon_status s = cuda_status(launch_scatter_gather_rows(P, f, s1, stream), "gridding"))
-                return s;
+            if (radon_status s = cuda_status(launch_grid_tiles(P, f, stream), "gridding")) return s;
+            if (radon_status s = cuda_status(launch_rows_r2c(P, s1, stream), "row FFT")) return s;
             if (radon_status s = cuda_status(launch_colconv(P, s1, s2, 0, stream), "convolution"))
                 return s;
             if (radon_status s = cuda_status(launch_rows_c2r(P, s2, stream), "inverse row FFT"))
