@@ -196,13 +196,26 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const __grid_constant__ Piec
         const int4 ch = __ldg(P.chunks + c);               // (trace, first sample, count)
         const int4* st = reinterpret_cast<const int4*>(P.stab + (size_t)ch.x * P.nj - P.jt_lo) + ch.y;
         const float* fk = f + (size_t)ch.x * P.Nt + ch.y;
+        // issue every load of the chunk before the first is used
+        int4 ent[8];
+        float fv[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            if (s < ch.z) {
+                ent[s] = __ldg(st + s);
+                fv[s] = __ldg(fk + s);
+            } else {
+                ent[s] = make_int4(0, 0, 0, 0);
+                fv[s] = 0.f;
+            }
+        }
         float acc[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) acc[q] = 0.f;
         int cur = -1;
-#pragma unroll 1
-        for (int s = 0; s < ch.z; ++s) {
-            const int4 e = __ldg(st + s);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int4 e = ent[s];
             const float w = __int_as_float(e.w);
             if (w == 0.f) continue;
             if (e.x != cur) {
@@ -214,7 +227,7 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const __grid_constant__ Piec
             float wt[4], wr[4];
             b3_weights(__int_as_float(e.y), wt);
             b3_weights(__int_as_float(e.z), wr);
-            const float v = __ldg(fk + s) * w;
+            const float v = fv[s] * w;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const float va = v * wt[a];
