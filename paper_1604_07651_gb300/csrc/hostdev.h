@@ -145,19 +145,41 @@ HD_UNROLL
 // Ns = product of the radices already applied, butterfly index j in
 // [0, n/R). tw[k] = exp(-2 pi i k / n), k < n (the forward twiddles; the
 // inverse, dir = +1, uses their conjugates).
+// Multiplies v[r] by w^r (conj(w)^r for dir = +1), r = 1..R-1, with
+// w = tw[t1] = exp(-2 pi i t1 / n). Radix 16 and 8 read only w and w^4 from
+// the table and form w^(4a+b) = (w^4)^a w^b with at most three complex
+// products each (relative error a few ulp); smaller radices read every power.
+template <int R>
+HD void apply_twiddles(const cf* tw, int t1, int dir, cf v[R]) {
+    if (R == 16 || R == 8) {
+        const cf w1 = tw[t1], w4 = tw[4 * t1];
+        const cf w2 = cmul(w1, w1);
+        const cf w3 = cmul(w2, w1);
+        const cf wb[4] = {{1.f, 0.f}, w1, w2, w3};
+        cf wa = w4;                              // w^(4a), a >= 1
+        HD_UNROLL
+        for (int b = 1; b < 4; ++b) v[b] = dir < 0 ? cmul(v[b], wb[b]) : cmulc(v[b], wb[b]);
+        HD_UNROLL
+        for (int a = 1; a < R / 4; ++a) {
+            HD_UNROLL
+            for (int b = 0; b < 4; ++b) {
+                const cf w = b ? cmul(wa, wb[b]) : wa;
+                v[4 * a + b] = dir < 0 ? cmul(v[4 * a + b], w) : cmulc(v[4 * a + b], w);
+            }
+            wa = cmul(wa, w4);
+        }
+    } else {
+        HD_UNROLL
+        for (int r = 1; r < R; ++r) v[r] = dir < 0 ? cmul(v[r], tw[r * t1]) : cmulc(v[r], tw[r * t1]);
+    }
+}
+
 template <int R>
 HD void stockham_load(const cf* in, int n, int Ns, int j, const cf* tw, int dir, cf v[R]) {
-    const int jm = j & (Ns - 1);                // Ns is a power of two
-    const int step = n / (Ns * R);              // twiddle index stride
-HD_UNROLL
-    for (int r = 0; r < R; ++r) {
-        cf x = in[sw(j + r * (n / R))];
-        if (r) {
-            const cf w = tw[r * jm * step];     // < n
-            x = dir < 0 ? cmul(x, w) : cmulc(x, w);
-        }
-        v[r] = x;
-    }
+    HD_UNROLL
+    for (int r = 0; r < R; ++r) v[r] = in[sw(j + r * (n / R))];
+    if (Ns > 1)                                 // the first stage's twiddles are all 1
+        apply_twiddles<R>(tw, (j & (Ns - 1)) * (n / (Ns * R)), dir, v);   // Ns is a power of two
 }
 
 template <int R>

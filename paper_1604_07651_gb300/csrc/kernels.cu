@@ -159,6 +159,9 @@ __device__ __forceinline__ void band_taps(int m0, int n0, int mb, int nrows, int
     }
 }
 
+// Shared tile row pitch: one float of padding puts the rows on different banks.
+constexpr int kTilePitch = kTileCols + 1;
+
 // Forward gridding (Eq. (15)) of the gather f[Nx][Nt] onto the lattice
 // P.lat (zeroed before). The plan lists, per tile of kTileRows x kTileCols
 // cells, chunks of at most 8 consecutive samples of one trace whose 4x4
@@ -179,18 +182,18 @@ __device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, float* ti
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int n = n0 + c;
-            if (n >= 0 && n < kTileCols) atomicAdd(tile + m * kTileCols + n, acc[4 * a + c]);
+            if (n >= 0 && n < kTileCols) atomicAdd(tile + m * kTilePitch + n, acc[4 * a + c]);
         }
     }
 }
 
 __global__ void __launch_bounds__(256) k_grid_tiles(const __grid_constant__ PieceDev P,
                                                     const float* __restrict__ f) {
-    __shared__ float tile[kTileRows * kTileCols];
+    __shared__ float tile[kTileRows * kTilePitch];
     const int4 u = __ldg(P.units + blockIdx.x);           // (tile, first chunk, end chunk)
     const int ti = u.x / P.ntc, tj = u.x - ti * P.ntc;
     const int m_lo = ti * kTileRows, n_lo = tj * kTileCols;
-    for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) tile[i] = 0.f;
+    for (int i = threadIdx.x; i < kTileRows * kTilePitch; i += blockDim.x) tile[i] = 0.f;
     __syncthreads();
     for (int c = u.y + threadIdx.x; c < u.z; c += blockDim.x) {
         const int4 ch = __ldg(P.chunks + c);               // (trace, first sample, count)
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(256) k_grid_tiles(const __grid_constant__ Piec
     const int nr = min(kTileRows, P.Ntheta - m_lo), nc = min(kTileCols, P.Nrho - n_lo);
     for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
         const int m = i / kTileCols, n = i - m * kTileCols;
-        const float v = tile[i];
+        const float v = tile[m * kTilePitch + n];
         if (v != 0.f && m < nr && n < nc) atomicAdd(P.lat + (size_t)(m_lo + m) * P.Nrho + n_lo + n, v);
     }
 }
