@@ -98,10 +98,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(tag_rank: int = 0):
+def make_workload(rank: int = 0):
+    """The benchmark gather of one rank: rank 0 has the reference workload,
+    rank r > 0 an independent gather of the same shape (its own seed)."""
     import synth
-    geo, f = synth.sweep_gather(N, tag=2, noise=0.05)
+    geo, f = synth.sweep_gather(N, tag=2 + 1000 * rank, noise=0.05)
     return geo, f
+
+
+def job_time_ms(local_ms: float, world: int, device=None) -> float:
+    """Whole-job time: the maximum over ranks of each rank's time."""
+    if world <= 1:
+        return local_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank transforms `steps` pairs of its own
+    gather, so the job processes world * steps pairs in the slowest rank's time."""
+    return world * steps / (total_ms / 1e3)
 
 
 # Library stage -> kernel that runs it.
@@ -115,6 +134,13 @@ STAGE_KERNEL = {"grid_fwd": "k_grid_tiles", "rows_r2c_fwd": "k_rows_r2c", "colco
 # on: the entry is dropped (traffic null) when csrc/kernels.cu changes.
 MEASURED_TRAFFIC = {
     # kernel: (sha256 prefix of csrc/kernels.cu, bytes per launch averaged over a step's launches)
+    "k_colconv": ("9f36637bd8eb735d", 20.90e6),
+    "k_grid_tiles": ("9f36637bd8eb735d", 44.38e6),
+    "k_scatter_radon": ("9f36637bd8eb735d", 50.51e6),
+    "k_rows_c2r": ("9f36637bd8eb735d", 12.57e6),
+    "k_rows_r2c": ("9f36637bd8eb735d", 13.58e6),
+    "k_gather_radon": ("9f36637bd8eb735d", 128.42e6),
+    "k_gather_samples": ("9f36637bd8eb735d", 110.69e6),
 }
 
 
@@ -263,12 +289,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     prof = plan.profile_read()
     plan.set_profiling(False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = job_time_ms(sum(step_ms), world, dev)
+    value = job_value(args.steps, world, total_ms)
 
     # dominant kernel (stages of the same kernel summed) and its roofline
     hbm, peak_kind = _peaks()
@@ -331,12 +353,8 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    result["e2e"] = {"value": world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+    e2e_ms = job_time_ms(e0.elapsed_time(e1), world, dev)
+    result["e2e"] = {"value": job_value(args.steps, world, e2e_ms), "unit": UNIT,
                      "h2d_bytes_per_step": f.numel() * 4,
                      "d2h_bytes_per_step": (g.numel() + fa.numel()) * 4}
 
