@@ -779,8 +779,8 @@ extern "C" radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau,
     d->qmax = qmax;
     d->tau0 = 0.0;
     d->dtau = 0.0;
-    d->sigma = 1.5;
-    d->omega_c = 0.3;
+    d->sigma = 1.25;
+    d->omega_c = 0.35;
     d->n_tsplit = 2;
     d->tsplit[0] = 0.25;
     d->tsplit[1] = 0.5;

@@ -35,7 +35,7 @@ def hr():
     return hr
 
 
-def _pair(hr, geo, sigma=1.5, omega_c=0.3, tsplit=(0.25, 0.5), nq=1, tau0=0.0, dtau=0.0):
+def _pair(hr, geo, sigma=1.25, omega_c=0.35, tsplit=(0.25, 0.5), nq=1, tau0=0.0, dtau=0.0):
     plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
                    tau0=tau0, dtau=dtau, sigma=sigma, omega_c=omega_c, tsplit=tsplit, n_qsplit=nq)
     desc = Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
