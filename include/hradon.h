@@ -180,9 +180,10 @@ radon_status radon_direct_adj(const float* g, float* f, int Nt, int Nx, int Ntau
  * FFT*K*IFFT (forward), 3 inverse row FFT (forward), 4 output interpolation
  * (forward), 5 output scatter + row FFT (adjoint), 6 column
  * FFT*conj(K)*IFFT (adjoint), 7 inverse row FFT (adjoint), 8 gather of the
- * samples (adjoint).
+ * samples (adjoint), 9 max |g| of every column of the adjoint input (the
+ * fixed-point scale of stage 5).
  */
-#define RADON_NSTAGES 9
+#define RADON_NSTAGES 10
 radon_status radon_plan_set_profiling(radon_plan p, int enable);
 
 /*

@@ -54,10 +54,11 @@ struct PieceDev {
     const RadonEnt* rtab;   // [ncol][Ntau] rho position of every output of the piece
     int ntr, ntc;           // lattice tiles of the forward gridding: rows, columns
     int nunits;             // work units of the forward gridding
-    const int4* units;      // (tile, first chunk, end chunk, 0), heaviest first
+    const int4* units;      // (tile, first chunk, end chunk, 28 - ilogb(cell weight bound)), heaviest first
     const int4* chunks;     // (trace k, first sample j, count <= 8, 0), grouped by tile
     const int* order_r;     // [nbands] bands in decreasing output work (launch order)
     const int2* lband;      // [nbands] candidate output-column range of each band
+    const int* bandsh;      // [nbands] 28 - ilogb(cell weight bound) of the adjoint scatter
     const float4* colw;     // [ncol] theta tap weights of each column
     const int* colm0;       // [ncol] first theta tap of each column
     const float* colscale;  // [ncol] output scale 2 X cos(psi) / a
@@ -70,14 +71,17 @@ struct PieceDev {
     float* lat;             // [Ntheta][Nrho] real lattice (Q forward, G' adjoint)
 };
 
-// Lattice tile of the forward gridding (rows x columns of cells).
+// Lattice tile of the forward gridding (rows x columns of cells) and the
+// largest work unit (chunks of <= 8 samples; one thread per chunk).
 constexpr int kTileRows = 16;
 constexpr int kTileCols = 128;
+constexpr int kUnitChunks = 256;
 
 // Launchers (kernels.cu)
 int launch_grid_tiles(const PieceDev& P, const float* f, void* stream);
 int launch_rows_r2c(const PieceDev& P, cf* spec, void* stream);
-int launch_scatter_radon_rows(const PieceDev& P, const float* g, cf* spec, void* stream);
+int launch_scatter_radon_rows(const PieceDev& P, const float* g, const float* colmax, cf* spec, void* stream);
+int launch_colmax(const float* g, int Nq, int Ntau, float* colmax, void* stream);
 int launch_colconv(const PieceDev& P, const cf* in, cf* out, int adjoint, void* stream);
 int launch_rows_c2r(const PieceDev& P, const cf* spec, void* stream);
 int launch_gather_radon(const PieceDev* pieces, int npieces, const PieceDev* dev_pieces,

@@ -146,33 +146,86 @@ __device__ __forceinline__ void zero_rows(const PieceDev& P) {
     for (int i = threadIdx.x; i < n4; i += blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+
+// Shared tile row pitch: one word of padding puts the rows on different banks.
+constexpr int kTilePitch = kTileCols + 1;
+
+// Fixed-point accumulation in shared memory. Integer adds to shared memory
+// are single fire-and-forget instructions, float adds are compare-and-swap
+// loops (measured 3.7x apart on conflict-free addresses), and integer sums do
+// not depend on the order in which warps arrive. A block accumulating into a
+// region whose cells provably stay below vmax * C in magnitude (vmax the
+// largest |input| it adds, C a plan-time bound on the total weight any cell
+// collects, C < 2^(ec+1)) scales its inputs by 2^sh with
+// sh = 28 - ec - ilogb(vmax): every cell stays below 2^30, and every
+// contribution is rounded to 2^-31 of at most four times the bound. The
+// power of two is applied as two factors so that it spans the whole float
+// range. The plan stores 28 - ec.
+__device__ __forceinline__ float pow2i(int k) { return __int_as_float((127 + k) << 23); }   // |k| <= 126
+
+struct Pow2Scale {
+    float up1, up2, down1, down2;
+    __device__ __forceinline__ Pow2Scale(int sh) {
+        const int h1 = sh / 2, h2 = sh - h1;
+        up1 = pow2i(h1);
+        up2 = pow2i(h2);
+        down1 = pow2i(-h1);
+        down2 = pow2i(-h2);
+    }
+    __device__ __forceinline__ float up(float v) const { return v * up1 * up2; }
+    __device__ __forceinline__ float down(int t) const { return (float)t * down1 * down2; }
+};
+
+__device__ __forceinline__ void red_fixed(int* p, float v) { atomicAdd(p, __float2int_rn(v)); }
+
+// 4x4 taps of one scaled output value onto the fixed-point band rows.
 __device__ __forceinline__ void band_taps(int m0, int n0, int mb, int nrows, int Prho, float val,
                                           const float wt[4], const float wr[4]) {
+    int* band = reinterpret_cast<int*>(smem_f);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int m = m0 + a - mb;
         if (m < 0 || m >= nrows) continue;
         const float va = val * wt[a];
-        float* row = smem_f + m * Prho;
+        int* row = band + m * Prho;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) atomicAdd(row + swr(n0 + c), va * wr[c]);
+        for (int c = 0; c < 4; ++c) red_fixed(row + swr(n0 + c), va * wr[c]);
     }
 }
 
-// Shared tile row pitch: one float of padding puts the rows on different banks.
-constexpr int kTilePitch = kTileCols + 1;
+// Maximum of a non-negative float over the block (all threads get it); NaN
+// wins, so a non-finite input shows as a non-finite maximum.
+__device__ __forceinline__ float block_max_abs(float v, float* red) {
+    v = fabsf(v);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const float o = __shfl_xor_sync(0xffffffffu, v, d);
+        v = (o > v || o != o) ? o : v;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        const float o = red[w];
+        m = (o > m || o != o) ? o : m;
+    }
+    return m;
+}
 
 // Forward gridding (Eq. (15)) of the gather f[Nx][Nt] onto the lattice
 // P.lat (zeroed before). The plan lists, per tile of kTileRows x kTileCols
 // cells, chunks of at most 8 consecutive samples of one trace whose 4x4
 // footprint meets the tile, and cuts every tile's list into work units of at
-// most 256 chunks (sample density varies by two orders of magnitude over the
-// lattice, so units, not tiles, balance the CTAs). A CTA takes one unit, each
-// thread walks one chunk: neighbouring threads are 8 samples apart, so their
-// footprints rarely meet, and a thread sums its samples in registers while
-// their first tap (m0, n0) stays the same, adding to the shared tile only when
-// it moves. The tile's touched cells are then added to P.lat.
-__device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, float* tile, const float acc[16]) {
+// most kUnitChunks chunks (sample density varies by two orders of magnitude
+// over the lattice, so units, not tiles, balance the CTAs), each with the
+// largest total B-spline weight one of its cells can collect. A CTA takes one
+// unit, each thread one chunk: neighbouring threads are 8 samples apart, so
+// their footprints rarely meet, and a thread sums its samples in registers
+// while their first tap (m0, n0) stays the same, adding to the fixed-point
+// shared tile only when it moves. The tile's touched cells are then added to
+// P.lat. A non-finite sample makes the unit's tile NaN (the FFTs that follow
+// would spread it over the whole piece in any case).
+__device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, int* tile, const float acc[16]) {
     if (mn < 0) return;
     const int m0 = (mn >> 16) - m_lo, n0 = (mn & 0xffff) - n_lo;
 #pragma unroll
@@ -182,70 +235,90 @@ __device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, float* ti
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int n = n0 + c;
-            if (n >= 0 && n < kTileCols) atomicAdd(tile + m * kTilePitch + n, acc[4 * a + c]);
+            if (n >= 0 && n < kTileCols) red_fixed(tile + m * kTilePitch + n, acc[4 * a + c]);
         }
     }
 }
 
-__global__ void __launch_bounds__(256) k_grid_tiles(const __grid_constant__ PieceDev P,
-                                                    const float* __restrict__ f) {
-    __shared__ float tile[kTileRows * kTilePitch];
-    const int4 u = __ldg(P.units + blockIdx.x);           // (tile, first chunk, end chunk)
+__global__ void __launch_bounds__(kUnitChunks) k_grid_tiles(const __grid_constant__ PieceDev P,
+                                                            const float* __restrict__ f) {
+    __shared__ int tile[kTileRows * kTilePitch];
+    __shared__ float red[kUnitChunks / 32];
+    const int4 u = __ldg(P.units + blockIdx.x);   // (tile, first chunk, end chunk, 28 - ec)
     const int ti = u.x / P.ntc, tj = u.x - ti * P.ntc;
     const int m_lo = ti * kTileRows, n_lo = tj * kTileCols;
-    for (int i = threadIdx.x; i < kTileRows * kTilePitch; i += blockDim.x) tile[i] = 0.f;
-    __syncthreads();
-    for (int c = u.y + threadIdx.x; c < u.z; c += blockDim.x) {
-        const int4 ch = __ldg(P.chunks + c);               // (trace, first sample, count)
+    for (int i = threadIdx.x; i < kTileRows * kTilePitch; i += blockDim.x) tile[i] = 0;
+    // one chunk per thread: issue every load of the chunk before the first is used
+    const int c = u.y + threadIdx.x;
+    int4 ent[8];
+    float v[8];
+    float vmax = 0.f;
+    {
+        int4 ch = make_int4(0, 0, 0, 0);                // (trace, first sample, count)
+        if (c < u.z) ch = __ldg(P.chunks + c);
         const int4* st = reinterpret_cast<const int4*>(P.stab + (size_t)ch.x * P.nj - P.jt_lo) + ch.y;
         const float* fk = f + (size_t)ch.x * P.Nt + ch.y;
-        // issue every load of the chunk before the first is used
-        int4 ent[8];
-        float fv[8];
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             if (s < ch.z) {
                 ent[s] = __ldg(st + s);
-                fv[s] = __ldg(fk + s);
+                v[s] = __ldg(fk + s);
             } else {
                 ent[s] = make_int4(0, 0, 0, 0);
-                fv[s] = 0.f;
+                v[s] = 0.f;
             }
         }
-        float acc[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-        int cur = -1;
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-            const int4 e = ent[s];
-            const float w = __int_as_float(e.w);
-            if (w == 0.f) continue;
-            if (e.x != cur) {
-                flush_tile(cur, m_lo, n_lo, tile, acc);
-#pragma unroll
-                for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-                cur = e.x;
-            }
-            float wt[4], wr[4];
-            b3_weights(__int_as_float(e.y), wt);
-            b3_weights(__int_as_float(e.z), wr);
-            const float v = fv[s] * w;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const float va = v * wt[a];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[4 * a + q] = fmaf(va, wr[q], acc[4 * a + q]);
-            }
+            const float w = __int_as_float(ent[s].w);
+            v[s] = w != 0.f ? v[s] * w : 0.f;   // muted samples add nothing, whatever f holds
+            const float a = fabsf(v[s]);
+            vmax = (a > vmax || a != a) ? a : vmax;
         }
-        flush_tile(cur, m_lo, n_lo, tile, acc);
     }
-    __syncthreads();
+    vmax = block_max_abs(vmax, red);   // also orders the tile's zeroing before the adds
+    if (vmax == 0.f) return;
     const int nr = min(kTileRows, P.Ntheta - m_lo), nc = min(kTileCols, P.Nrho - n_lo);
+    if (!(vmax <= 3.402823466e38f)) {
+        for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
+            const int m = i / kTileCols, n = i - m * kTileCols;
+            if (m < nr && n < nc) P.lat[(size_t)(m_lo + m) * P.Nrho + n_lo + n] = __int_as_float(0x7fc00000);
+        }
+        return;
+    }
+    const Pow2Scale sc(u.w - ilogbf(vmax));
+#pragma unroll
+    for (int s = 0; s < 8; ++s) v[s] = sc.up(v[s]);
+    float acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+    int cur = -1;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int4 e = ent[s];
+        if (v[s] == 0.f) continue;
+        if (e.x != cur) {
+            flush_tile(cur, m_lo, n_lo, tile, acc);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+            cur = e.x;
+        }
+        float wt[4], wr[4];
+        b3_weights(__int_as_float(e.y), wt);
+        b3_weights(__int_as_float(e.z), wr);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const float va = v[s] * wt[a];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[4 * a + q] = fmaf(va, wr[q], acc[4 * a + q]);
+        }
+    }
+    flush_tile(cur, m_lo, n_lo, tile, acc);
+    __syncthreads();
     for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
         const int m = i / kTileCols, n = i - m * kTileCols;
-        const float v = tile[m * kTilePitch + n];
-        if (v != 0.f && m < nr && n < nc) atomicAdd(P.lat + (size_t)(m_lo + m) * P.Nrho + n_lo + n, v);
+        const int t = tile[m * kTilePitch + n];
+        if (t != 0 && m < nr && n < nc) atomicAdd(P.lat + (size_t)(m_lo + m) * P.Nrho + n_lo + n, sc.down(t));
     }
 }
 
@@ -300,31 +373,42 @@ __device__ __forceinline__ void scatter_column_group(int2 e, float v, int m0, co
     const bool tail = lane == 31 || knext != key;
     if (valid && tail) {
         const float sv[4] = {s0, s1, s2, s3};
+        int* band = reinterpret_cast<int*>(smem_f);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int m = m0 + a - mb;
             if (m < 0 || m >= nrows) continue;
-            float* row = smem_f + m * Prho;
+            int* row = band + m * Prho;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) atomicAdd(row + swr(e.x + c), wt[a] * sv[c]);
+            for (int c = 0; c < 4; ++c) red_fixed(row + swr(e.x + c), wt[a] * sv[c]);
         }
     }
 }
 
 // Adjoint of the output interpolation: scatter g[Nq][Ntau] of this slowness
-// piece's columns onto one band of rows (transpose of Eq. (17)). Work items
-// are (column, block of 64 intercept times), two groups of 32 per item.
+// piece's columns onto one band of rows (transpose of Eq. (17)), in fixed
+// point with the bound max|g| over the band's columns (colmax, per column)
+// times the band's plan-time weight bound. Work items are (column, block of
+// 64 intercept times), two groups of 32 per item. A non-finite g makes the
+// bands of its column NaN.
 __global__ void __launch_bounds__(512, 2) k_scatter_radon(const __grid_constant__ PieceDev P, const float* __restrict__ g,
-                                                       cf* __restrict__ spec) {
+                                                       const float* __restrict__ colmax, cf* __restrict__ spec) {
     const int band = __ldg(P.order_r + blockIdx.x);   // heaviest bands first
     const int mb = band * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
+    const int2 lr = __ldg(P.lband + band);
+    float vmax = 0.f;
+    for (int l = lr.x; l <= lr.y; ++l) {
+        const float o = __ldg(colmax + l);
+        vmax = (o > vmax || o != o) ? o : vmax;
+    }
+    const bool finite = vmax <= 3.402823466e38f;
     zero_rows(P);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int2 lr = __ldg(P.lband + band);
     const int nblk = (P.Ntau + 63) >> 6;
-    const int items = lr.y >= lr.x ? (lr.y - lr.x + 1) * nblk : 0;
+    const int items = (lr.y >= lr.x && vmax > 0.f && finite) ? (lr.y - lr.x + 1) * nblk : 0;
+    const Pow2Scale scl(__ldg(P.bandsh + band) - (vmax > 0.f && finite ? ilogbf(vmax) : 0));
     for (int it = warp; it < items; it += nw) {
         const int l = lr.x + it / nblk;
         const int i = ((it % nblk) << 6) + lane;
@@ -339,11 +423,40 @@ __global__ void __launch_bounds__(512, 2) k_scatter_radon(const __grid_constant_
         const float4 w4 = __ldg(P.colw + lc);
         const float wt[4] = {w4.x, w4.y, w4.z, w4.w};
         const float sc = __ldg(P.colscale + lc);
-        scatter_column_group(e0, g0 * sc, m0, wt, mb, nrows, P.Prho, lane);
-        scatter_column_group(e1, g1 * sc, m0, wt, mb, nrows, P.Prho, lane);
+        scatter_column_group(e0, scl.up(g0 * sc), m0, wt, mb, nrows, P.Prho, lane);
+        scatter_column_group(e1, scl.up(g1 * sc), m0, wt, mb, nrows, P.Prho, lane);
+    }
+    __syncthreads();
+    // fixed point -> float, in place
+    {
+        const int n = nrows * P.Prho;
+        int* bi = reinterpret_cast<int*>(smem_f);
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            smem_f[i] = finite ? scl.down(bi[i]) : __int_as_float(0x7fc00000);
     }
     __syncthreads();
     rows_r2c_write(P, mb, nrows, spec);
+}
+
+// Largest |g| of every output column (one warp per column of Ntau values);
+// NaN wins.
+__global__ void __launch_bounds__(256) k_colmax(const float* __restrict__ g, int Nq, int Ntau,
+                                                float* __restrict__ colmax) {
+    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (l >= Nq) return;
+    const float* gl = g + (size_t)l * Ntau;
+    float m = 0.f;
+    for (int i = lane; i < Ntau; i += 32) {
+        const float a = fabsf(__ldg(gl + i));
+        m = (a > m || a != a) ? a : m;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const float o = __shfl_xor_sync(0xffffffffu, m, d);
+        m = (o > m || o != o) ? o : m;
+    }
+    if (lane == 0) colmax[l] = m;
 }
 
 // --------------------------------------------------------------------------
@@ -713,7 +826,7 @@ static int set_smem(const void* fn, size_t bytes) {
 int launch_grid_tiles(const PieceDev& P, const float* f, void* stream) {
     cudaError_t e = cudaMemsetAsync(P.lat, 0, (size_t)P.Ntheta * P.Nrho * sizeof(float), (cudaStream_t)stream);
     if (e != cudaSuccess) return (int)e;
-    if (P.nunits > 0) k_grid_tiles<<<P.nunits, 256, 0, (cudaStream_t)stream>>>(P, f);
+    if (P.nunits > 0) k_grid_tiles<<<P.nunits, kUnitChunks, 0, (cudaStream_t)stream>>>(P, f);
     return check_launch();
 }
 
@@ -724,10 +837,15 @@ int launch_rows_r2c(const PieceDev& P, cf* spec, void* stream) {
     return check_launch();
 }
 
-int launch_scatter_radon_rows(const PieceDev& P, const float* g, cf* spec, void* stream) {
+int launch_scatter_radon_rows(const PieceDev& P, const float* g, const float* colmax, cf* spec, void* stream) {
     const size_t sm = scatter_smem_bytes(P);
     if (int e = set_smem((const void*)k_scatter_radon, sm)) return e;
-    k_scatter_radon<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, g, spec);
+    k_scatter_radon<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, g, colmax, spec);
+    return check_launch();
+}
+
+int launch_colmax(const float* g, int Nq, int Ntau, float* colmax, void* stream) {
+    k_colmax<<<(Nq + 7) / 8, 256, 0, (cudaStream_t)stream>>>(g, Nq, Ntau, colmax);
     return check_launch();
 }
 

@@ -197,6 +197,7 @@ struct radon_plan_s {
     PieceDev* dev_pieces = nullptr;
     cf* spec1 = nullptr;
     cf* spec2 = nullptr;
+    float* colmax = nullptr;                     // [Nq] max|g| of each column (adjoint scatter scale)
     std::vector<void*> allocs;
     size_t bytes = 0;
     // per-stage timing
@@ -528,18 +529,39 @@ radon_status build_tile_lists(radon_plan_s* p, const HostPiece& h, PieceDev& P) 
                 }
         }
     }
-    // work units: every tile's chunks cut into pieces of at most 256 chunks
-    const int kUnit = 256;
+    // work units: every tile's chunks cut into pieces of at most kUnitChunks
+    // chunks, each with the exponent of the largest B-spline weight sum a
+    // cell of the tile collects from the unit's samples (the fixed-point
+    // bound of the kernel, computed with the kernel's own weights)
     std::vector<int4> flat, units;
     std::vector<long> uwork;
+    std::vector<double> cell((size_t)TR * TC);
     for (int t = 0; t < ntiles; ++t) {
         const int base = (int)flat.size();
+        const int m_lo = (t / P.ntc) * TR, n_lo = (t % P.ntc) * TC;
         flat.insert(flat.end(), runs[t].begin(), runs[t].end());
-        for (int c = 0; c < (int)runs[t].size(); c += kUnit) {
-            const int e = std::min((int)runs[t].size(), c + kUnit);
+        for (int c = 0; c < (int)runs[t].size(); c += kUnitChunks) {
+            const int e = std::min((int)runs[t].size(), c + kUnitChunks);
             long w = 0;
-            for (int q = c; q < e; ++q) w += runs[t][q].z;
-            units.push_back(int4{t, base + c, base + e, 0});
+            std::fill(cell.begin(), cell.end(), 0.0);
+            for (int q = c; q < e; ++q) {
+                const int4 ch = runs[t][q];
+                w += ch.z;
+                for (int sidx = 0; sidx < ch.z; ++sidx) {
+                    const SampleEnt& se = tab[(size_t)ch.x * P.nj + (ch.y - P.jt_lo) + sidx];
+                    float wt[4], wr[4];
+                    b3_weights(se.ft, wt);
+                    b3_weights(se.fr, wr);
+                    const int m0 = (se.mn >> 16) - m_lo, n0 = (se.mn & 0xffff) - n_lo;
+                    for (int a = 0; a < 4; ++a)
+                        for (int b = 0; b < 4; ++b) {
+                            const int m = m0 + a, n = n0 + b;
+                            if (m >= 0 && m < TR && n >= 0 && n < TC) cell[(size_t)m * TC + n] += (double)wt[a] * wr[b];
+                        }
+                }
+            }
+            const double cmax = *std::max_element(cell.begin(), cell.end());
+            units.push_back(int4{t, base + c, base + e, 28 - std::ilogb(cmax > 0 ? cmax : 1.0)});
             uwork.push_back(w);
         }
     }
@@ -718,6 +740,38 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.rtab = (const RadonEnt*)tab;
     if (int e = launch_radon_table(A, dqb2, (RadonEnt*)tab))
         return fail(RADON_ERR_CUDA, std::string("position table: ") + cudaGetErrorString((cudaError_t)e));
+    // fixed-point bound of the adjoint scatter: per band, the exponent of the
+    // largest total weight scale * wt * wr one of its cells collects from all
+    // outputs (computed with the kernel's own float weights)
+    {
+        std::vector<RadonEnt> rt((size_t)ncol * d.Ntau);
+        if (cudaMemcpy(rt.data(), tab, rt.size() * sizeof(RadonEnt), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(RADON_ERR_CUDA, "reading back the output position table failed");
+        std::vector<double> rows((size_t)h.Ntheta * h.Nrho, 0.0), prof(h.Nrho);
+        for (int lc = 0; lc < ncol; ++lc) {
+            std::fill(prof.begin(), prof.end(), 0.0);
+            for (int i = 0; i < d.Ntau; ++i) {
+                const RadonEnt e = rt[(size_t)lc * d.Ntau + i];
+                if (e.n0 < 0) continue;
+                float wr[4];
+                b3_weights(e.fr, wr);
+                for (int c = 0; c < 4; ++c) prof[e.n0 + c] += (double)colscale[lc] * wr[c];
+            }
+            const float wt[4] = {colw[lc].x, colw[lc].y, colw[lc].z, colw[lc].w};
+            for (int a = 0; a < 4; ++a) {
+                double* row = rows.data() + (size_t)(colm0[lc] + a) * h.Nrho;
+                for (int n = 0; n < h.Nrho; ++n) row[n] += wt[a] * prof[n];
+            }
+        }
+        std::vector<int> bandsh(P.nbands);
+        for (int b = 0; b < P.nbands; ++b) {
+            double cmax = 0.0;
+            for (size_t i = (size_t)b * R * h.Nrho; i < std::min((size_t)(b + 1) * R, (size_t)h.Ntheta) * h.Nrho; ++i)
+                cmax = std::max(cmax, rows[i]);
+            bandsh[b] = 28 - std::ilogb(cmax > 0 ? cmax : 1.0);
+        }
+        if ((s = dev_upload(p, bandsh, &P.bandsh))) return s;
+    }
     void* lat = nullptr;
     if ((s = dev_alloc(p, (size_t)h.Ntheta * h.Nrho * sizeof(float), &lat))) return s;
     P.lat = (float*)lat;
@@ -849,6 +903,8 @@ extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* 
     p->spec1 = (cf*)a;
     if ((s = dev_alloc(p, spec * sizeof(cf), &a))) { destroy_plan(p); return s; }
     p->spec2 = (cf*)a;
+    if ((s = dev_alloc(p, (size_t)p->d.Nq * sizeof(float), &a))) { destroy_plan(p); return s; }
+    p->colmax = (float*)a;
     std::vector<PieceDev> devs;
     for (auto& h : p->pieces) devs.push_back(h.dev);
     const PieceDev* dp = nullptr;
@@ -929,6 +985,11 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
     if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
     if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
     DeviceGuard guard(p->device);
+    if (radon_status s = cuda_status(
+            timed(p, 9, 4.0 * p->d.Nq * p->d.Ntau, stream,
+                  [&] { return launch_colmax(g, p->d.Nq, p->d.Ntau, p->colmax, stream); }),
+            "adjoint input maximum"))
+        return s;
     double lat = 0;
     for (auto& h : p->pieces) {
         const PieceDev& P = h.dev;
@@ -936,7 +997,7 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
         lat += bytes_lattice(P);
         const double gb = 4.0 * p->d.Ntau * (P.l_hi - P.l_lo + 1);
         if (radon_status s = cuda_status(
-                timed(p, 5, gb + bs, stream, [&] { return launch_scatter_radon_rows(P, g, p->spec1, stream); }),
+                timed(p, 5, gb + bs, stream, [&] { return launch_scatter_radon_rows(P, g, p->colmax, p->spec1, stream); }),
                 "adjoint interpolation"))
             return s;
         if (radon_status s = cuda_status(

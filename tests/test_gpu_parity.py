@@ -202,3 +202,46 @@ def test_edge_cases(hr, oracle_direct):
     assert _rel(plan1.forward(_cuda(f1)).cpu().numpy(), LogPolar(desc1).forward(f1)) < PARITY_TOL
     z = plan1.forward(torch.zeros((geo1.Nx, geo1.Nt), device="cuda"))
     assert float(z.abs().max()) == 0.0
+
+
+def test_fixed_point_scale_range(hr):
+    """The gridding and the adjoint scatter accumulate in fixed point scaled
+    by the input's own maximum: the transforms stay linear (to FP32 rounding)
+    across the whole float range, and a spike well above the rest of the
+    data does not wipe out the small values beside it."""
+    geo = synth.Geometry(256, 96, 200, 64, 0.004, 0.02, 0.2, 0.7)
+    plan, desc = _pair(hr, geo)
+    ref = LogPolar(desc)
+    f = synth.band_limited_gather(geo, 51, n_events=5, nu=10.0)
+    g = synth.random_radon_image(geo, 52)
+    fwd1 = plan.forward(_cuda(f)).cpu().numpy().astype(np.float64)
+    adj1 = plan.adjoint(_cuda(g)).cpu().numpy().astype(np.float64)
+    for c in (2.0 ** -80, 1e-20, 3e15, 2.0 ** 90):
+        assert _rel(plan.forward(_cuda(f * c)).cpu().numpy() / c, fwd1) < 1e-6, c
+        assert _rel(plan.adjoint(_cuda(g * c)).cpu().numpy() / c, adj1) < 1e-6, c
+    # a spike 1e3 times the data (FP32 FFT round-off of the spike alone is
+    # ~1e-5 of the rest): the transform of the rest keeps that accuracy
+    spike = np.zeros_like(f)
+    spike[40, 100] = 1e3 * np.abs(f).max()
+    fs = plan.forward(_cuda(f + spike)).cpu().numpy() - plan.forward(_cuda(spike)).cpu().numpy()
+    assert _rel(fs, ref.forward(f)) < 1e-4
+    gsp = np.zeros_like(g)
+    gsp[10, 50] = 1e3 * np.abs(g).max()
+    ad = plan.adjoint(_cuda(g + gsp)).cpu().numpy() - plan.adjoint(_cuda(gsp)).cpu().numpy()
+    assert _rel(ad, ref.adjoint(g)) < 1e-4
+
+
+def test_non_finite_input_gives_non_finite_output(hr):
+    """A NaN or infinite sample poisons its pieces (as the FFTs would) instead
+    of being dropped or faulting; the next call on clean data is exact."""
+    geo = synth.Geometry(128, 64, 128, 32, 0.004, 0.02, 0.2, 0.7)
+    plan, desc = _pair(hr, geo)
+    f = synth.band_limited_gather(geo, 61, n_events=4, nu=10.0)
+    for bad in (np.nan, np.inf):
+        fb = f.copy()
+        fb[30, 70] = bad
+        assert not np.isfinite(plan.forward(_cuda(fb)).cpu().numpy()).all()
+        g = synth.random_radon_image(geo, 62)
+        g[5, 60] = bad
+        assert not np.isfinite(plan.adjoint(_cuda(g)).cpu().numpy()).all()
+    assert _rel(plan.forward(_cuda(f)).cpu().numpy(), LogPolar(desc).forward(f)) < PARITY_TOL
