@@ -125,10 +125,10 @@ def job_value(steps: int, world: int, total_ms: float) -> float:
 
 # Library stage -> kernel that runs it.
 STAGE_KERNEL = {"grid_fwd": "k_grid_tiles", "rows_r2c_fwd": "k_rows_r2c", "colconv_fwd": "k_colconv",
-                "rows_c2r_fwd": "k_rows_c2r", "interp_fwd": "k_gather_radon",
-                "scatter_rowfft_adj": "k_scatter_radon", "colconv_adj": "k_colconv",
+                "rows_c2r_fwd": "k_rows_c2r", "interp_fwd": "k_interp_columns",
+                "bandrows_rowfft_adj": "k_band_rows", "colconv_adj": "k_colconv",
                 "rows_c2r_adj": "k_rows_c2r", "gather_adj": "k_gather_samples",
-                "colmax_adj": "k_colmax"}
+                "profiles_adj": "k_col_profiles"}
 
 # DRAM bytes (read + write) per launch from one ncu capture of the benchmark
 # workload (profiles/*.md), valid only for the kernel source they were taken

@@ -178,10 +178,9 @@ radon_status radon_direct_adj(const float* g, float* f, int Nt, int Nx, int Ntau
  * radon_fwd / radon_adj is bracketed by CUDA events recorded on the launch
  * stream. Stages: 0 gridding (forward), 1 row FFT (forward), 2 column
  * FFT*K*IFFT (forward), 3 inverse row FFT (forward), 4 output interpolation
- * (forward), 5 output scatter + row FFT (adjoint), 6 column
- * FFT*conj(K)*IFFT (adjoint), 7 inverse row FFT (adjoint), 8 gather of the
- * samples (adjoint), 9 max |g| of every column of the adjoint input (the
- * fixed-point scale of stage 5).
+ * (forward), 5 theta spread of the column profiles + row FFT (adjoint), 6
+ * column FFT*conj(K)*IFFT (adjoint), 7 inverse row FFT (adjoint), 8 gather
+ * of the samples (adjoint), 9 rho profiles of the output columns (adjoint).
  */
 #define RADON_NSTAGES 10
 radon_status radon_plan_set_profiling(radon_plan p, int enable);

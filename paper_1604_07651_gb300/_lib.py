@@ -9,7 +9,7 @@ from . import build as _build
 MAX_TSPLIT = 8
 NSTAGES = 10
 STAGE_NAMES = ["grid_fwd", "rows_r2c_fwd", "colconv_fwd", "rows_c2r_fwd", "interp_fwd",
-               "scatter_rowfft_adj", "colconv_adj", "rows_c2r_adj", "gather_adj", "colmax_adj"]
+               "bandrows_rowfft_adj", "colconv_adj", "rows_c2r_adj", "gather_adj", "profiles_adj"]
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
 

@@ -56,9 +56,8 @@ struct PieceDev {
     int nunits;             // work units of the forward gridding
     const int4* units;      // (tile, first chunk, end chunk, 28 - ilogb(cell weight bound)), heaviest first
     const int4* chunks;     // (trace k, first sample j, count <= 8, 0), grouped by tile
-    const int* order_r;     // [nbands] bands in decreasing output work (launch order)
     const int2* lband;      // [nbands] candidate output-column range of each band
-    const int* bandsh;      // [nbands] 28 - ilogb(cell weight bound) of the adjoint scatter
+    const int* colsh;       // [ncol] 28 - ilogb(cell weight bound) of the adjoint column profiles
     const float4* colw;     // [ncol] theta tap weights of each column
     const int* colm0;       // [ncol] first theta tap of each column
     const float* colscale;  // [ncol] output scale 2 X cos(psi) / a
@@ -69,6 +68,18 @@ struct PieceDev {
     FftPlan fftM;           // row FFT (length Prho/2)
     FftPlan fftT;           // column FFT (length Ptheta)
     float* lat;             // [Ntheta][Nrho] real lattice (Q forward, G' adjoint)
+    cf* spec;               // [nkb][Ntheta][CB] half spectrum of the lattice rows (in-place column pass)
+    float* prof;            // [ncol][hpitch] rho profiles of the output columns (adjoint)
+    int hpitch;             // row pitch of prof, floats, multiple of 4
+};
+
+// Up to kMaxBatch sub-problems launched as one grid: the blocks of piece k
+// are [first[k], first[k+1]); passed by value (about 3.3 KB of parameters).
+constexpr int kMaxBatch = 8;
+struct PieceBatch {
+    int n;
+    int first[kMaxBatch + 1];
+    PieceDev p[kMaxBatch];
 };
 
 // Lattice tile of the forward gridding (rows x columns of cells) and the
@@ -76,16 +87,19 @@ struct PieceDev {
 constexpr int kTileRows = 16;
 constexpr int kTileCols = 128;
 constexpr int kUnitChunks = 256;
+// Most lattice rows one band of the row kernels holds.
+constexpr int kMaxBandRows = 4;
 
-// Launchers (kernels.cu)
-int launch_grid_tiles(const PieceDev& P, const float* f, void* stream);
-int launch_rows_r2c(const PieceDev& P, cf* spec, void* stream);
-int launch_scatter_radon_rows(const PieceDev& P, const float* g, const float* colmax, cf* spec, void* stream);
-int launch_colmax(const float* g, int Nq, int Ntau, float* colmax, void* stream);
-int launch_colconv(const PieceDev& P, const cf* in, cf* out, int adjoint, void* stream);
-int launch_rows_c2r(const PieceDev& P, const cf* spec, void* stream);
-int launch_gather_radon(const PieceDev* pieces, int npieces, const PieceDev* dev_pieces,
-                        int l_lo, int l_hi, float* g, void* stream);
+// Launchers (kernels.cu). The batched ones take n <= kMaxBatch pieces (host
+// copies of the descriptors) and launch one grid over all of them.
+int launch_grid_tiles(const PieceDev* P, int n, const float* f, void* stream);
+int launch_rows_r2c(const PieceDev* P, int n, void* stream);
+int launch_col_profiles(const PieceDev* P, int n, const float* g, void* stream);
+int launch_band_rows(const PieceDev* P, int n, void* stream);
+int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream);
+int launch_rows_c2r(const PieceDev* P, int n, void* stream);
+int launch_interp_columns(const PieceDev* pieces, int npieces, const PieceDev* dev_pieces,
+                          int l_lo, int l_hi, float* g, void* stream);
 int launch_gather_samples(const PieceDev* dev_pieces, int npieces, int Nt, int Nx,
                           float* f, void* stream);
 int launch_sample_table(const TableArgs& A, const double* cj, const double* wk, const int* jfirst,

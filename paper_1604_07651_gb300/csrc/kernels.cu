@@ -9,10 +9,10 @@
 //   k_colconv          FFT along theta, product with the kernel spectrum
 //                      chi_L zeta_hat / B3_hat^2 (Eq. (16)-(17)), inverse FFT;
 //   k_rows_c2r         inverse real FFT of the rows -> B-spline coefficients;
-//   k_gather_radon     cubic B-spline interpolation at (phi, eta) = P2 S(tau^2,
+//   k_interp_columns   cubic B-spline interpolation at (phi, eta) = P2 S(tau^2,
 //                      q^2) (Eq. (17)), summed over the time pieces.
 // Adjoint (Eq. (16), Section 3): the same kernels with the roles exchanged:
-//   k_scatter_radon -> k_colconv (conjugate kernel) -> k_rows_c2r ->
+//   k_col_profiles -> k_band_rows -> k_colconv (conjugate kernel) -> k_rows_c2r ->
 //   k_gather_samples.
 //
 // Lattice positions do not depend on the data: the plan computes them once in
@@ -21,6 +21,8 @@
 // sums. Shared-memory accumulation uses FP32 atomics, so the last bits of the
 // gridding depend on the order in which warps arrive.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "internal.h"
 
@@ -118,10 +120,21 @@ __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* _
 
 extern __shared__ __align__(16) float smem_f[];
 
+// Piece of this block in a batched launch, and the block's index within it.
+__device__ __forceinline__ int batch_piece(const PieceBatch& B, int& bx) {
+    int pi = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxBatch; ++k)
+        if (k < B.n && (int)blockIdx.x >= B.first[k]) pi = k;
+    bx = (int)blockIdx.x - B.first[pi];
+    return pi;
+}
+
 // Real sample n of a row buffer (stored as complex pairs in the sw layout).
 __device__ __forceinline__ int swr(int n) { return 2 * sw(n >> 1) + (n & 1); }
 
-__device__ __forceinline__ void rows_r2c_write(const PieceDev& P, int mb, int nrows, cf* __restrict__ spec) {
+__device__ __forceinline__ void rows_r2c_write(const PieceDev& P, int mb, int nrows) {
+    cf* __restrict__ spec = P.spec;
     const int M = P.Prho / 2;
     cf* Z = reinterpret_cast<cf*>(smem_f);
     block_fft<-1>(Z, M, nrows, P.twM, P.fftM);
@@ -178,21 +191,6 @@ struct Pow2Scale {
 
 __device__ __forceinline__ void red_fixed(int* p, float v) { atomicAdd(p, __float2int_rn(v)); }
 
-// 4x4 taps of one scaled output value onto the fixed-point band rows.
-__device__ __forceinline__ void band_taps(int m0, int n0, int mb, int nrows, int Prho, float val,
-                                          const float wt[4], const float wr[4]) {
-    int* band = reinterpret_cast<int*>(smem_f);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int m = m0 + a - mb;
-        if (m < 0 || m >= nrows) continue;
-        const float va = val * wt[a];
-        int* row = band + m * Prho;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) red_fixed(row + swr(n0 + c), va * wr[c]);
-    }
-}
-
 // Maximum of a non-negative float over the block (all threads get it); NaN
 // wins, so a non-finite input shows as a non-finite maximum.
 __device__ __forceinline__ float block_max_abs(float v, float* red) {
@@ -240,11 +238,13 @@ __device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, int* tile
     }
 }
 
-__global__ void __launch_bounds__(kUnitChunks) k_grid_tiles(const __grid_constant__ PieceDev P,
+__global__ void __launch_bounds__(kUnitChunks) k_grid_tiles(const __grid_constant__ PieceBatch B,
                                                             const float* __restrict__ f) {
     __shared__ int tile[kTileRows * kTilePitch];
     __shared__ float red[kUnitChunks / 32];
-    const int4 u = __ldg(P.units + blockIdx.x);   // (tile, first chunk, end chunk, 28 - ec)
+    int bx;
+    const PieceDev& P = B.p[batch_piece(B, bx)];
+    const int4 u = __ldg(P.units + bx);           // (tile, first chunk, end chunk, 28 - ec)
     const int ti = u.x / P.ntc, tj = u.x - ti * P.ntc;
     const int m_lo = ti * kTileRows, n_lo = tj * kTileCols;
     for (int i = threadIdx.x; i < kTileRows * kTilePitch; i += blockDim.x) tile[i] = 0;
@@ -324,8 +324,10 @@ __global__ void __launch_bounds__(kUnitChunks) k_grid_tiles(const __grid_constan
 
 // Real FFT of a band of lattice rows (P.lat, zero-padded to Prho) into the
 // half spectrum (first half of Eq. (7)/(16)).
-__global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ PieceDev P, cf* __restrict__ spec) {
-    const int mb = blockIdx.x * P.R;
+__global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ PieceBatch B) {
+    int bx;
+    const PieceDev& P = B.p[batch_piece(B, bx)];
+    const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int Pr = P.Prho, Nr = P.Nrho;
     for (int idx = threadIdx.x; idx < nrows * Pr; idx += blockDim.x) {
@@ -333,130 +335,169 @@ __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Pie
         smem_f[m * Pr + swr(n)] = n < Nr ? P.lat[(size_t)(mb + m) * Nr + n] : 0.f;
     }
     __syncthreads();
-    rows_r2c_write(P, mb, nrows, spec);
+    rows_r2c_write(P, mb, nrows);
 }
 
-// One group of 32 consecutive outputs of a column (same theta taps; rho tap
-// n0 nondecreasing in the lane index) onto the band. When neighbouring lanes
-// share a first tap -- small intercept times put dozens of outputs in one
-// cell -- the lanes of each run of equal n0 are summed first with a
+// Adjoint of the output interpolation (transpose of Eq. (17)), separated
+// along the two axes. Every output of a slowness column has the same theta
+// taps (the column's angle), so the transpose is a 1-D scatter along rho per
+// column followed by a 4-tap spread of the column profiles over theta:
+//   h_l[n]   = s_l sum_i g[l][i] B3(rho_il - rho_n)          (k_col_profiles)
+//   G'[m][n] = sum_l B3(theta_l - theta_m) h_l[n]            (k_band_rows)
+// The profiles are summed in fixed point (order-independent), the spread is a
+// plain per-thread sum over the band's columns in a fixed order: the adjoint
+// interpolation has no floating-point atomics and is deterministic.
+
+// One group of 32 consecutive outputs of a column (rho tap n0 nondecreasing
+// in the lane index) onto the column's fixed-point profile. When neighbouring
+// lanes share a first tap -- small intercept times put dozens of outputs in
+// one cell -- the lanes of each run of equal n0 are summed first with a
 // segmented warp scan and only the run's last lane adds to shared memory.
-__device__ __forceinline__ void scatter_column_group(int2 e, float v, int m0, const float wt[4],
-                                                     int mb, int nrows, int Prho, int lane) {
+__device__ __forceinline__ void profile_group(int2 e, float v, int* prof, int lane) {
     const unsigned FULL = 0xffffffffu;
     const bool valid = e.x >= 0;
     const int key = valid ? e.x : -1 - lane;
     float wr[4] = {0.f, 0.f, 0.f, 0.f};
     if (valid) b3_weights(__int_as_float(e.y), wr);
+    float s0 = v * wr[0], s1 = v * wr[1], s2 = v * wr[2], s3 = v * wr[3];
     const int kprev = __shfl_up_sync(FULL, key, 1);
     const bool head = lane == 0 || kprev != key;
-    if (!__any_sync(FULL, !head)) {
-        if (valid) band_taps(m0, e.x, mb, nrows, Prho, v, wt, wr);
-        return;
-    }
-    float s0 = v * wr[0], s1 = v * wr[1], s2 = v * wr[2], s3 = v * wr[3];
-    int h = head;
+    bool write = valid;
+    if (__any_sync(FULL, !head)) {
+        int h = head;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const float t0 = __shfl_up_sync(FULL, s0, d), t1 = __shfl_up_sync(FULL, s1, d);
-        const float t2 = __shfl_up_sync(FULL, s2, d), t3 = __shfl_up_sync(FULL, s3, d);
-        const int th = __shfl_up_sync(FULL, h, d);
-        if (lane >= d && !h) {
-            s0 += t0;
-            s1 += t1;
-            s2 += t2;
-            s3 += t3;
-            h |= th;
+        for (int d = 1; d < 32; d <<= 1) {
+            const float t0 = __shfl_up_sync(FULL, s0, d), t1 = __shfl_up_sync(FULL, s1, d);
+            const float t2 = __shfl_up_sync(FULL, s2, d), t3 = __shfl_up_sync(FULL, s3, d);
+            const int th = __shfl_up_sync(FULL, h, d);
+            if (lane >= d && !h) {
+                s0 += t0;
+                s1 += t1;
+                s2 += t2;
+                s3 += t3;
+                h |= th;
+            }
         }
+        const int knext = __shfl_down_sync(FULL, key, 1);
+        write = valid && (lane == 31 || knext != key);
     }
-    const int knext = __shfl_down_sync(FULL, key, 1);
-    const bool tail = lane == 31 || knext != key;
-    if (valid && tail) {
-        const float sv[4] = {s0, s1, s2, s3};
-        int* band = reinterpret_cast<int*>(smem_f);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int m = m0 + a - mb;
-            if (m < 0 || m >= nrows) continue;
-            int* row = band + m * Prho;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) red_fixed(row + swr(e.x + c), wt[a] * sv[c]);
-        }
+    if (write) {
+        red_fixed(prof + e.x, s0);
+        red_fixed(prof + e.x + 1, s1);
+        red_fixed(prof + e.x + 2, s2);
+        red_fixed(prof + e.x + 3, s3);
     }
 }
 
-// Adjoint of the output interpolation: scatter g[Nq][Ntau] of this slowness
-// piece's columns onto one band of rows (transpose of Eq. (17)), in fixed
-// point with the bound max|g| over the band's columns (colmax, per column)
-// times the band's plan-time weight bound. Work items are (column, block of
-// 64 intercept times), two groups of 32 per item. A non-finite g makes the
-// bands of its column NaN.
-__global__ void __launch_bounds__(512, 2) k_scatter_radon(const __grid_constant__ PieceDev P, const float* __restrict__ g,
-                                                       const float* __restrict__ colmax, cf* __restrict__ spec) {
-    const int band = __ldg(P.order_r + blockIdx.x);   // heaviest bands first
+// One CTA per output column of the piece: P.prof[lc][0..Nrho) (pitch hpitch) of
+// the column's outputs g[l_lo + lc][*], scaled by the column's output scale.
+// Fixed point with the bound max|g| of the column times the column's
+// plan-time weight bound; a non-finite g makes the profile NaN.
+__global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ PieceBatch B, const float* __restrict__ g) {
+    int* prof = reinterpret_cast<int*>(smem_f);
+    __shared__ float red[8];
+    int lc;
+    const PieceDev& P = B.p[batch_piece(B, lc)];
+    const int hp = P.hpitch;
+    const float* gl = g + (size_t)(P.l_lo + lc) * P.Ntau;
+    const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * P.Ntau);
+    float* hl = P.prof + (size_t)lc * hp;
+    for (int n = threadIdx.x; n < P.Nrho; n += blockDim.x) prof[n] = 0;
+    constexpr int Q = 8;                        // outputs per thread in flight
+    const int chunk = Q * (int)blockDim.x;
+    float m = 0.f;
+    for (int i0 = 0; i0 < P.Ntau; i0 += chunk) {
+        float v[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int i = i0 + q * (int)blockDim.x + threadIdx.x;
+            v[q] = i < P.Ntau ? __ldg(gl + i) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const float a = fabsf(v[q]);
+            m = (a > m || a != a) ? a : m;
+        }
+    }
+    const float vmax = block_max_abs(m, red);   // also orders the zeroing before the adds
+    if (!(vmax > 0.f && vmax <= 3.402823466e38f)) {
+        const float fill = vmax == 0.f ? 0.f : __int_as_float(0x7fc00000);
+        for (int n = threadIdx.x; n < hp; n += blockDim.x) hl[n] = fill;
+        return;
+    }
+    const Pow2Scale scl(__ldg(P.colsh + lc) - ilogbf(vmax));
+    const float sc = __ldg(P.colscale + lc);
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < P.Ntau; i0 += chunk) {   // uniform over the block: every lane takes part
+        int2 e[Q];
+        float v[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int i = i0 + q * (int)blockDim.x + threadIdx.x;   // a warp: 32 consecutive outputs
+            e[q] = make_int2(-1, 0);
+            v[q] = 0.f;
+            if (i < P.Ntau) {
+                e[q] = __ldg(rt + i);
+                v[q] = __ldg(gl + i);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) profile_group(e[q], scl.up(v[q] * sc), prof, lane);
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < hp; n += blockDim.x) hl[n] = n < P.Nrho ? scl.down(prof[n]) : 0.f;
+}
+
+// One band of R <= kMaxBandRows lattice rows: G' rows from the profiles of
+// the band's candidate columns (theta taps of each column from the plan),
+// then the row FFT into the half spectrum. Each thread owns four rho cells
+// of every row of the band and sums the columns in order in registers.
+__global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ PieceBatch B) {
+    int band;
+    const PieceDev& P = B.p[batch_piece(B, band)];
+    const float* __restrict__ h = P.prof;
+    const int hp = P.hpitch;
     const int mb = band * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int2 lr = __ldg(P.lband + band);
-    float vmax = 0.f;
-    for (int l = lr.x; l <= lr.y; ++l) {
-        const float o = __ldg(colmax + l);
-        vmax = (o > vmax || o != o) ? o : vmax;
-    }
-    const bool finite = vmax <= 3.402823466e38f;
-    zero_rows(P);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nblk = (P.Ntau + 63) >> 6;
-    const int items = (lr.y >= lr.x && vmax > 0.f && finite) ? (lr.y - lr.x + 1) * nblk : 0;
-    const Pow2Scale scl(__ldg(P.bandsh + band) - (vmax > 0.f && finite ? ilogbf(vmax) : 0));
-    for (int it = warp; it < items; it += nw) {
-        const int l = lr.x + it / nblk;
-        const int i = ((it % nblk) << 6) + lane;
-        const int lc = l - P.l_lo;
-        const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * P.Ntau);
-        const float* gl = g + (size_t)l * P.Ntau;
-        int2 e0 = make_int2(-1, 0), e1 = e0;
-        float g0 = 0.f, g1 = 0.f;
-        if (i < P.Ntau) { e0 = __ldg(rt + i); g0 = __ldg(gl + i); }
-        if (i + 32 < P.Ntau) { e1 = __ldg(rt + i + 32); g1 = __ldg(gl + i + 32); }
-        const int m0 = __ldg(P.colm0 + lc);
-        const float4 w4 = __ldg(P.colw + lc);
-        const float wt[4] = {w4.x, w4.y, w4.z, w4.w};
-        const float sc = __ldg(P.colscale + lc);
-        scatter_column_group(e0, scl.up(g0 * sc), m0, wt, mb, nrows, P.Prho, lane);
-        scatter_column_group(e1, scl.up(g1 * sc), m0, wt, mb, nrows, P.Prho, lane);
-    }
-    __syncthreads();
-    // fixed point -> float, in place
-    {
-        const int n = nrows * P.Prho;
-        int* bi = reinterpret_cast<int*>(smem_f);
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
-            smem_f[i] = finite ? scl.down(bi[i]) : __int_as_float(0x7fc00000);
-    }
-    __syncthreads();
-    rows_r2c_write(P, mb, nrows, spec);
-}
-
-// Largest |g| of every output column (one warp per column of Ntau values);
-// NaN wins.
-__global__ void __launch_bounds__(256) k_colmax(const float* __restrict__ g, int Nq, int Ntau,
-                                                float* __restrict__ colmax) {
-    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (l >= Nq) return;
-    const float* gl = g + (size_t)l * Ntau;
-    float m = 0.f;
-    for (int i = lane; i < Ntau; i += 32) {
-        const float a = fabsf(__ldg(gl + i));
-        m = (a > m || a != a) ? a : m;
-    }
+    const int Pr = P.Prho;
+    for (int n4 = threadIdx.x; n4 < Pr / 4; n4 += blockDim.x) {
+        float4 acc[kMaxBandRows];
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        const float o = __shfl_xor_sync(0xffffffffu, m, d);
-        m = (o > m || o != o) ? o : m;
+        for (int r = 0; r < kMaxBandRows; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * n4 < hp) {
+            for (int l = lr.x; l <= lr.y; ++l) {
+                const int lc = l - P.l_lo;
+                const int a0 = mb - __ldg(P.colm0 + lc);     // tap of the band's first row
+                const float4 w4 = __ldg(P.colw + lc);
+                const float4 hv = __ldg(reinterpret_cast<const float4*>(h + (size_t)lc * hp) + n4);
+#pragma unroll
+                for (int r = 0; r < kMaxBandRows; ++r) {
+                    const int a = a0 + r;
+                    if (r < nrows && a >= 0 && a < 4) {
+                        const float w = a == 0 ? w4.x : a == 1 ? w4.y : a == 2 ? w4.z : w4.w;
+                        acc[r].x = fmaf(w, hv.x, acc[r].x);
+                        acc[r].y = fmaf(w, hv.y, acc[r].y);
+                        acc[r].z = fmaf(w, hv.z, acc[r].z);
+                        acc[r].w = fmaf(w, hv.w, acc[r].w);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kMaxBandRows; ++r) {
+            if (r < nrows) {
+                float* row = smem_f + r * Pr;
+                const int n = 4 * n4;
+                row[swr(n)] = acc[r].x;
+                row[swr(n + 1)] = acc[r].y;
+                row[swr(n + 2)] = acc[r].z;
+                row[swr(n + 3)] = acc[r].w;
+            }
+        }
     }
-    if (lane == 0) colmax[l] = m;
+    __syncthreads();
+    rows_r2c_write(P, mb, nrows);
 }
 
 // --------------------------------------------------------------------------
@@ -464,9 +505,11 @@ __global__ void __launch_bounds__(256) k_colmax(const float* __restrict__ g, int
 // One block of CB spectrum columns per CTA; the blocked layout
 // [kb][m][CB] makes every load and store contiguous.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ PieceDev P, const cf* __restrict__ in,
-                                                 cf* __restrict__ out, int adjoint) {
-    const int kb = blockIdx.x;
+__global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ PieceBatch B, int adjoint) {
+    int kb;
+    const PieceDev& P = B.p[batch_piece(B, kb)];
+    const cf* in = P.spec;   // in place: the CTA owns its column block
+    cf* out = P.spec;
     const int CB = P.CB, Pt = P.Ptheta, Nth = P.Ntheta;
     cf* A = reinterpret_cast<cf*>(smem_f);
     const cf* src = in + (size_t)kb * Nth * CB;
@@ -521,8 +564,11 @@ __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Piec
 // Inverse real FFT of a band of rows from the half spectrum (bins <= k2max,
 // the rest zero) into the real lattice P.lat[Ntheta][Nrho].
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ PieceDev P, const cf* __restrict__ spec) {
-    const int mb = blockIdx.x * P.R;
+__global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ PieceBatch B) {
+    int bx;
+    const PieceDev& P = B.p[batch_piece(B, bx)];
+    const cf* __restrict__ spec = P.spec;
+    const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int M = P.Prho / 2;
     cf* X = reinterpret_cast<cf*>(smem_f);
@@ -579,27 +625,47 @@ __device__ __forceinline__ float taps16(const float* __restrict__ lat, int Nr, i
     return s;
 }
 
-// Forward output interpolation (Eq. (17)) for the columns [l_lo, l_hi] of one
-// slowness piece, summed over its time pieces (pieces[0..np)).
-__global__ void __launch_bounds__(256) k_gather_radon(const PieceDev* __restrict__ pieces, int np,
-                                                      int l_lo, int ncol, int Ntau,
-                                                      float* __restrict__ g) {
-    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long)ncol * Ntau) return;
-    const int lc = (int)(idx / Ntau);
-    float acc = 0.f;
+// Forward output interpolation (Eq. (17)) for the columns [l_lo, l_lo + ncol)
+// of one slowness piece, summed over its time pieces (pieces[0..np)). As in
+// the adjoint, the column's outputs share its theta taps, so the 4x4 taps
+// separate: one CTA per column first spreads the four lattice rows of the
+// column's angle into a rho profile in shared memory,
+//   r[n] = sum_a B3(theta_l - theta_{m0+a}) H[m0 + a][n],
+// then every output takes 4 taps of it; the pieces are summed per output in
+// a fixed order (shared memory: [nrho_max] profile, [Ntau] sums).
+__global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restrict__ pieces, int np,
+                                                        int l_lo, int Ntau, int nrho_max,
+                                                        float* __restrict__ g) {
+    const int l = l_lo + blockIdx.x;
+    float* prof = smem_f;
+    float* acc = smem_f + nrho_max;
+    for (int i = threadIdx.x; i < Ntau; i += blockDim.x) acc[i] = 0.f;
     for (int p = 0; p < np; ++p) {
         const PieceDev& P = pieces[p];
-        const int2 e = __ldg(reinterpret_cast<const int2*>(P.rtab + idx));
-        if (e.x < 0) continue;
-        float wr[4];
-        b3_weights(__int_as_float(e.y), wr);
+        const int lc = l - P.l_lo;
+        const int Nr = P.Nrho;
         const float4 w4 = __ldg(P.colw + lc);
-        const float wt[4] = {w4.x, w4.y, w4.z, w4.w};
-        const int m0 = __ldg(P.colm0 + lc);
-        acc += __ldg(P.colscale + lc) * taps16(P.lat, P.Nrho, m0, e.x, wt, wr);
+        const float sc = __ldg(P.colscale + lc);
+        const float* r0 = P.lat + (size_t)__ldg(P.colm0 + lc) * Nr;
+        __syncthreads();   // the previous piece's taps are read
+        for (int n = threadIdx.x; n < Nr; n += blockDim.x) {
+            const float a0 = __ldg(r0 + n), a1 = __ldg(r0 + Nr + n);
+            const float a2 = __ldg(r0 + 2 * Nr + n), a3 = __ldg(r0 + 3 * Nr + n);
+            prof[n] = w4.x * a0 + w4.y * a1 + w4.z * a2 + w4.w * a3;
+        }
+        __syncthreads();
+        const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * Ntau);
+        for (int i = threadIdx.x; i < Ntau; i += blockDim.x) {
+            const int2 e = __ldg(rt + i);
+            if (e.x < 0) continue;
+            float wr[4];
+            b3_weights(__int_as_float(e.y), wr);
+            const float* r = prof + e.x;
+            acc[i] += sc * (wr[0] * r[0] + wr[1] * r[1] + wr[2] * r[2] + wr[3] * r[3]);
+        }
     }
-    g[(size_t)l_lo * Ntau + idx] = acc;
+    float* gl = g + (size_t)l * Ntau;
+    for (int i = threadIdx.x; i < Ntau; i += blockDim.x) gl[i] = acc[i];
 }
 
 // Adjoint of the gridding (transpose of Eq. (15)): every gather sample reads
@@ -823,56 +889,90 @@ static int set_smem(const void* fn, size_t bytes) {
     return e == cudaSuccess ? 0 : (int)e;
 }
 
-int launch_grid_tiles(const PieceDev& P, const float* f, void* stream) {
-    cudaError_t e = cudaMemsetAsync(P.lat, 0, (size_t)P.Ntheta * P.Nrho * sizeof(float), (cudaStream_t)stream);
-    if (e != cudaSuccess) return (int)e;
-    if (P.nunits > 0) k_grid_tiles<<<P.nunits, kUnitChunks, 0, (cudaStream_t)stream>>>(P, f);
+// Batch descriptor of n pieces with count(piece) blocks each; returns the
+// total number of blocks.
+template <class F>
+static int make_batch(const PieceDev* P, int n, PieceBatch& B, F&& count) {
+    B.n = n;
+    int total = 0;
+    for (int k = 0; k < kMaxBatch; ++k) {
+        B.first[k] = total;
+        if (k < n) {
+            B.p[k] = P[k];
+            total += count(P[k]);
+        }
+    }
+    B.first[kMaxBatch] = total;
+    return total;
+}
+
+int launch_grid_tiles(const PieceDev* P, int n, const float* f, void* stream) {
+    PieceBatch B;
+    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nunits; });
+    if (nb > 0) k_grid_tiles<<<nb, kUnitChunks, 0, (cudaStream_t)stream>>>(B, f);
     return check_launch();
 }
 
-int launch_rows_r2c(const PieceDev& P, cf* spec, void* stream) {
-    const size_t sm = scatter_smem_bytes(P);
+static size_t max_over(const PieceDev* P, int n, size_t (*fn)(const PieceDev&)) {
+    size_t m = 0;
+    for (int k = 0; k < n; ++k) m = std::max(m, fn(P[k]));
+    return m;
+}
+
+int launch_rows_r2c(const PieceDev* P, int n, void* stream) {
+    const size_t sm = max_over(P, n, scatter_smem_bytes);
     if (int e = set_smem((const void*)k_rows_r2c, sm)) return e;
-    k_rows_r2c<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, spec);
+    PieceBatch B;
+    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
+    if (nb > 0) k_rows_r2c<<<nb, 512, sm, (cudaStream_t)stream>>>(B);
     return check_launch();
 }
 
-int launch_scatter_radon_rows(const PieceDev& P, const float* g, const float* colmax, cf* spec, void* stream) {
-    const size_t sm = scatter_smem_bytes(P);
-    if (int e = set_smem((const void*)k_scatter_radon, sm)) return e;
-    k_scatter_radon<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, g, colmax, spec);
+int launch_col_profiles(const PieceDev* P, int n, const float* g, void* stream) {
+    const size_t sm = max_over(P, n, [](const PieceDev& q) { return (size_t)q.Nrho * sizeof(int); });
+    if (int e = set_smem((const void*)k_col_profiles, sm)) return e;
+    PieceBatch B;
+    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.l_hi - q.l_lo + 1; });
+    if (nb > 0) k_col_profiles<<<nb, 256, sm, (cudaStream_t)stream>>>(B, g);
     return check_launch();
 }
 
-int launch_colmax(const float* g, int Nq, int Ntau, float* colmax, void* stream) {
-    k_colmax<<<(Nq + 7) / 8, 256, 0, (cudaStream_t)stream>>>(g, Nq, Ntau, colmax);
+int launch_band_rows(const PieceDev* P, int n, void* stream) {
+    const size_t sm = max_over(P, n, scatter_smem_bytes);
+    if (int e = set_smem((const void*)k_band_rows, sm)) return e;
+    PieceBatch B;
+    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
+    if (nb > 0) k_band_rows<<<nb, 512, sm, (cudaStream_t)stream>>>(B);
     return check_launch();
 }
 
-int launch_colconv(const PieceDev& P, const cf* in, cf* out, int adjoint, void* stream) {
-    const size_t sm = colconv_smem_bytes(P);
+int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream) {
+    const size_t sm = max_over(P, n, colconv_smem_bytes);
     if (int e = set_smem((const void*)k_colconv, sm)) return e;
-    k_colconv<<<P.nkb, 512, sm, (cudaStream_t)stream>>>(P, in, out, adjoint);
+    PieceBatch B;
+    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nkb; });
+    if (nb > 0) k_colconv<<<nb, 512, sm, (cudaStream_t)stream>>>(B, adjoint);
     return check_launch();
 }
 
-int launch_rows_c2r(const PieceDev& P, const cf* spec, void* stream) {
-    const size_t sm = scatter_smem_bytes(P);
+int launch_rows_c2r(const PieceDev* P, int n, void* stream) {
+    const size_t sm = max_over(P, n, scatter_smem_bytes);
     if (int e = set_smem((const void*)k_rows_c2r, sm)) return e;
-    k_rows_c2r<<<P.nbands, 512, sm, (cudaStream_t)stream>>>(P, spec);
+    PieceBatch B;
+    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
+    if (nb > 0) k_rows_c2r<<<nb, 512, sm, (cudaStream_t)stream>>>(B);
     return check_launch();
 }
 
-int launch_gather_radon(const PieceDev* pieces, int npieces, const PieceDev* dev_pieces, int l_lo,
-                        int l_hi, float* g, void* stream) {
-    (void)pieces;
+int launch_interp_columns(const PieceDev* pieces, int npieces, const PieceDev* dev_pieces, int l_lo,
+                          int l_hi, float* g, void* stream) {
     const int ncol = l_hi - l_lo + 1;
     const int Ntau = pieces[0].Ntau;
-    const long total = (long)ncol * Ntau;
-    const int bs = 256;
-    const long nb = (total + bs - 1) / bs;
-    k_gather_radon<<<(unsigned)nb, bs, 0, (cudaStream_t)stream>>>(dev_pieces, npieces, l_lo, ncol,
-                                                                 Ntau, g);
+    int nrho_max = 0;
+    for (int p = 0; p < npieces; ++p) nrho_max = std::max(nrho_max, pieces[p].Nrho);
+    const size_t sm = ((size_t)nrho_max + Ntau) * sizeof(float);
+    if (int e = set_smem((const void*)k_interp_columns, sm)) return e;
+    k_interp_columns<<<ncol, 256, sm, (cudaStream_t)stream>>>(dev_pieces, npieces, l_lo, Ntau, nrho_max, g);
     return check_launch();
 }
 

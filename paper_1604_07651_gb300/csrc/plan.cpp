@@ -195,9 +195,8 @@ struct radon_plan_s {
     std::vector<std::pair<int, int>> qpieces;    // columns of each slowness piece
     std::vector<int> qfirst, qcount;             // pieces of each slowness piece
     PieceDev* dev_pieces = nullptr;
-    cf* spec1 = nullptr;
-    cf* spec2 = nullptr;
-    float* colmax = nullptr;                     // [Nq] max|g| of each column (adjoint scatter scale)
+    float* lat_all = nullptr;                    // every piece's lattice, back to back
+    size_t lat_bytes = 0;
     std::vector<void*> allocs;
     size_t bytes = 0;
     // per-stage timing
@@ -596,10 +595,10 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
                         " above the block FFT's limit (4096, or 6144 = 3*2048)");
     // rows per band: 3 (more rows mean fewer, longer CTAs and worse balance;
     // fewer mean more duplicated samples; 3 measured best on 2048^2 gathers)
-    int R = (int)std::min<size_t>(3, (size_t)smem_max / (h.Prho * sizeof(float)));
+    int R = (int)std::min<size_t>(3, (size_t)smem_max / (h.Prho * sizeof(float)));   // <= kMaxBandRows
     if (const char* env = std::getenv("HRADON_ROWS_PER_BAND")) {   // tuning knob
         const int r = std::atoi(env);
-        if (r >= 1 && (size_t)r * h.Prho * sizeof(float) <= (size_t)smem_max) R = r;
+        if (r >= 1 && r <= kMaxBandRows && (size_t)r * h.Prho * sizeof(float) <= (size_t)smem_max) R = r;
     }
     if (R < 1) {
         R = 1;
@@ -672,13 +671,6 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
             }
         }
     }
-    std::vector<int> order_r(P.nbands);
-    for (int b = 0; b < P.nbands; ++b) order_r[b] = b;
-    std::stable_sort(order_r.begin(), order_r.end(), [&](int x, int y) {
-        const int wx = lband[x].y >= lband[x].x ? lband[x].y - lband[x].x + 1 : 0;
-        const int wy = lband[y].y >= lband[y].x ? lband[y].y - lband[y].x + 1 : 0;
-        return wx > wy;
-    });
     // twiddles
     const int M = h.Prho / 2;
     std::vector<cf> twM(M), twP(M + 1), twT(h.Ptheta);
@@ -692,8 +684,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     if (radon_status s = kernel_spectrum(p, h, CB, P.nkb, K)) return s;
 
     radon_status s = RADON_OK;
-    if ((s = dev_upload(p, order_r, &P.order_r)) ||
-        (s = dev_upload(p, lband, &P.lband)) ||
+    if ((s = dev_upload(p, lband, &P.lband)) ||
         (s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
         (s = dev_upload(p, colscale, &P.colscale)) || (s = dev_upload(p, K, &P.K)) ||
         (s = dev_upload(p, twM, &P.twM)) || (s = dev_upload(p, twP, &P.twP)) ||
@@ -740,14 +731,15 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.rtab = (const RadonEnt*)tab;
     if (int e = launch_radon_table(A, dqb2, (RadonEnt*)tab))
         return fail(RADON_ERR_CUDA, std::string("position table: ") + cudaGetErrorString((cudaError_t)e));
-    // fixed-point bound of the adjoint scatter: per band, the exponent of the
-    // largest total weight scale * wt * wr one of its cells collects from all
-    // outputs (computed with the kernel's own float weights)
+    // fixed-point bound of the adjoint column profiles: per column, the
+    // exponent of the largest total weight scale * wr one of its rho cells
+    // collects from the column's outputs (the kernel's own float weights)
     {
         std::vector<RadonEnt> rt((size_t)ncol * d.Ntau);
         if (cudaMemcpy(rt.data(), tab, rt.size() * sizeof(RadonEnt), cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(RADON_ERR_CUDA, "reading back the output position table failed");
-        std::vector<double> rows((size_t)h.Ntheta * h.Nrho, 0.0), prof(h.Nrho);
+        std::vector<double> prof(h.Nrho);
+        std::vector<int> colsh(ncol);
         for (int lc = 0; lc < ncol; ++lc) {
             std::fill(prof.begin(), prof.end(), 0.0);
             for (int i = 0; i < d.Ntau; ++i) {
@@ -757,25 +749,20 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
                 b3_weights(e.fr, wr);
                 for (int c = 0; c < 4; ++c) prof[e.n0 + c] += (double)colscale[lc] * wr[c];
             }
-            const float wt[4] = {colw[lc].x, colw[lc].y, colw[lc].z, colw[lc].w};
-            for (int a = 0; a < 4; ++a) {
-                double* row = rows.data() + (size_t)(colm0[lc] + a) * h.Nrho;
-                for (int n = 0; n < h.Nrho; ++n) row[n] += wt[a] * prof[n];
-            }
+            const double cmax = *std::max_element(prof.begin(), prof.end());
+            colsh[lc] = 28 - std::ilogb(cmax > 0 ? cmax : 1.0);
         }
-        std::vector<int> bandsh(P.nbands);
-        for (int b = 0; b < P.nbands; ++b) {
-            double cmax = 0.0;
-            for (size_t i = (size_t)b * R * h.Nrho; i < std::min((size_t)(b + 1) * R, (size_t)h.Ntheta) * h.Nrho; ++i)
-                cmax = std::max(cmax, rows[i]);
-            bandsh[b] = 28 - std::ilogb(cmax > 0 ? cmax : 1.0);
-        }
-        if ((s = dev_upload(p, bandsh, &P.bandsh))) return s;
+        if ((s = dev_upload(p, colsh, &P.colsh))) return s;
     }
-    void* lat = nullptr;
-    if ((s = dev_alloc(p, (size_t)h.Ntheta * h.Nrho * sizeof(float), &lat))) return s;
-    P.lat = (float*)lat;
+    P.hpitch = (h.Nrho + 3) & ~3;
     return RADON_OK;
+}
+
+size_t round256b(size_t v) { return (v + 255) & ~(size_t)255; }
+size_t piece_lattice_bytes(const PieceDev& P) { return round256b((size_t)P.Ntheta * P.Nrho * sizeof(float)); }
+size_t piece_spectrum_bytes(const PieceDev& P) { return round256b((size_t)P.nkb * P.CB * P.Ntheta * sizeof(cf)); }
+size_t piece_profile_bytes(const PieceDev& P) {
+    return round256b((size_t)(P.l_hi - P.l_lo + 1) * P.hpitch * sizeof(float));
 }
 
 void destroy_plan(radon_plan_s* p) {
@@ -894,17 +881,30 @@ extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* 
         }
         p->qcount.push_back((int)tps.size());
     }
-    // shared spectrum buffers and the device copy of the piece descriptors
-    size_t spec = 0;
-    for (auto& h : p->pieces) spec = std::max(spec, (size_t)h.dev.nkb * h.dev.CB * h.dev.Ntheta);
-    void* a = nullptr;
+    // per-piece work buffers: lattices back to back (one clear per forward),
+    // spectra (the column pass works in place), adjoint column profiles
+    size_t lat_b = 0, spec_b = 0, prof_b = 0;
+    for (auto& h : p->pieces) {
+        lat_b += piece_lattice_bytes(h.dev);
+        spec_b += piece_spectrum_bytes(h.dev);
+        prof_b += piece_profile_bytes(h.dev);
+    }
+    void *lat = nullptr, *spec = nullptr, *prof = nullptr;
     radon_status s = RADON_OK;
-    if ((s = dev_alloc(p, spec * sizeof(cf), &a))) { destroy_plan(p); return s; }
-    p->spec1 = (cf*)a;
-    if ((s = dev_alloc(p, spec * sizeof(cf), &a))) { destroy_plan(p); return s; }
-    p->spec2 = (cf*)a;
-    if ((s = dev_alloc(p, (size_t)p->d.Nq * sizeof(float), &a))) { destroy_plan(p); return s; }
-    p->colmax = (float*)a;
+    if ((s = dev_alloc(p, lat_b, &lat)) || (s = dev_alloc(p, spec_b, &spec)) || (s = dev_alloc(p, prof_b, &prof))) {
+        destroy_plan(p);
+        return s;
+    }
+    p->lat_all = (float*)lat;
+    p->lat_bytes = lat_b;
+    for (auto& h : p->pieces) {
+        h.dev.lat = (float*)lat;
+        h.dev.spec = (cf*)spec;
+        h.dev.prof = (float*)prof;
+        lat = (char*)lat + piece_lattice_bytes(h.dev);
+        spec = (char*)spec + piece_spectrum_bytes(h.dev);
+        prof = (char*)prof + piece_profile_bytes(h.dev);
+    }
     std::vector<PieceDev> devs;
     for (auto& h : p->pieces) devs.push_back(h.dev);
     const PieceDev* dp = nullptr;
@@ -931,49 +931,58 @@ static radon_status cuda_status(int e, const char* what) {
     return fail(RADON_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString((cudaError_t)e));
 }
 
-extern "C" radon_status radon_fwd(radon_plan p, const float* f, float* g, void* stream) {
-    if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
-    if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
-    DeviceGuard guard(p->device);
+// The forward chain over the pieces `P` (host copies; `dP` the same on the
+// device), lattices in [lat, lat + lat_bytes). Every stage is one launch per
+// group of at most kMaxBatch pieces; the output interpolation is one launch
+// per slowness piece.
+static radon_status run_forward(radon_plan_s* p, const PieceDev* P, const PieceDev* dP, float* lat,
+                                size_t lat_bytes, const float* f, float* g, void* stream) {
+    const int np = (int)p->pieces.size();
+    double b_samp = 0, b_lat = 0, b_spec = 0, b_ker = 0;
+    for (int i = 0; i < np; ++i) {
+        b_samp += bytes_samples(P[i]);
+        b_lat += bytes_lattice(P[i]);
+        b_spec += bytes_spectrum(P[i]);
+        b_ker += bytes_kernel(P[i]);
+    }
+    auto groups = [&](auto&& launch) {
+        for (int i = 0; i < np; i += kMaxBatch)
+            if (int e = launch(P + i, std::min(kMaxBatch, np - i))) return e;
+        return 0;
+    };
+    if (radon_status s = cuda_status(
+            timed(p, 0, b_samp + b_lat, stream,
+                  [&] {
+                      if (cudaError_t e = cudaMemsetAsync(lat, 0, lat_bytes, (cudaStream_t)stream)) return (int)e;
+                      return groups([&](const PieceDev* q, int n) { return launch_grid_tiles(q, n, f, stream); });
+                  }),
+            "gridding"))
+        return s;
+    if (radon_status s = cuda_status(
+            timed(p, 1, b_lat + b_spec, stream,
+                  [&] { return groups([&](const PieceDev* q, int n) { return launch_rows_r2c(q, n, stream); }); }),
+            "row FFT"))
+        return s;
+    if (radon_status s = cuda_status(
+            timed(p, 2, 2 * b_spec + b_ker, stream,
+                  [&] { return groups([&](const PieceDev* q, int n) { return launch_colconv(q, n, 0, stream); }); }),
+            "convolution"))
+        return s;
+    if (radon_status s = cuda_status(
+            timed(p, 3, b_spec + b_lat, stream,
+                  [&] { return groups([&](const PieceDev* q, int n) { return launch_rows_c2r(q, n, stream); }); }),
+            "inverse row FFT"))
+        return s;
     for (size_t qi = 0; qi < p->qpieces.size(); ++qi) {
         const int first = p->qfirst[qi], count = p->qcount[qi];
-        for (int t = 0; t < count; ++t) {
-            const PieceDev& P = p->pieces[first + t].dev;
-            const double bs = bytes_spectrum(P);
-            if (radon_status s = cuda_status(
-                    timed(p, 0, bytes_samples(P) + bytes_lattice(P), stream,
-                          [&] { return launch_grid_tiles(P, f, stream); }),
-                    "gridding"))
-                return s;
-            if (radon_status s = cuda_status(
-                    timed(p, 1, bytes_lattice(P) + bs, stream,
-                          [&] { return launch_rows_r2c(P, p->spec1, stream); }),
-                    "row FFT"))
-                return s;
-            if (radon_status s = cuda_status(
-                    timed(p, 2, 2 * bs + bytes_kernel(P), stream,
-                          [&] { return launch_colconv(P, p->spec1, p->spec2, 0, stream); }),
-                    "convolution"))
-                return s;
-            if (radon_status s = cuda_status(
-                    timed(p, 3, bs + bytes_lattice(P), stream,
-                          [&] { return launch_rows_c2r(P, p->spec2, stream); }),
-                    "inverse row FFT"))
-                return s;
-        }
-        std::vector<PieceDev> host(count);
-        double lat = 0;
-        for (int t = 0; t < count; ++t) {
-            host[t] = p->pieces[first + t].dev;
-            lat += bytes_lattice(host[t]);
-        }
+        double bl = 0;
+        for (int t = 0; t < count; ++t) bl += bytes_lattice(P[first + t]);
         const double gb = 4.0 * p->d.Ntau * (p->qpieces[qi].second - p->qpieces[qi].first + 1);
         if (radon_status s = cuda_status(
-                timed(p, 4, lat + gb, stream,
+                timed(p, 4, bl + gb, stream,
                       [&] {
-                          return launch_gather_radon(host.data(), count, p->dev_pieces + first,
-                                                     p->qpieces[qi].first, p->qpieces[qi].second, g,
-                                                     stream);
+                          return launch_interp_columns(P + first, count, dP + first, p->qpieces[qi].first,
+                                                       p->qpieces[qi].second, g, stream);
                       }),
                 "interpolation"))
             return s;
@@ -981,39 +990,62 @@ extern "C" radon_status radon_fwd(radon_plan p, const float* f, float* g, void* 
     return RADON_OK;
 }
 
+static std::vector<PieceDev> host_pieces(const radon_plan_s* p) {
+    std::vector<PieceDev> v;
+    for (auto& h : p->pieces) v.push_back(h.dev);
+    return v;
+}
+
+extern "C" radon_status radon_fwd(radon_plan p, const float* f, float* g, void* stream) {
+    if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
+    if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    DeviceGuard guard(p->device);
+    const std::vector<PieceDev> P = host_pieces(p);
+    return run_forward(p, P.data(), p->dev_pieces, p->lat_all, p->lat_bytes, f, g, stream);
+}
+
 extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* stream) {
     if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
     if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
     DeviceGuard guard(p->device);
-    if (radon_status s = cuda_status(
-            timed(p, 9, 4.0 * p->d.Nq * p->d.Ntau, stream,
-                  [&] { return launch_colmax(g, p->d.Nq, p->d.Ntau, p->colmax, stream); }),
-            "adjoint input maximum"))
-        return s;
-    double lat = 0;
-    for (auto& h : p->pieces) {
-        const PieceDev& P = h.dev;
-        const double bs = bytes_spectrum(P);
-        lat += bytes_lattice(P);
-        const double gb = 4.0 * p->d.Ntau * (P.l_hi - P.l_lo + 1);
-        if (radon_status s = cuda_status(
-                timed(p, 5, gb + bs, stream, [&] { return launch_scatter_radon_rows(P, g, p->colmax, p->spec1, stream); }),
-                "adjoint interpolation"))
-            return s;
-        if (radon_status s = cuda_status(
-                timed(p, 6, 2 * bs + bytes_kernel(P), stream,
-                      [&] { return launch_colconv(P, p->spec1, p->spec2, 1, stream); }),
-                "adjoint convolution"))
-            return s;
-        if (radon_status s = cuda_status(
-                timed(p, 7, bs + bytes_lattice(P), stream, [&] { return launch_rows_c2r(P, p->spec2, stream); }),
-                "inverse row FFT"))
-            return s;
+    const std::vector<PieceDev> P = host_pieces(p);
+    const int np = (int)P.size();
+    double b_lat = 0, b_spec = 0, b_ker = 0, b_g = 0, b_h = 0;
+    for (const PieceDev& q : P) {
+        b_lat += bytes_lattice(q);
+        b_spec += bytes_spectrum(q);
+        b_ker += bytes_kernel(q);
+        b_g += 4.0 * q.Ntau * (q.l_hi - q.l_lo + 1);
+        b_h += 4.0 * (q.l_hi - q.l_lo + 1) * q.Nrho;
     }
-    return cuda_status(timed(p, 8, lat + 4.0 * p->d.Nt * p->d.Nx, stream,
+    auto groups = [&](auto&& launch) {
+        for (int i = 0; i < np; i += kMaxBatch)
+            if (int e = launch(P.data() + i, std::min(kMaxBatch, np - i))) return e;
+        return 0;
+    };
+    if (radon_status s = cuda_status(
+            timed(p, 9, b_g + b_h, stream,
+                  [&] { return groups([&](const PieceDev* q, int n) { return launch_col_profiles(q, n, g, stream); }); }),
+            "adjoint interpolation (profiles)"))
+        return s;
+    if (radon_status s = cuda_status(
+            timed(p, 5, b_h + b_spec, stream,
+                  [&] { return groups([&](const PieceDev* q, int n) { return launch_band_rows(q, n, stream); }); }),
+            "adjoint interpolation (bands)"))
+        return s;
+    if (radon_status s = cuda_status(
+            timed(p, 6, 2 * b_spec + b_ker, stream,
+                  [&] { return groups([&](const PieceDev* q, int n) { return launch_colconv(q, n, 1, stream); }); }),
+            "adjoint convolution"))
+        return s;
+    if (radon_status s = cuda_status(
+            timed(p, 7, b_spec + b_lat, stream,
+                  [&] { return groups([&](const PieceDev* q, int n) { return launch_rows_c2r(q, n, stream); }); }),
+            "inverse row FFT"))
+        return s;
+    return cuda_status(timed(p, 8, b_lat + 4.0 * p->d.Nt * p->d.Nx, stream,
                              [&] {
-                                 return launch_gather_samples(p->dev_pieces, (int)p->pieces.size(), p->d.Nt,
-                                                              p->d.Nx, f, stream);
+                                 return launch_gather_samples(p->dev_pieces, np, p->d.Nt, p->d.Nx, f, stream);
                              }),
                        "adjoint gridding");
 }
@@ -1158,21 +1190,14 @@ extern "C" const char* radon_version(void) { return "hradon 0.1 (sm_103a)"; }
 // ---------------------------------------------------------------------------
 // Forward transform on caller-given work memory (used by radon_fwd_noalloc in
 // noalloc.cu). Layout of the area: the device copies of the piece
-// descriptors, the two spectrum buffers, then one lattice per piece, each
-// 256-byte aligned. Every byte the kernels read there is written earlier in
-// the same call, so nothing has to be cleared.
+// descriptors, every piece's lattice back to back, then every piece's
+// spectrum, each 256-byte aligned. Every byte the kernels read there is
+// written earlier in the same call, so nothing has to be cleared beforehand.
 // ---------------------------------------------------------------------------
 namespace hr {
 
 namespace {
 const int kWorkMaxPieces = 32;
-size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
-
-size_t spec_elems(const radon_plan_s* p) {
-    size_t spec = 0;
-    for (auto& h : p->pieces) spec = std::max(spec, (size_t)h.dev.nkb * h.dev.CB * h.dev.Ntheta);
-    return spec;
-}
 }  // namespace
 
 int set_error(int status, const char* msg) { return fail((radon_status)status, msg); }
@@ -1181,9 +1206,8 @@ int plan_device(const radon_plan_s* p) { return p->device; }
 
 int plan_forward_work_bytes(const radon_plan_s* p, size_t* bytes) {
     if (!p || !bytes) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
-    size_t b = round256(p->pieces.size() * sizeof(PieceDev));
-    b += 2 * round256(spec_elems(p) * sizeof(cf));
-    for (auto& h : p->pieces) b += round256((size_t)h.dev.Ntheta * h.dev.Nrho * sizeof(float));
+    size_t b = round256b(p->pieces.size() * sizeof(PieceDev));
+    for (auto& h : p->pieces) b += piece_lattice_bytes(h.dev) + piece_spectrum_bytes(h.dev);
     *bytes = b;
     return RADON_OK;
 }
@@ -1203,40 +1227,27 @@ int plan_forward_in_work(radon_plan_s* p, const float* f, float* g, void* work, 
                         std::to_string(bytes));
     char* base = (char*)work;
     PieceDev* dpieces = (PieceDev*)base;
-    size_t off = round256(np * sizeof(PieceDev));
-    cf* s1 = (cf*)(base + off);
-    off += round256(spec_elems(p) * sizeof(cf));
-    cf* s2 = (cf*)(base + off);
-    off += round256(spec_elems(p) * sizeof(cf));
+    size_t off = round256b(np * sizeof(PieceDev));
+    float* lat = (float*)(base + off);
+    size_t lat_bytes = 0;
     PieceDev local[kWorkMaxPieces];
     for (int i = 0; i < np; ++i) {
         local[i] = p->pieces[i].dev;
         local[i].lat = (float*)(base + off);
-        off += round256((size_t)local[i].Ntheta * local[i].Nrho * sizeof(float));
+        local[i].prof = nullptr;
+        off += piece_lattice_bytes(local[i]);
+        lat_bytes += piece_lattice_bytes(local[i]);
+    }
+    for (int i = 0; i < np; ++i) {
+        local[i].spec = (cf*)(base + off);
+        off += piece_spectrum_bytes(local[i]);
     }
     DeviceGuard guard(p->device);
     // pageable source: the copy is staged before the call returns
     if (cudaMemcpyAsync(dpieces, local, np * sizeof(PieceDev), cudaMemcpyHostToDevice,
                         (cudaStream_t)stream) != cudaSuccess)
         return fail(RADON_ERR_CUDA, "copy of the piece descriptors failed");
-    for (size_t qi = 0; qi < p->qpieces.size(); ++qi) {
-        const int first = p->qfirst[qi], count = p->qcount[qi];
-        for (int t = 0; t < count; ++t) {
-            const PieceDev& P = local[first + t];
-            if (radon_status s = cuda_status(launch_grid_tiles(P, f, stream), "gridding")) return s;
-            if (radon_status s = cuda_status(launch_rows_r2c(P, s1, stream), "row FFT")) return s;
-            if (radon_status s = cuda_status(launch_colconv(P, s1, s2, 0, stream), "convolution"))
-                return s;
-            if (radon_status s = cuda_status(launch_rows_c2r(P, s2, stream), "inverse row FFT"))
-                return s;
-        }
-        if (radon_status s = cuda_status(launch_gather_radon(local + first, count, dpieces + first,
-                                                             p->qpieces[qi].first, p->qpieces[qi].second,
-                                                             g, stream),
-                                         "interpolation"))
-            return s;
-    }
-    return RADON_OK;
+    return run_forward(p, local, dpieces, lat, lat_bytes, f, g, stream);
 }
 
 }  // namespace hr

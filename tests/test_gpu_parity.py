@@ -205,7 +205,7 @@ def test_edge_cases(hr, oracle_direct):
 
 
 def test_fixed_point_scale_range(hr):
-    """The gridding and the adjoint scatter accumulate in fixed point scaled
+    """The gridding and the adjoint column profiles accumulate in fixed point scaled
     by the input's own maximum: the transforms stay linear (to FP32 rounding)
     across the whole float range, and a spike well above the rest of the
     data does not wipe out the small values beside it."""
