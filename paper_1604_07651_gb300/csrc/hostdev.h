@@ -103,6 +103,51 @@ HD cf unit_root(int k, int dir) {
     return {cos16(i), dir * cos16(i - 4)};   // sin(x) = cos(x - pi/2)
 }
 
+// exp(dir * 2 pi i m / 12) for the in-register DFTs of size 6 and 12; m is
+// a compile-time constant after unrolling.
+HD float cos12(int i) {
+    switch (((i % 12) + 12) % 12) {
+        case 0: return 1.0f;
+        case 1: case 11: return 0.86602540378443864676f;   // sqrt(3)/2
+        case 2: case 10: return 0.5f;
+        case 3: case 9: return 0.0f;
+        case 4: case 8: return -0.5f;
+        case 5: case 7: return -0.86602540378443864676f;
+        default: return -1.0f;
+    }
+}
+HD cf root12(int m, int dir) { return {cos12(m), dir * cos12(m - 3)}; }
+
+// Size 6 as 3 x 2 and size 12 as 3 x 4 (Cooley-Tukey with n = F n1 + n2,
+// k = k1 + 3 k2): Y[n2][k1] = DFT3 over n1 of x[F n1 + n2], times
+// W^(n2 k1), then X[k1 + 3 k2] = DFT-F over n2.
+template <int F>
+HD void dft_3xF(cf v[3 * F], int dir) {
+    cf y[F][3];
+HD_UNROLL
+    for (int n2 = 0; n2 < F; ++n2) {
+HD_UNROLL
+        for (int n1 = 0; n1 < 3; ++n1) y[n2][n1] = v[F * n1 + n2];
+        dft_small<3>(y[n2], dir);
+    }
+HD_UNROLL
+    for (int k1 = 0; k1 < 3; ++k1) {
+        cf z[F];
+HD_UNROLL
+        for (int n2 = 0; n2 < F; ++n2)
+            z[n2] = (n2 * k1 != 0) ? cmul(y[n2][k1], root12(n2 * k1 * (12 / (3 * F)), dir)) : y[n2][k1];
+        dft_small<F>(z, dir);
+HD_UNROLL
+        for (int k2 = 0; k2 < F; ++k2) v[k1 + 3 * k2] = z[k2];
+    }
+}
+
+template <>
+HD void dft_small<6>(cf v[6], int dir) { dft_3xF<2>(v, dir); }
+
+template <>
+HD void dft_small<12>(cf v[12], int dir) { dft_3xF<4>(v, dir); }
+
 // Size 8 as 2 x 4: inputs x[2 n1 + n2], X[k1 + 4 k2].
 template <>
 HD void dft_small<8>(cf v[8], int dir) {
@@ -146,12 +191,13 @@ HD_UNROLL
 // [0, n/R). tw[k] = exp(-2 pi i k / n), k < n (the forward twiddles; the
 // inverse, dir = +1, uses their conjugates).
 // Multiplies v[r] by w^r (conj(w)^r for dir = +1), r = 1..R-1, with
-// w = tw[t1] = exp(-2 pi i t1 / n). Radix 16 and 8 read only w and w^4 from
+// w = tw[t1] = exp(-2 pi i t1 / n). Radix 16, 12 and 8 read only w and w^4 from
 // the table and form w^(4a+b) = (w^4)^a w^b with at most three complex
-// products each (relative error a few ulp); smaller radices read every power.
+// products each (relative error a few ulp), as does radix 12; smaller
+// radices read every power.
 template <int R>
 HD void apply_twiddles(const cf* tw, int t1, int dir, cf v[R]) {
-    if (R == 16 || R == 8) {
+    if (R == 16 || R == 12 || R == 8) {
         const cf w1 = tw[t1], w4 = tw[4 * t1];
         const cf w2 = cmul(w1, w1);
         const cf w3 = cmul(w2, w1);
@@ -198,19 +244,26 @@ HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int lgNs, int j
     stockham_store<R>(out, Ns, lgNs, j, dir, v);
 }
 
-// Radix plan of n = 2^a 3^b (b <= 1): radix 16 while possible, one radix
-// 8, 4 or 2 for the remaining power of two, radix 3 last (so that every
-// stage sees a power-of-two Ns). Returns the number of stages, or -1 if n
-// has another prime factor or more than one factor 3.
+// Radix plan of n = 2^a 3^b (b <= 1): radix 16 while possible, then the
+// rest r = n / 16^k in one stage when r is 2, 3, 4, 6, 8 or 12, else (r = 24)
+// radix 8 followed by radix 3; a factor 3 is always in the last stage, so
+// every stage sees a power-of-two Ns. Returns the number of stages, or -1 if
+// n has another prime factor or more than one factor 3.
 HD int fft_radices(int n, int rad[32]) {
+    int m = n;
+    if (m % 3 == 0) m /= 3;
+    if (m < 1 || (m & (m - 1)) != 0) return -1;   // another prime or a second factor 3
     int k = 0;
-    int three = 0;
-    if (n % 3 == 0) { n /= 3; three = 1; }
-    if (n % 3 == 0) return -1;
-    while (n % 16 == 0) { rad[k++] = 16; n /= 16; }
-    if (n == 8 || n == 4 || n == 2) { rad[k++] = n; n = 1; }
-    if (n != 1) return -1;
-    if (three) rad[k++] = 3;
+    while (n % 16 == 0) {
+        rad[k++] = 16;
+        n /= 16;
+    }
+    if (n == 24) {
+        rad[k++] = 8;
+        rad[k++] = 3;
+    } else if (n != 1) {
+        rad[k++] = n;   // 2, 3, 4, 6, 8 or 12
+    }
     return k;
 }
 

@@ -73,10 +73,21 @@ __device__ __forceinline__ void fft_stage(cf* buf, int n, int nrows, int Ns, int
 
 // Block-cooperative in-place FFT of `nrows` sequences of length n
 // (unnormalised; DIR = -1 forward, +1 inverse). The radix plan is radix 16
-// stages, at most one radix 8, 4 or 2 stage, and at most one radix 3 stage
+// stages and one last stage of radix 2, 3, 4, 6, 8 or 12 (or 8 then 3)
 // (fft_radices); written as straight-line code so that each stage keeps its
-// own small register footprint. Supported: n = 2^a <= 4096 and
-// n = 3 * 2^a <= 6144 with 512 threads.
+// own small register footprint. Q, the butterflies a thread holds at once,
+// is chosen so that a stage covers every row in one round where the
+// registers allow. Supported: n = 2^a <= 4096 and n = 3 * 2^a <= 6144 with
+// 512 threads.
+template <int R, int QMAX, int DIR>
+__device__ __forceinline__ void fft_stage_q(cf* buf, int n, int nrows, int Ns, int lgNs, const cf* __restrict__ tw) {
+    const int need = (n / R) * nrows;
+    const int nthr = (int)blockDim.x;
+    if (QMAX >= 4 && need > 2 * nthr) fft_stage<R, 4, DIR>(buf, n, nrows, Ns, lgNs, tw);
+    else if (QMAX >= 2 && need > nthr) fft_stage<R, 2, DIR>(buf, n, nrows, Ns, lgNs, tw);
+    else fft_stage<R, 1, DIR>(buf, n, nrows, Ns, lgNs, tw);
+}
+
 template <int DIR>
 __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* __restrict__ tw,
                                           const FftPlan& fp) {
@@ -87,29 +98,19 @@ __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* _
         Ns <<= 4;
         lg += 4;
     }
-    if (s < fp.nst && fp.rad[s] != 3) {
+    if (s < fp.nst) {
         const int R = fp.rad[s];
-        const bool q1 = n / R <= (int)blockDim.x;
-        if (R == 8) {
-            if (q1) fft_stage<8, 1, DIR>(buf, n, nrows, Ns, lg, tw);
-            else fft_stage<8, 2, DIR>(buf, n, nrows, Ns, lg, tw);
-        } else if (R == 4) {
-            if (q1) fft_stage<4, 1, DIR>(buf, n, nrows, Ns, lg, tw);
-            else fft_stage<4, 2, DIR>(buf, n, nrows, Ns, lg, tw);
-        } else {
-            if (q1) fft_stage<2, 1, DIR>(buf, n, nrows, Ns, lg, tw);
-            else fft_stage<2, 2, DIR>(buf, n, nrows, Ns, lg, tw);
-        }
+        if (R == 12) fft_stage_q<12, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+        else if (R == 8) fft_stage_q<8, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+        else if (R == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        else if (R == 4) fft_stage_q<4, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        else if (R == 3) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);
+        else fft_stage_q<2, 2, DIR>(buf, n, nrows, Ns, lg, tw);
         Ns *= R;
         lg = 31 - __clz(Ns);
         ++s;
     }
-    if (s < fp.nst) {
-        const int nb = n / 3;
-        if (nb <= (int)blockDim.x) fft_stage<3, 1, DIR>(buf, n, nrows, Ns, lg, tw);
-        else if (nb <= 2 * (int)blockDim.x) fft_stage<3, 2, DIR>(buf, n, nrows, Ns, lg, tw);
-        else fft_stage<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);
-    }
+    if (s < fp.nst) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);   // after radix 8 (n / 16^k = 24)
 }
 
 // --------------------------------------------------------------------------

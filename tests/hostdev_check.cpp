@@ -42,6 +42,8 @@ static std::vector<cf> fft_emul_sw(std::vector<cf> a, int dir) {
         const int R = rad[s];
         for (int j = 0; j < n / R; ++j) {
             if (R == 16) stockham_butterfly<16>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
+            else if (R == 12) stockham_butterfly<12>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
+            else if (R == 6) stockham_butterfly<6>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
             else if (R == 8) stockham_butterfly<8>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
             else if (R == 4) stockham_butterfly<4>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
             else if (R == 2) stockham_butterfly<2>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
@@ -145,7 +147,7 @@ static double b3_error() {
 int main() {
     std::mt19937 rng(1604);
     double e = 0;
-    for (int n : {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256, 384, 512, 1024, 1536, 2048, 3072, 4096})
+    for (int n : {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 6144})
         e = std::max(e, std::max(fft_error(n, -1, rng), fft_error(n, +1, rng)));
     std::printf("fft_rel_l2 %.3e\n", e);
     e = 0;
