@@ -140,11 +140,11 @@ class Partition:
 
 
 def fft_size(n: int) -> int:
-    """Smallest size >= n of the form 2^a or 3*2^a (a >= 0)."""
+    """Smallest size >= n of the form 2^a, 3*2^a or 5*2^a (a >= 0)."""
     best = None
     p = 1
     while p < 2 * n + 2:
-        for c in (p, 3 * p):
+        for c in (p, 3 * p, 5 * p):
             if c >= n and (best is None or c < best):
                 best = c
         p *= 2

@@ -148,6 +148,69 @@ HD void dft_small<6>(cf v[6], int dir) { dft_3xF<2>(v, dir); }
 template <>
 HD void dft_small<12>(cf v[12], int dir) { dft_3xF<4>(v, dir); }
 
+// Size 5 directly: with t1 = x1 + x4, t2 = x2 + x3, t3 = x1 - x4,
+// t4 = x2 - x3 and c_m = cos(2 pi m / 5), s_m = sin(2 pi m / 5):
+// X1,4 = x0 + c1 t1 + c2 t2 +- i dir (s1 t3 + s2 t4),
+// X2,3 = x0 + c2 t1 + c1 t2 +- i dir (s2 t3 - s1 t4).
+template <>
+HD void dft_small<5>(cf v[5], int dir) {
+    const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;   // (sqrt5 - 1)/4, -(sqrt5 + 1)/4
+    const float s1 = 0.95105651629515357212f * (float)dir, s2 = 0.58778525229247312917f * (float)dir;
+    const cf t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    const cf t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+    const cf a1 = {v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y};
+    const cf a2 = {v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y};
+    const cf b1 = {s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y};
+    const cf b2 = {s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y};
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = {a1.x - b1.y, a1.y + b1.x};   // a1 + i b1
+    v[4] = {a1.x + b1.y, a1.y - b1.x};   // a1 - i b1
+    v[2] = {a2.x - b2.y, a2.y + b2.x};
+    v[3] = {a2.x + b2.y, a2.y - b2.x};
+}
+
+// cos(2 pi m / 10) and exp(dir * 2 pi i m / 10), m a compile-time constant
+// after unrolling.
+HD float cos10(int i) {
+    switch (((i % 10) + 10) % 10) {
+        case 0: return 1.0f;
+        case 1: case 9: return 0.80901699437494742410f;    // (sqrt5 + 1)/4
+        case 2: case 8: return 0.30901699437494742410f;    // (sqrt5 - 1)/4
+        case 3: case 7: return -0.30901699437494742410f;
+        case 4: case 6: return -0.80901699437494742410f;
+        default: return -1.0f;
+    }
+}
+HD float sin10(int i) {
+    switch (((i % 10) + 10) % 10) {
+        case 1: case 4: return 0.58778525229247312917f;    // sin 36 deg = sin 144 deg
+        case 2: case 3: return 0.95105651629515357212f;    // sin 72 deg = sin 108 deg
+        case 6: case 9: return -0.58778525229247312917f;
+        case 7: case 8: return -0.95105651629515357212f;
+        default: return 0.0f;
+    }
+}
+
+// Size 10 as 5 x 2: Y[n2][k1] = DFT5 over n1 of x[2 n1 + n2], times
+// W10^(n2 k1), then X[k1 + 5 k2] = DFT2 over n2.
+template <>
+HD void dft_small<10>(cf v[10], int dir) {
+    cf y0[5], y1[5];
+HD_UNROLL
+    for (int n1 = 0; n1 < 5; ++n1) {
+        y0[n1] = v[2 * n1];
+        y1[n1] = v[2 * n1 + 1];
+    }
+    dft_small<5>(y0, dir);
+    dft_small<5>(y1, dir);
+HD_UNROLL
+    for (int k1 = 0; k1 < 5; ++k1) {
+        const cf t = k1 ? cmul(y1[k1], cf{cos10(k1), dir * sin10(k1)}) : y1[k1];
+        v[k1] = cadd(y0[k1], t);
+        v[k1 + 5] = csub(y0[k1], t);
+    }
+}
+
 // Size 8 as 2 x 4: inputs x[2 n1 + n2], X[k1 + 4 k2].
 template <>
 HD void dft_small<8>(cf v[8], int dir) {
@@ -244,15 +307,17 @@ HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int lgNs, int j
     stockham_store<R>(out, Ns, lgNs, j, dir, v);
 }
 
-// Radix plan of n = 2^a 3^b (b <= 1): radix 16 while possible, then the
-// rest r = n / 16^k in one stage when r is 2, 3, 4, 6, 8 or 12, else (r = 24)
-// radix 8 followed by radix 3; a factor 3 is always in the last stage, so
-// every stage sees a power-of-two Ns. Returns the number of stages, or -1 if
-// n has another prime factor or more than one factor 3.
+// Radix plan of n = 2^a, 3 * 2^a or 5 * 2^a: radix 16 while possible, then
+// the rest r = n / 16^k in one stage when r is 2, 3, 4, 5, 6, 8, 10 or 12,
+// else radix 8 then 3 (r = 24), radix 4 then 5 (r = 20) or radix 8 then 5
+// (r = 40); the factor 3 or 5 is always in the last stage, so every stage
+// sees a power-of-two Ns. Returns the number of stages, or -1 for any other
+// n.
 HD int fft_radices(int n, int rad[32]) {
     int m = n;
     if (m % 3 == 0) m /= 3;
-    if (m < 1 || (m & (m - 1)) != 0) return -1;   // another prime or a second factor 3
+    else if (m % 5 == 0) m /= 5;
+    if (m < 1 || (m & (m - 1)) != 0) return -1;
     int k = 0;
     while (n % 16 == 0) {
         rad[k++] = 16;
@@ -261,8 +326,14 @@ HD int fft_radices(int n, int rad[32]) {
     if (n == 24) {
         rad[k++] = 8;
         rad[k++] = 3;
+    } else if (n == 20) {
+        rad[k++] = 4;
+        rad[k++] = 5;
+    } else if (n == 40) {
+        rad[k++] = 8;
+        rad[k++] = 5;
     } else if (n != 1) {
-        rad[k++] = n;   // 2, 3, 4, 6, 8 or 12
+        rad[k++] = n;   // 2, 3, 4, 5, 6, 8, 10 or 12
     }
     return k;
 }

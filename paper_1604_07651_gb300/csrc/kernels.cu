@@ -73,12 +73,12 @@ __device__ __forceinline__ void fft_stage(cf* buf, int n, int nrows, int Ns, int
 
 // Block-cooperative in-place FFT of `nrows` sequences of length n
 // (unnormalised; DIR = -1 forward, +1 inverse). The radix plan is radix 16
-// stages and one last stage of radix 2, 3, 4, 6, 8 or 12 (or 8 then 3)
-// (fft_radices); written as straight-line code so that each stage keeps its
-// own small register footprint. Q, the butterflies a thread holds at once,
-// is chosen so that a stage covers every row in one round where the
-// registers allow. Supported: n = 2^a <= 4096 and n = 3 * 2^a <= 6144 with
-// 512 threads.
+// stages and a rest of radix 2, 3, 4, 5, 6, 8, 10 or 12 (or 8 then 3, 4
+// then 5, 8 then 5) (fft_radices); written as straight-line code so that
+// each stage keeps its own small register footprint. Q, the butterflies a
+// thread holds at once, is chosen so that a stage covers every row in one
+// round where the registers allow. Supported with 512 threads: n = 2^a <=
+// 4096, 3 * 2^a <= 6144, 5 * 2^a <= 5120.
 template <int R, int QMAX, int DIR>
 __device__ __forceinline__ void fft_stage_q(cf* buf, int n, int nrows, int Ns, int lgNs, const cf* __restrict__ tw) {
     const int need = (n / R) * nrows;
@@ -101,8 +101,10 @@ __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* _
     if (s < fp.nst) {
         const int R = fp.rad[s];
         if (R == 12) fft_stage_q<12, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+        else if (R == 10) fft_stage_q<10, 1, DIR>(buf, n, nrows, Ns, lg, tw);
         else if (R == 8) fft_stage_q<8, 1, DIR>(buf, n, nrows, Ns, lg, tw);
         else if (R == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        else if (R == 5) fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, tw);
         else if (R == 4) fft_stage_q<4, 2, DIR>(buf, n, nrows, Ns, lg, tw);
         else if (R == 3) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);
         else fft_stage_q<2, 2, DIR>(buf, n, nrows, Ns, lg, tw);
@@ -110,7 +112,10 @@ __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* _
         lg = 31 - __clz(Ns);
         ++s;
     }
-    if (s < fp.nst) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);   // after radix 8 (n / 16^k = 24)
+    if (s < fp.nst) {   // radix 3 after 8 (n / 16^k = 24), radix 5 after 4 or 8 (20, 40)
+        if (fp.rad[s] == 3) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);
+        else fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+    }
 }
 
 // --------------------------------------------------------------------------

@@ -36,7 +36,7 @@ const double kBetaMin = 1e-3;    // smallest angular opening of a sub-problem
 int fft_size(int n) {
     long best = -1;
     for (long p = 1; p < 2L * n + 2; p *= 2) {
-        for (long c : {p, 3 * p})
+        for (long c : {p, 3 * p, 5 * p})
             if (c >= n && (best < 0 || c < best)) best = c;
     }
     return (int)best;
@@ -587,14 +587,15 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.Prho = h.Prho;
     P.k1max = h.k1max;
     P.k2max = h.k2max;
-    // FFT lengths the in-place block FFT handles (512 threads): 2^a <= 4096, 3 * 2^a <= 6144
-    auto fft_ok = [](int n) { return (n % 3 == 0) ? n <= 6144 : n <= 4096; };
+    // FFT lengths the in-place block FFT handles (512 threads): 2^a <= 4096,
+    // 3 * 2^a <= 6144, 5 * 2^a <= 5120
+    auto fft_ok = [](int n) { return (n % 3 == 0) ? n <= 6144 : (n % 5 == 0) ? n <= 5120 : n <= 4096; };
     if (!fft_ok(h.Prho / 2) || !fft_ok(h.Ptheta))
         return fail(RADON_ERR_UNSUPPORTED,
                     "FFT length " + std::to_string(std::max(h.Prho / 2, h.Ptheta)) +
-                        " above the block FFT's limit (4096, or 6144 = 3*2048)");
-    // rows per band: 3 (more rows mean fewer, longer CTAs and worse balance;
-    // fewer mean more duplicated samples; 3 measured best on 2048^2 gathers)
+                        " above the block FFT's limit (4096, 6144 = 3*2048 or 5120 = 5*1024)");
+    // rows per band: 3 (more rows mean fewer, longer CTAs and worse balance,
+    // fewer leave threads of the radix-16 stages idle)
     int R = (int)std::min<size_t>(3, (size_t)smem_max / (h.Prho * sizeof(float)));   // <= kMaxBandRows
     if (const char* env = std::getenv("HRADON_ROWS_PER_BAND")) {   // tuning knob
         const int r = std::atoi(env);
