@@ -166,8 +166,14 @@ __device__ __forceinline__ void zero_rows(const PieceDev& P) {
 }
 
 
-// Shared tile row pitch: one word of padding puts the rows on different banks.
-constexpr int kTilePitch = kTileCols + 1;
+// Shared gridding tile: the kTileRows x kTileCols cells plus a halo of 3
+// cells on every side, so that every tap of a sample whose footprint meets
+// the tile lands in it without a bounds check (the halo is dropped at the
+// end: the neighbouring tiles' units add those cells). The odd pitch puts
+// the rows on different banks.
+constexpr int kHalo = 3;
+constexpr int kTilePitch = kTileCols + 2 * kHalo + 1;
+constexpr int kTileRowsH = kTileRows + 2 * kHalo;
 
 // Fixed-point accumulation in shared memory. Integer adds to shared memory
 // are single fire-and-forget instructions, float adds are compare-and-swap
@@ -231,29 +237,23 @@ __device__ __forceinline__ float block_max_abs(float v, float* red) {
 // would spread it over the whole piece in any case).
 __device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, int* tile, const float acc[16]) {
     if (mn < 0) return;
-    const int m0 = (mn >> 16) - m_lo, n0 = (mn & 0xffff) - n_lo;
+    int* t = tile + ((mn >> 16) - m_lo + kHalo) * kTilePitch + (mn & 0xffff) - n_lo + kHalo;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int m = m0 + a;
-        if (m < 0 || m >= kTileRows) continue;
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int n = n0 + c;
-            if (n >= 0 && n < kTileCols) red_fixed(tile + m * kTilePitch + n, acc[4 * a + c]);
-        }
-    }
+        for (int c = 0; c < 4; ++c) red_fixed(t + a * kTilePitch + c, acc[4 * a + c]);
 }
 
-__global__ void __launch_bounds__(kUnitChunks) k_grid_tiles(const __grid_constant__ PieceBatch B,
-                                                            const float* __restrict__ f) {
-    __shared__ int tile[kTileRows * kTilePitch];
+__global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_constant__ PieceBatch B,
+                                                               const float* __restrict__ f) {
+    __shared__ int tile[kTileRowsH * kTilePitch];
     __shared__ float red[kUnitChunks / 32];
     int bx;
     const PieceDev& P = B.p[batch_piece(B, bx)];
     const int4 u = __ldg(P.units + bx);           // (tile, first chunk, end chunk, 28 - ec)
     const int ti = u.x / P.ntc, tj = u.x - ti * P.ntc;
     const int m_lo = ti * kTileRows, n_lo = tj * kTileCols;
-    for (int i = threadIdx.x; i < kTileRows * kTilePitch; i += blockDim.x) tile[i] = 0;
+    for (int i = threadIdx.x; i < kTileRowsH * kTilePitch; i += blockDim.x) tile[i] = 0;
     // one chunk per thread: issue every load of the chunk before the first is used
     const int c = u.y + threadIdx.x;
     int4 ent[8];
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kUnitChunks) k_grid_tiles(const __grid_constan
     __syncthreads();
     for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
         const int m = i / kTileCols, n = i - m * kTileCols;
-        const int t = tile[m * kTilePitch + n];
+        const int t = tile[(m + kHalo) * kTilePitch + n + kHalo];
         if (t != 0 && m < nr && n < nc) atomicAdd(P.lat + (size_t)(m_lo + m) * P.Nrho + n_lo + n, sc.down(t));
     }
 }
