@@ -197,6 +197,44 @@ radon_status radon_plan_profile_read(radon_plan p, double ms[RADON_NSTAGES],
                                      double bytes[RADON_NSTAGES]);
 
 /*
+ * Sparse Radon inversion by iterative soft thresholding (Section 3, the
+ * iterations (iters) and, with a trace mask, (itersmd)): runs `iters`
+ * iterations of
+ *   g <- S_{c2 mu}( y + c2 R_h (f - chi_S R_h* y) ),  S_m(v) = sign(v) max(|v| - m/2, 0),
+ * the proximal-gradient method of min_g ||chi_S R_h* g - f||^2 + mu ||g||_1,
+ * with y = g (accelerate = 0, the paper's iteration) or the FISTA
+ * extrapolation y = g_n + ((t_{n-1} - 1)/t_n)(g_n - g_{n-1}),
+ * t_n = (1 + sqrt(1 + 4 t_{n-1}^2))/2, t_0 = 1 (accelerate = 1).
+ *   f     [Nx][Nt] device FP32 data, zero on missing traces (read only);
+ *   mask  [Nx] device FP32 trace weights chi_S (1 recorded, 0 missing), or
+ *         NULL for every trace;
+ *   g     [Nq][Ntau] device FP32: the starting iterate in, the result out;
+ *   c2    step c^2 > 0 with c^2 ||R_h||^2 < 1 for convergence (radon_opnorm);
+ *   mu    sparsity weight >= 0;
+ *   work  device scratch, 256-byte aligned, of radon_ista_work_bytes bytes,
+ *         owned by the caller and not used by anything else during the call.
+ * Asynchronous on `stream`; no host synchronisation. Errors: INVALID_ARG for
+ * NULL pointers, iters < 0, c2 <= 0, mu < 0, non-finite c2 or mu, or a short
+ * or misaligned work area; CUDA for launch failures.
+ */
+radon_status radon_ista_work_bytes(radon_plan p, size_t* bytes);
+radon_status radon_ista(radon_plan p, const float* f, const float* mask, float* g, int iters,
+                        float c2, float mu, int accelerate, void* work, size_t work_bytes,
+                        void* stream);
+
+/*
+ * Power iteration for the step bound of radon_ista: starting from v0
+ * ([Nq][Ntau] device FP32, any vector not orthogonal to the top singular
+ * vector), `iters` >= 1 steps of v <- R_h R_h* v / ||R_h R_h* v||; writes
+ * ||R_h R_h* v|| of the last step, which increases to ||R_h||^2, to *norm2
+ * (one device float). Scratch `work` of radon_opnorm_work_bytes bytes,
+ * 256-byte aligned. Asynchronous on `stream`. Same errors as radon_ista.
+ */
+radon_status radon_opnorm_work_bytes(radon_plan p, size_t* bytes);
+radon_status radon_opnorm(radon_plan p, const float* v0, int iters, float* norm2, void* work,
+                          size_t work_bytes, void* stream);
+
+/*
  * Forward transform that allocates nothing, for callers that cannot call
  * cudaMalloc when they run (a host framework that has reserved the whole
  * device for its own pool, deployments with a fixed device footprint, loops

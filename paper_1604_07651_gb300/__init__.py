@@ -9,6 +9,7 @@ or without the built library every call raises.
     g = plan.forward(f)        # f: cuda float32 [Nx][Nt]  ->  g: [Nq][Ntau]
     f2 = plan.adjoint(g)       # exact transpose (Eq. (16))
     g = radon(f, plan)         # autograd op: backward is the adjoint
+    g = plan.ista(f, mu, mask=m)   # sparse inversion / trace interpolation (FISTA)
 """
 from __future__ import annotations
 
@@ -149,6 +150,54 @@ class Plan:
         _check_tensor(out, (self.Nx, self.Nt), "out", self.device)
         _lib.check(_lib.load().radon_adj(self._handle, ctypes.c_void_p(g.data_ptr()),
                                          ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device)))
+        return out
+
+
+    # -- sparse inversion (Section 3) ----------------------------------------
+    def _work(self, fn_name: str) -> torch.Tensor:
+        v = ctypes.c_size_t()
+        _lib.check(getattr(_lib.load(), fn_name)(self._handle, ctypes.byref(v)))
+        # torch's caching allocator returns blocks aligned to at least 512 bytes
+        return torch.empty(max(1, v.value), dtype=torch.uint8, device=self.device)
+
+    def opnorm(self, iters: int = 30, v0: torch.Tensor | None = None, seed: int = 0) -> float:
+        """Estimate of ||R_h||^2 by the power iteration on R_h R_h*
+        (``radon_opnorm``). ``v0`` defaults to a seeded Gaussian image."""
+        if v0 is None:
+            gen = torch.Generator(device="cpu").manual_seed(seed)
+            v0 = torch.randn((self.Nq, self.Ntau), generator=gen).to(self.device)
+        _check_tensor(v0, (self.Nq, self.Ntau), "v0", self.device)
+        work = self._work("radon_opnorm_work_bytes")
+        out = torch.zeros(1, dtype=torch.float32, device=self.device)
+        _lib.check(_lib.load().radon_opnorm(self._handle, ctypes.c_void_p(v0.data_ptr()), int(iters),
+                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                            work.numel(), _stream_ptr(self.device)))
+        return float(out.item())
+
+    def ista(self, f: torch.Tensor, mu: float, iters: int = 50, *, mask: torch.Tensor | None = None,
+             g0: torch.Tensor | None = None, step: float | None = None, accelerate: bool = True,
+             out: torch.Tensor | None = None) -> torch.Tensor:
+        """Sparse Radon image of ``f`` by soft thresholding (``radon_ista``):
+        ``iters`` iterations of the paper's ISTA (``accelerate=False``) or of
+        FISTA. ``mask`` [Nx] marks recorded traces (missing-data form);
+        ``step`` is c^2 (default 0.95 / ||R_h||^2 from ``opnorm``)."""
+        _check_tensor(f, (self.Nx, self.Nt), "f", self.device)
+        if mask is not None:
+            _check_tensor(mask, (self.Nx,), "mask", self.device)
+        if step is None:
+            step = 0.95 / self.opnorm()
+        if out is None:
+            out = torch.zeros((self.Nq, self.Ntau), dtype=torch.float32, device=self.device)
+        _check_tensor(out, (self.Nq, self.Ntau), "out", self.device)
+        if g0 is not None:
+            _check_tensor(g0, (self.Nq, self.Ntau), "g0", self.device)
+            out.copy_(g0)
+        work = self._work("radon_ista_work_bytes")
+        _lib.check(_lib.load().radon_ista(
+            self._handle, ctypes.c_void_p(f.data_ptr()),
+            ctypes.c_void_p(mask.data_ptr() if mask is not None else None), ctypes.c_void_p(out.data_ptr()),
+            int(iters), float(step), float(mu), int(bool(accelerate)), ctypes.c_void_p(work.data_ptr()),
+            work.numel(), _stream_ptr(self.device)))
         return out
 
 

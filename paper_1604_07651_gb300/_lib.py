@@ -47,6 +47,11 @@ SIGNATURES = {
     "radon_geometry": (_c_int, [ctypes.POINTER(RadonDesc), ctypes.POINTER(_c_int),
                                 ctypes.POINTER(RadonPieceInfo), _c_int]),
     "radon_plan_device_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "radon_ista_work_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "radon_ista": (_c_int, [_vp, _vp, _vp, _vp, _c_int, ctypes.c_float, ctypes.c_float, _c_int, _vp,
+                            ctypes.c_size_t, _vp]),
+    "radon_opnorm_work_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "radon_opnorm": (_c_int, [_vp, _vp, _c_int, _vp, _vp, ctypes.c_size_t, _vp]),
     "radon_direct_fwd": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_double,
                                   _c_double, _c_double, _c_double, _c_double, _c_double, _vp]),
     "radon_direct_adj": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_double,

@@ -1,10 +1,10 @@
 """Builds the in-tree shared library ``libhradon.so`` for sm_103a.
 
-Three translation units, compiled in parallel: ``csrc/kernels.cu`` and
-``csrc/noalloc.cu`` with nvcc (``-gencode arch=compute_103a,code=sm_103a``)
-and ``csrc/plan.cpp`` with the
-host compiler (``-ffp-contract=off`` keeps the FP64 geometry identical on
-x86-64 and aarch64 hosts). No torch, no cmake.
+Every ``csrc/*.cu`` (kernels, the no-alloc entry point, the sparse-inversion
+solver) with nvcc (``-gencode arch=compute_103a,code=sm_103a``) and
+``csrc/plan.cpp`` with the host compiler (``-ffp-contract=off`` keeps the FP64
+geometry identical on x86-64 and aarch64 hosts), compiled in parallel. No
+torch, no cmake.
 """
 from __future__ import annotations
 
@@ -51,17 +51,19 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
     inc = ["-I", CSRC, "-I", INCLUDE, "-I", os.path.join(cuda, "include")]
-    ko = os.path.join(bdir, "kernels.o")
-    no = os.path.join(bdir, "noalloc.o")
+    cmds, objs = [], []
+    for name in sorted(n for n in os.listdir(CSRC) if n.endswith(".cu")):
+        obj = os.path.join(bdir, name[:-3] + ".o")
+        cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+               "-Xcompiler", "-ffp-contract=off", *inc, "-c", os.path.join(CSRC, name), "-o", obj]
+        if ptxas_info:
+            cmd.insert(1, "-Xptxas=-v")
+        cmds.append(cmd)
+        objs.append(obj)
     po = os.path.join(bdir, "plan.o")
-    kcmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-            "-Xcompiler", "-ffp-contract=off", *inc, "-c", os.path.join(CSRC, "kernels.cu"), "-o", ko]
-    if ptxas_info:
-        kcmd.insert(1, "-Xptxas=-v")
-    ncmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *inc, "-c",
-            os.path.join(CSRC, "noalloc.cu"), "-o", no]
-    pcmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", *inc, "-c",
-            os.path.join(CSRC, "plan.cpp"), "-o", po]
+    cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", *inc, "-c",
+                 os.path.join(CSRC, "plan.cpp"), "-o", po])
+    objs.append(po)
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -70,10 +72,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         if verbose or ptxas_info:
             sys.stderr.write(r.stdout + r.stderr)
 
-    with ThreadPoolExecutor(3) as ex:
-        list(ex.map(run, [kcmd, ncmd, pcmd]))
+    with ThreadPoolExecutor(len(cmds)) as ex:
+        list(ex.map(run, cmds))
     tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc, *ARCH, "-shared", ko, no, po, "-o", tmp, "-L", os.path.join(cuda, "lib64"), "-lcudart"])
+    run([nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-L", os.path.join(cuda, "lib64"), "-lcudart"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -309,7 +309,7 @@ HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int lgNs, int j
 
 // Radix plan of n = 2^a, 3 * 2^a or 5 * 2^a: radix 16 while possible, then
 // the rest r = n / 16^k in one stage when r is 2, 3, 4, 5, 6, 8, 10 or 12,
-// else radix 8 then 3 (r = 24), radix 4 then 5 (r = 20) or radix 8 then 5
+// else radix 4 then 6 (r = 24), radix 4 then 5 (r = 20) or radix 8 then 5
 // (r = 40); the factor 3 or 5 is always in the last stage, so every stage
 // sees a power-of-two Ns. Returns the number of stages, or -1 for any other
 // n.
@@ -324,8 +324,8 @@ HD int fft_radices(int n, int rad[32]) {
         n /= 16;
     }
     if (n == 24) {
-        rad[k++] = 8;
-        rad[k++] = 3;
+        rad[k++] = 4;
+        rad[k++] = 6;
     } else if (n == 20) {
         rad[k++] = 4;
         rad[k++] = 5;
@@ -336,6 +336,28 @@ HD int fft_radices(int n, int rad[32]) {
         rad[k++] = n;   // 2, 3, 4, 5, 6, 8, 10 or 12
     }
     return k;
+}
+
+// Butterflies of one radix a thread of the block FFT holds at once (the
+// register budget of 64 per thread): one sequence of length n fits one stage
+// round when n / R <= threads * fft_qmax(R).
+HD int fft_qmax(int R) {
+    switch (R) {
+        case 16: case 12: case 10: case 8: return 1;
+        case 6: case 5: case 2: return 2;
+        case 4: return 3;
+        default: return 4;   // 3
+    }
+}
+
+// Whether the block FFT of `threads` threads handles length n.
+HD bool fft_fits(int n, int threads) {
+    int rad[32];
+    const int nst = fft_radices(n, rad);
+    if (nst < 0) return false;
+    for (int s = 0; s < nst; ++s)
+        if (n / rad[s] > threads * fft_qmax(rad[s])) return false;
+    return true;
 }
 
 // Real FFT of length P = 2M through a complex FFT of length M of the packed

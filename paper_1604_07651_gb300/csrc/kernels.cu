@@ -73,18 +73,26 @@ __device__ __forceinline__ void fft_stage(cf* buf, int n, int nrows, int Ns, int
 
 // Block-cooperative in-place FFT of `nrows` sequences of length n
 // (unnormalised; DIR = -1 forward, +1 inverse). The radix plan is radix 16
-// stages and a rest of radix 2, 3, 4, 5, 6, 8, 10 or 12 (or 8 then 3, 4
+// stages and a rest of radix 2, 3, 4, 5, 6, 8, 10 or 12 (or 4 then 6, 4
 // then 5, 8 then 5) (fft_radices); written as straight-line code so that
 // each stage keeps its own small register footprint. Q, the butterflies a
 // thread holds at once, is chosen so that a stage covers every row in one
-// round where the registers allow. Supported with 512 threads: n = 2^a <=
-// 4096, 3 * 2^a <= 6144, 5 * 2^a <= 5120.
+// round where the registers allow. Supported: every n with fft_fits(n, 512)
+// (2^a <= 4096, 3 * 2^a <= 6144, 5 * 2^a <= 5120).
+// One stage with Q butterflies per thread: enough for all rows of the block
+// in one round where the register budget QMAX = fft_qmax(R) allows, and at
+// least enough for one whole sequence (fft_fits guarantees that fits).
 template <int R, int QMAX, int DIR>
 __device__ __forceinline__ void fft_stage_q(cf* buf, int n, int nrows, int Ns, int lgNs, const cf* __restrict__ tw) {
-    const int need = (n / R) * nrows;
+    const int nb = n / R;
     const int nthr = (int)blockDim.x;
-    if (QMAX >= 4 && need > 2 * nthr) fft_stage<R, 4, DIR>(buf, n, nrows, Ns, lgNs, tw);
-    else if (QMAX >= 2 && need > nthr) fft_stage<R, 2, DIR>(buf, n, nrows, Ns, lgNs, tw);
+    int q = (nb * nrows + nthr - 1) / nthr;
+    q = q > QMAX ? QMAX : q;
+    const int qmin = (nb + nthr - 1) / nthr;
+    q = q < qmin ? qmin : q;
+    if (QMAX >= 4 && q >= 4) fft_stage<R, (QMAX >= 4 ? 4 : 1), DIR>(buf, n, nrows, Ns, lgNs, tw);
+    else if (QMAX >= 3 && q == 3) fft_stage<R, (QMAX >= 3 ? 3 : 1), DIR>(buf, n, nrows, Ns, lgNs, tw);
+    else if (QMAX >= 2 && q == 2) fft_stage<R, (QMAX >= 2 ? 2 : 1), DIR>(buf, n, nrows, Ns, lgNs, tw);
     else fft_stage<R, 1, DIR>(buf, n, nrows, Ns, lgNs, tw);
 }
 
@@ -105,15 +113,15 @@ __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* _
         else if (R == 8) fft_stage_q<8, 1, DIR>(buf, n, nrows, Ns, lg, tw);
         else if (R == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, tw);
         else if (R == 5) fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, tw);
-        else if (R == 4) fft_stage_q<4, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        else if (R == 4) fft_stage_q<4, 3, DIR>(buf, n, nrows, Ns, lg, tw);
         else if (R == 3) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);
         else fft_stage_q<2, 2, DIR>(buf, n, nrows, Ns, lg, tw);
         Ns *= R;
         lg = 31 - __clz(Ns);
         ++s;
     }
-    if (s < fp.nst) {   // radix 3 after 8 (n / 16^k = 24), radix 5 after 4 or 8 (20, 40)
-        if (fp.rad[s] == 3) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);
+    if (s < fp.nst) {   // after radix 4 or 8 (n / 16^k = 24, 20, 40): radix 6 or 5
+        if (fp.rad[s] == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, tw);
         else fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, tw);
     }
 }

@@ -589,7 +589,9 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.k2max = h.k2max;
     // FFT lengths the in-place block FFT handles (512 threads): 2^a <= 4096,
     // 3 * 2^a <= 6144, 5 * 2^a <= 5120
-    auto fft_ok = [](int n) { return (n % 3 == 0) ? n <= 6144 : (n % 5 == 0) ? n <= 5120 : n <= 4096; };
+    auto fft_ok = [](int n) {
+        return ((n % 3 == 0) ? n <= 6144 : (n % 5 == 0) ? n <= 5120 : n <= 4096) && fft_fits(n, 512);
+    };
     if (!fft_ok(h.Prho / 2) || !fft_ok(h.Ptheta))
         return fail(RADON_ERR_UNSUPPORTED,
                     "FFT length " + std::to_string(std::max(h.Prho / 2, h.Ptheta)) +

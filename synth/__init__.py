@@ -163,11 +163,12 @@ def band_limited_gather(geo: Geometry, tag: int, n_events: int = 8,
 
 def large_gather(N: int = 4096, tag: int = 5, n_events: int = 64,
                  T: float = 2.0, X: float = 2.0) -> tuple[Geometry, np.ndarray]:
-    """Large square gather with primaries and their first multiples
-    (events at 2*tau0 with the same q0)."""
+    """Large square gather: n_events Ricker primaries (20-40 Hz) and their
+    first multiples (events at 2*tau0 with the same q0, half amplitude,
+    opposite sign)."""
     geo = Geometry(N, N, N, N, T / (N - 1), X / (N - 1), 0.2, 0.7)
     rng = rng_for(tag * 100003 + N)
-    npri = n_events // 2
+    npri = n_events
     tau0 = rng.uniform(0.1, 0.45 * T, npri)
     q0 = rng.uniform(0.25, 0.65, npri)
     nu = rng.uniform(20.0, 40.0, npri)

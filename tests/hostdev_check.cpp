@@ -173,5 +173,13 @@ int main() {
         }
     }
     std::printf("swizzle_violations %d\n", bad);
+    // every length within the limits fits the 512-thread block FFT
+    int nofit = 0;
+    for (int n = 2; n <= 6144; ++n) {
+        int rad[32];
+        if (fft_radices(n, rad) < 0 || (n % 3 == 0 ? n > 6144 : n % 5 == 0 ? n > 5120 : n > 4096)) continue;
+        if (!fft_fits(n, 512)) ++nofit;
+    }
+    std::printf("fft_sizes_not_fitting %d\n", nofit);
     return 0;
 }

@@ -134,6 +134,29 @@ def test_full_size_2048_sampled_against_direct_sum(hr, oracle_direct):
     assert _rel(fa[kk, jj], refa) < METHOD_TOL
 
 
+def test_large_4096_sampled_against_direct_sum(hr, oracle_direct):
+    """Large single gather (4096^2, 64 Ricker primaries plus their multiples,
+    default method parameters; FFT lengths up to 6144): forward on 4096
+    random outputs and adjoint on 4096 random gather points against the FP64
+    direct sum, O(N) per point."""
+    geo, f = synth.large_gather(4096)
+    plan, _ = _pair(hr, geo)
+    assert max(max(p["Ptheta"], p["Prho"]) for p in plan.pieces()) > 4096
+    rng = np.random.default_rng(4096)
+    ii = rng.integers(0, geo.Ntau, 4096)
+    li = rng.integers(0, geo.Nq, 4096)
+    g = plan.forward(_cuda(f)).cpu().numpy()
+    ref = odirect.fwd_points(f, geo.dt, geo.dx, geo.tau(), geo.q(), ii, li)
+    assert _rel(g[li, ii], ref) < METHOD_TOL
+    gg = synth.smooth_radon_image(geo, 78)
+    fa = plan.adjoint(_cuda(gg)).cpu().numpy()
+    jj = rng.integers(0, geo.Nt, 4096)
+    kk = rng.integers(0, geo.Nx, 4096)
+    refa = odirect.adj_points(gg, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q(), jj, kk)
+    assert _rel(fa[kk, jj], refa) < METHOD_TOL
+    plan.close()
+
+
 def test_full_size_2048_against_logpolar_oracle(hr):
     """Same workload, every output, against the FP64 log-polar oracle."""
     geo, f = synth.sweep_gather(2048, noise=0.05)

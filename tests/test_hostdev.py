@@ -37,3 +37,9 @@ def test_b3_weights(results):
 
 def test_shared_memory_swizzle_is_a_permutation(results):
     assert results["swizzle_violations"] == 0
+
+
+def test_every_supported_length_fits_the_block_fft(results):
+    """No stage of any supported FFT length needs more butterflies per thread
+    than its radix's register budget allows (512 threads)."""
+    assert results["fft_sizes_not_fitting"] == 0
