@@ -18,7 +18,7 @@ import numpy as np
 
 __all__ = [
     "Geometry", "ricker", "rng_for", "hyperbolic_gather", "gaussian_gather",
-    "random_radon_image", "single_gather", "sweep_gather", "large_gather",
+    "random_radon_image", "single_gather", "sweep_gather", "large_gather", "missing_trace_gather",
     "band_limited_gather", "batch_geometries",
 ]
 
@@ -176,6 +176,26 @@ def large_gather(N: int = 4096, tag: int = 5, n_events: int = 64,
     f = hyperbolic_gather(geo, tau0, q0, nu, amp)
     f += hyperbolic_gather(geo, 2 * tau0, q0, nu, -0.5 * amp)
     return geo, f
+
+
+def missing_trace_gather(tag: int = 3, Nt: int = 1024, Nx: int = 256, n_events: int = 20,
+                         missing: float = 0.4) -> tuple[Geometry, np.ndarray, np.ndarray]:
+    """Trace-interpolation workload: Nt samples at dt = 2 ms, Nx offsets on
+    [0, 2] km, Ntau = Nt, Nq = Nx on q in [0.2, 0.7] s/km; n_events Ricker
+    hyperbolas (tau0 ~ U[0.1, 1.8] s, q0 ~ U[0.25, 0.65], 15-30 Hz,
+    A ~ N(0, 1)). Returns the geometry, the complete gather and the trace
+    mask (1 recorded, 0 missing; a `missing` fraction of the traces, chosen
+    at random)."""
+    geo = Geometry(Nt, Nx, Nt, Nx, 0.002, 2.0 / (Nx - 1), 0.2, 0.7)
+    rng = rng_for(tag * 1000 + 7)
+    tau0 = rng.uniform(0.1, 1.8, n_events)
+    q0 = rng.uniform(0.25, 0.65, n_events)
+    nu = rng.uniform(15.0, 30.0, n_events)
+    amp = rng.standard_normal(n_events)
+    f = hyperbolic_gather(geo, tau0, q0, nu, amp)
+    mask = np.ones(Nx)
+    mask[rng.choice(Nx, int(round(missing * Nx)), replace=False)] = 0.0
+    return geo, f, mask
 
 
 def batch_geometries(n: int, tag: int = 4) -> list[Geometry]:
