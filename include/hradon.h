@@ -197,6 +197,31 @@ radon_status radon_plan_profile_read(radon_plan p, double ms[RADON_NSTAGES],
                                      double bytes[RADON_NSTAGES]);
 
 /*
+ * Batches of gathers of different sizes (many CMP gathers at once). The
+ * batch holds one plan per descriptor (all on the first descriptor's
+ * device) and runs every stage of the transform as ONE launch over all
+ * sub-problems of all gathers, with descriptors and block maps in device
+ * memory; the calls are therefore also cheap to capture in a CUDA graph.
+ * Data are packed back to back: gather i occupies elements
+ * [f_offsets[i], f_offsets[i+1]) of the packed gather buffer ([Nx][Nt],
+ * time fastest) and image i [g_offsets[i], g_offsets[i+1]) of the packed image
+ * buffer ([Nq][Ntau]); radon_batch_layout fills the n+1 offsets (elements).
+ * radon_batch_fwd reads FP32 (in_type RADON_IN_F32) or BF16 (RADON_IN_BF16,
+ * stored as raw bfloat16) gathers and computes in FP32; the image and the
+ * adjoint's output are FP32. Asynchronous on `stream`; the batch may be used
+ * on one stream at a time. Errors as for radon_plan_create_ex / radon_fwd.
+ */
+typedef struct radon_batch_s* radon_batch;
+#define RADON_IN_F32 0
+#define RADON_IN_BF16 1
+radon_status radon_batch_create(radon_batch* out, int n, const radon_desc* descs);
+radon_status radon_batch_destroy(radon_batch b);
+radon_status radon_batch_layout(radon_batch b, int* n, long long* f_offsets, long long* g_offsets);
+radon_status radon_batch_plan(radon_batch b, int i, radon_desc* d);
+radon_status radon_batch_fwd(radon_batch b, const void* f, int in_type, float* g, void* stream);
+radon_status radon_batch_adj(radon_batch b, const float* g, float* f, void* stream);
+
+/*
  * Sparse Radon inversion by iterative soft thresholding (Section 3, the
  * iterations (iters) and, with a trace mask, (itersmd)): runs `iters`
  * iterations of

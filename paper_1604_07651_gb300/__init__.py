@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import RadonError, RadonDesc, RadonPieceInfo
 
-__all__ = ["Plan", "radon", "radon_adjoint", "direct_forward", "direct_adjoint", "RadonError",
+__all__ = ["Plan", "Batch", "radon", "radon_adjoint", "direct_forward", "direct_adjoint", "RadonError",
            "HRadon"]
 
 
@@ -198,6 +198,107 @@ class Plan:
             ctypes.c_void_p(mask.data_ptr() if mask is not None else None), ctypes.c_void_p(out.data_ptr()),
             int(iters), float(step), float(mu), int(bool(accelerate)), ctypes.c_void_p(work.data_ptr()),
             work.numel(), _stream_ptr(self.device)))
+        return out
+
+
+def _desc(Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax, tau0=0.0, dtau=0.0, sigma=None, omega_c=None,
+          tsplit=None, n_qsplit=1, device=0) -> RadonDesc:
+    d = RadonDesc()
+    _lib.check(_lib.load().radon_desc_init(ctypes.byref(d), Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax))
+    d.tau0, d.dtau, d.n_qsplit, d.device = tau0, dtau, n_qsplit, device
+    if sigma is not None:
+        d.sigma = sigma
+    if omega_c is not None:
+        d.omega_c = omega_c
+    if tsplit is not None:
+        ts = list(tsplit)
+        if len(ts) > _lib.MAX_TSPLIT:
+            raise ValueError(f"at most {_lib.MAX_TSPLIT} time splits")
+        d.n_tsplit = len(ts)
+        for i, v in enumerate(ts):
+            d.tsplit[i] = v
+    return d
+
+
+class Batch:
+    """Many gathers of different sizes transformed together: every stage of
+    the transform is one launch over all of them (``radon_batch_*``).
+
+    ``geometries``: a list of dicts with the ``Plan`` arguments (``Nt``,
+    ``Nx``, ``Ntau``, ``Nq``, ``dt``, ``dx``, ``qmin``, ``qmax`` and
+    optionally ``tau0``, ``dtau``, ``sigma``, ``omega_c``, ``tsplit``,
+    ``n_qsplit``). Data are packed back to back (``f_offsets``,
+    ``g_offsets``): gather i is ``f[f_offsets[i]:f_offsets[i+1]]`` viewed as
+    [Nx][Nt]; ``forward`` accepts float32 or bfloat16 gathers."""
+
+    def __init__(self, geometries: Sequence[dict], device: int | None = None):
+        lib = _lib.load()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = torch.device("cuda", dev)
+        n = len(geometries)
+        arr = (RadonDesc * n)(*[_desc(device=dev, **g) for g in geometries])
+        self._handle = ctypes.c_void_p()
+        _lib.check(lib.radon_batch_create(ctypes.byref(self._handle), n, arr))
+        fo = (ctypes.c_longlong * (n + 1))()
+        go = (ctypes.c_longlong * (n + 1))()
+        _lib.check(lib.radon_batch_layout(self._handle, None, fo, go))
+        self.f_offsets = list(fo)
+        self.g_offsets = list(go)
+        self.shapes = [((g["Nx"], g["Nt"]), (g["Nq"], g["Ntau"])) for g in geometries]
+
+    def close(self):
+        if getattr(self, "_handle", None) is not None and self._handle.value:
+            _lib.load().radon_batch_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, gathers: Sequence[torch.Tensor], dtype=torch.float32) -> torch.Tensor:
+        """The packed gather buffer of the batch's layout."""
+        out = torch.empty(self.f_offsets[-1], dtype=dtype, device=self.device)
+        for i, t in enumerate(gathers):
+            out[self.f_offsets[i]:self.f_offsets[i + 1]].copy_(t.reshape(-1))
+        return out
+
+    def unpack_images(self, g: torch.Tensor) -> list[torch.Tensor]:
+        return [g[self.g_offsets[i]:self.g_offsets[i + 1]].view(*self.shapes[i][1])
+                for i in range(len(self.shapes))]
+
+    def unpack_gathers(self, f: torch.Tensor) -> list[torch.Tensor]:
+        return [f[self.f_offsets[i]:self.f_offsets[i + 1]].view(*self.shapes[i][0])
+                for i in range(len(self.shapes))]
+
+    def forward(self, f: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if f.device != self.device or not f.is_contiguous() or f.numel() != self.f_offsets[-1]:
+            raise ValueError("f must be the contiguous packed gather buffer on the batch's device")
+        if f.dtype == torch.float32:
+            kind = 0
+        elif f.dtype == torch.bfloat16:
+            kind = 1
+        else:
+            raise ValueError("f must be float32 or bfloat16")
+        if out is None:
+            out = torch.empty(self.g_offsets[-1], dtype=torch.float32, device=self.device)
+        if out.numel() != self.g_offsets[-1] or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("out must be the contiguous packed float32 image buffer")
+        _lib.check(_lib.load().radon_batch_fwd(self._handle, ctypes.c_void_p(f.data_ptr()), kind,
+                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device)))
+        return out
+
+    def adjoint(self, g: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if (g.device != self.device or not g.is_contiguous() or g.numel() != self.g_offsets[-1]
+                or g.dtype != torch.float32):
+            raise ValueError("g must be the contiguous packed float32 image buffer on the batch's device")
+        if out is None:
+            out = torch.empty(self.f_offsets[-1], dtype=torch.float32, device=self.device)
+        if out.numel() != self.f_offsets[-1] or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("out must be the contiguous packed float32 gather buffer")
+        _lib.check(_lib.load().radon_batch_adj(self._handle, ctypes.c_void_p(g.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device)))
         return out
 
 

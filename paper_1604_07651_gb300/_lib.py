@@ -47,6 +47,13 @@ SIGNATURES = {
     "radon_geometry": (_c_int, [ctypes.POINTER(RadonDesc), ctypes.POINTER(_c_int),
                                 ctypes.POINTER(RadonPieceInfo), _c_int]),
     "radon_plan_device_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "radon_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(RadonDesc)]),
+    "radon_batch_destroy": (_c_int, [_vp]),
+    "radon_batch_layout": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_longlong)]),
+    "radon_batch_plan": (_c_int, [_vp, _c_int, ctypes.POINTER(RadonDesc)]),
+    "radon_batch_fwd": (_c_int, [_vp, _vp, _c_int, _vp, _vp]),
+    "radon_batch_adj": (_c_int, [_vp, _vp, _vp, _vp]),
     "radon_ista_work_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "radon_ista": (_c_int, [_vp, _vp, _vp, _vp, _c_int, ctypes.c_float, ctypes.c_float, _c_int, _vp,
                             ctypes.c_size_t, _vp]),

@@ -71,6 +71,8 @@ struct PieceDev {
     cf* spec;               // [nkb][Ntheta][CB] half spectrum of the lattice rows (in-place column pass)
     float* prof;            // [ncol][hpitch] rho profiles of the output columns (adjoint)
     int hpitch;             // row pitch of prof, floats, multiple of 4
+    long long f_off;        // element offset of this gather in packed gather buffers (0: single plan)
+    long long g_off;        // element offset of this gather's image in packed image buffers
 };
 
 // Up to kMaxBatch sub-problems launched as one grid: the blocks of piece k
@@ -81,6 +83,17 @@ struct PieceBatch {
     int first[kMaxBatch + 1];
     PieceDev p[kMaxBatch];
 };
+
+// Any number of sub-problems (of many gathers) launched as one grid: the
+// descriptors live in device memory and map[b] = (piece, block within the
+// piece) for every block b of the launch.
+struct DevBatch {
+    const PieceDev* p;
+    const int2* map;
+};
+
+// Input element types of the gridding.
+enum { kInF32 = 0, kInBF16 = 1 };
 
 // Lattice tile of the forward gridding (rows x columns of cells) and the
 // largest work unit (chunks of <= 8 samples; one thread per chunk).
@@ -98,10 +111,25 @@ int launch_col_profiles(const PieceDev* P, int n, const float* g, void* stream);
 int launch_band_rows(const PieceDev* P, int n, void* stream);
 int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream);
 int launch_rows_c2r(const PieceDev* P, int n, void* stream);
-int launch_interp_columns(const PieceDev* pieces, int npieces, const PieceDev* dev_pieces,
-                          int l_lo, int l_hi, float* g, void* stream);
-int launch_gather_samples(const PieceDev* dev_pieces, int npieces, int Nt, int Nx,
-                          float* f, void* stream);
+// The same stages over a device-resident batch: `nblocks` blocks, map in S,
+// `smem` the largest dynamic shared memory any piece of the launch needs.
+int launch_grid_tiles_dev(const DevBatch& S, int nblocks, const void* f, int in_type, void* stream);
+int launch_rows_r2c_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
+int launch_col_profiles_dev(const DevBatch& S, int nblocks, size_t smem, const float* g, void* stream);
+int launch_band_rows_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
+int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream);
+int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
+// Output interpolation: one CTA per output column; cmap[b] = (first piece,
+// number of time pieces, column l, 0) in `pieces` (device). Shared memory
+// (nrho_max + ntau_max) floats.
+int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int ntau_max,
+                          float* g, void* stream);
+// Adjoint gather: one CTA per kSampleBlock samples of one gather;
+// smap[b] = (first piece, number of pieces, first sample, 0).
+constexpr int kSampleBlock = 256;
+int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, void* stream);
+size_t rows_smem_bytes(const PieceDev& P);
+size_t profile_smem_bytes(const PieceDev& P);
 int launch_sample_table(const TableArgs& A, const double* cj, const double* wk, const int* jfirst,
                         SampleEnt* out);
 int launch_radon_table(const TableArgs& A, const double* qb2, RadonEnt* out);
@@ -111,7 +139,7 @@ int launch_direct_fwd(const float* f, float* g, int Nt, int Nx, int Ntau, int Nq
                       double dx, double tau0, double dtau, double qmin, double dq, void* stream);
 int launch_direct_adj(const float* g, float* f, int Nt, int Nx, int Ntau, int Nq, double dt,
                       double dx, double tau0, double dtau, double qmin, double dq, void* stream);
-size_t scatter_smem_bytes(const PieceDev& P);
+size_t scatter_smem_bytes(const PieceDev& P);   // = rows_smem_bytes
 
 // Forward transform of a plan with every work buffer carved out of the
 // caller-given device area `work` (256-byte aligned, `bytes` long) instead of

@@ -20,6 +20,7 @@
 // part, so the transforms themselves are FP32 loads, B-spline weights and
 // sums. Shared-memory accumulation uses FP32 atomics, so the last bits of the
 // gridding depend on the order in which warps arrive.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -134,7 +135,9 @@ __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* _
 
 extern __shared__ __align__(16) float smem_f[];
 
-// Piece of this block in a batched launch, and the block's index within it.
+// Piece of this block in a batched launch, and the block's index within it:
+// from the descriptors passed as a kernel parameter (up to kMaxBatch pieces)
+// or from a device-resident batch (any number of pieces of many gathers).
 __device__ __forceinline__ int batch_piece(const PieceBatch& B, int& bx) {
     int pi = 0;
 #pragma unroll
@@ -143,6 +146,15 @@ __device__ __forceinline__ int batch_piece(const PieceBatch& B, int& bx) {
     bx = (int)blockIdx.x - B.first[pi];
     return pi;
 }
+__device__ __forceinline__ const PieceDev& piece_of(const PieceBatch& B, int& bx) { return B.p[batch_piece(B, bx)]; }
+__device__ __forceinline__ const PieceDev& piece_of(const DevBatch& B, int& bx) {
+    const int2 m = __ldg(B.map + blockIdx.x);
+    bx = m.y;
+    return B.p[m.x];
+}
+
+__device__ __forceinline__ float load_in(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float load_in(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 
 // Real sample n of a row buffer (stored as complex pairs in the sw layout).
 __device__ __forceinline__ int swr(int n) { return 2 * sw(n >> 1) + (n & 1); }
@@ -252,12 +264,13 @@ __device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, int* tile
         for (int c = 0; c < 4; ++c) red_fixed(t + a * kTilePitch + c, acc[4 * a + c]);
 }
 
-__global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_constant__ PieceBatch B,
-                                                               const float* __restrict__ f) {
+template <class Src, class T>
+__global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_constant__ Src B,
+                                                               const T* __restrict__ f) {
     __shared__ int tile[kTileRowsH * kTilePitch];
     __shared__ float red[kUnitChunks / 32];
     int bx;
-    const PieceDev& P = B.p[batch_piece(B, bx)];
+    const PieceDev& P = piece_of(B, bx);
     const int4 u = __ldg(P.units + bx);           // (tile, first chunk, end chunk, 28 - ec)
     const int ti = u.x / P.ntc, tj = u.x - ti * P.ntc;
     const int m_lo = ti * kTileRows, n_lo = tj * kTileCols;
@@ -271,12 +284,12 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
         int4 ch = make_int4(0, 0, 0, 0);                // (trace, first sample, count)
         if (c < u.z) ch = __ldg(P.chunks + c);
         const int4* st = reinterpret_cast<const int4*>(P.stab + (size_t)ch.x * P.nj - P.jt_lo) + ch.y;
-        const float* fk = f + (size_t)ch.x * P.Nt + ch.y;
+        const T* fk = f + P.f_off + (size_t)ch.x * P.Nt + ch.y;
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
             if (s < ch.z) {
                 ent[s] = __ldg(st + s);
-                v[s] = __ldg(fk + s);
+                v[s] = load_in(fk + s);
             } else {
                 ent[s] = make_int4(0, 0, 0, 0);
                 v[s] = 0.f;
@@ -338,9 +351,10 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
 
 // Real FFT of a band of lattice rows (P.lat, zero-padded to Prho) into the
 // half spectrum (first half of Eq. (7)/(16)).
-__global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ PieceBatch B) {
+template <class Src>
+__global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src B) {
     int bx;
-    const PieceDev& P = B.p[batch_piece(B, bx)];
+    const PieceDev& P = piece_of(B, bx);
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int Pr = P.Prho, Nr = P.Nrho;
@@ -407,13 +421,14 @@ __device__ __forceinline__ void profile_group(int2 e, float v, int* prof, int la
 // the column's outputs g[l_lo + lc][*], scaled by the column's output scale.
 // Fixed point with the bound max|g| of the column times the column's
 // plan-time weight bound; a non-finite g makes the profile NaN.
-__global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ PieceBatch B, const float* __restrict__ g) {
+template <class Src>
+__global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Src B, const float* __restrict__ g) {
     int* prof = reinterpret_cast<int*>(smem_f);
     __shared__ float red[8];
     int lc;
-    const PieceDev& P = B.p[batch_piece(B, lc)];
+    const PieceDev& P = piece_of(B, lc);
     const int hp = P.hpitch;
-    const float* gl = g + (size_t)(P.l_lo + lc) * P.Ntau;
+    const float* gl = g + P.g_off + (size_t)(P.l_lo + lc) * P.Ntau;
     const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * P.Ntau);
     float* hl = P.prof + (size_t)lc * hp;
     for (int n = threadIdx.x; n < P.Nrho; n += blockDim.x) prof[n] = 0;
@@ -466,9 +481,10 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Pi
 // the band's candidate columns (theta taps of each column from the plan),
 // then the row FFT into the half spectrum. Each thread owns four rho cells
 // of every row of the band and sums the columns in order in registers.
-__global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ PieceBatch B) {
+template <class Src>
+__global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Src B) {
     int band;
-    const PieceDev& P = B.p[batch_piece(B, band)];
+    const PieceDev& P = piece_of(B, band);
     const float* __restrict__ h = P.prof;
     const int hp = P.hpitch;
     const int mb = band * P.R;
@@ -519,9 +535,10 @@ __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Pi
 // One block of CB spectrum columns per CTA; the blocked layout
 // [kb][m][CB] makes every load and store contiguous.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ PieceBatch B, int adjoint) {
+template <class Src>
+__global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src B, int adjoint) {
     int kb;
-    const PieceDev& P = B.p[batch_piece(B, kb)];
+    const PieceDev& P = piece_of(B, kb);
     const cf* in = P.spec;   // in place: the CTA owns its column block
     cf* out = P.spec;
     const int CB = P.CB, Pt = P.Ptheta, Nth = P.Ntheta;
@@ -578,9 +595,10 @@ __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Piec
 // Inverse real FFT of a band of rows from the half spectrum (bins <= k2max,
 // the rest zero) into the real lattice P.lat[Ntheta][Nrho].
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ PieceBatch B) {
+template <class Src>
+__global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ Src B) {
     int bx;
-    const PieceDev& P = B.p[batch_piece(B, bx)];
+    const PieceDev& P = piece_of(B, bx);
     const cf* __restrict__ spec = P.spec;
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
@@ -639,22 +657,24 @@ __device__ __forceinline__ float taps16(const float* __restrict__ lat, int Nr, i
     return s;
 }
 
-// Forward output interpolation (Eq. (17)) for the columns [l_lo, l_lo + ncol)
-// of one slowness piece, summed over its time pieces (pieces[0..np)). As in
-// the adjoint, the column's outputs share its theta taps, so the 4x4 taps
-// separate: one CTA per column first spreads the four lattice rows of the
-// column's angle into a rho profile in shared memory,
+// Forward output interpolation (Eq. (17)): one CTA per output column, summed
+// over the time pieces of its slowness piece; cmap[b] = (first piece, number
+// of pieces, column l). As in the adjoint, the column's outputs share its
+// theta taps, so the 4x4 taps separate: the CTA first spreads the four
+// lattice rows of the column's angle into a rho profile in shared memory,
 //   r[n] = sum_a B3(theta_l - theta_{m0+a}) H[m0 + a][n],
 // then every output takes 4 taps of it; the pieces are summed per output in
-// a fixed order (shared memory: [nrho_max] profile, [Ntau] sums).
-__global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restrict__ pieces, int np,
-                                                        int l_lo, int Ntau, int nrho_max,
+// a fixed order (shared memory: [nrho_max] profile, [ntau_max] sums).
+__global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restrict__ pieces,
+                                                        const int4* __restrict__ cmap, int nrho_max,
                                                         float* __restrict__ g) {
-    const int l = l_lo + blockIdx.x;
+    const int4 c = __ldg(cmap + blockIdx.x);
+    const int l = c.z, np = c.y;
+    const int Ntau = pieces[c.x].Ntau;
     float* prof = smem_f;
     float* acc = smem_f + nrho_max;
     for (int i = threadIdx.x; i < Ntau; i += blockDim.x) acc[i] = 0.f;
-    for (int p = 0; p < np; ++p) {
+    for (int p = c.x; p < c.x + np; ++p) {
         const PieceDev& P = pieces[p];
         const int lc = l - P.l_lo;
         const int Nr = P.Nrho;
@@ -678,20 +698,26 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
             acc[i] += sc * (wr[0] * r[0] + wr[1] * r[1] + wr[2] * r[2] + wr[3] * r[3]);
         }
     }
-    float* gl = g + (size_t)l * Ntau;
+    float* gl = g + pieces[c.x].g_off + (size_t)l * Ntau;
     for (int i = threadIdx.x; i < Ntau; i += blockDim.x) gl[i] = acc[i];
 }
 
 // Adjoint of the gridding (transpose of Eq. (15)): every gather sample reads
-// the 4x4 taps of each sub-problem that holds it.
-__global__ void __launch_bounds__(256) k_gather_samples(const PieceDev* __restrict__ pieces, int np,
-                                                        int Nt, int Nx, float* __restrict__ f) {
-    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long)Nt * Nx) return;
+// the 4x4 taps of each sub-problem that holds it. One CTA per kSampleBlock
+// samples of one gather: smap[b] = (first piece, number of pieces, first
+// sample of the block within the gather).
+__global__ void __launch_bounds__(kSampleBlock) k_gather_samples(const PieceDev* __restrict__ pieces,
+                                                                 const int4* __restrict__ smap,
+                                                                 float* __restrict__ f) {
+    const int4 m = __ldg(smap + blockIdx.x);
+    const PieceDev& P0 = pieces[m.x];
+    const int Nt = P0.Nt;
+    const long idx = (long)m.z + threadIdx.x;
+    if (idx >= (long)Nt * P0.Nx) return;
     const int k = (int)(idx / Nt);
     const int j = (int)(idx - (long)k * Nt);
     float acc = 0.f;
-    for (int p = 0; p < np; ++p) {
+    for (int p = m.x; p < m.x + m.y; ++p) {
         const PieceDev& P = pieces[p];
         if (j < P.jt_lo || j > P.jt_hi) continue;
         const int4 e = __ldg(reinterpret_cast<const int4*>(P.stab + (size_t)k * P.nj + (j - P.jt_lo)));
@@ -702,7 +728,7 @@ __global__ void __launch_bounds__(256) k_gather_samples(const PieceDev* __restri
         b3_weights(__int_as_float(e.z), wr);
         acc += w * taps16(P.lat, P.Nrho, e.x >> 16, e.x & 0xffff, wt, wr);
     }
-    f[idx] = acc;
+    f[P0.f_off + idx] = acc;
 }
 
 // --------------------------------------------------------------------------
@@ -923,7 +949,7 @@ static int make_batch(const PieceDev* P, int n, PieceBatch& B, F&& count) {
 int launch_grid_tiles(const PieceDev* P, int n, const float* f, void* stream) {
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nunits; });
-    if (nb > 0) k_grid_tiles<<<nb, kUnitChunks, 0, (cudaStream_t)stream>>>(B, f);
+    if (nb > 0) k_grid_tiles<PieceBatch, float><<<nb, kUnitChunks, 0, (cudaStream_t)stream>>>(B, f);
     return check_launch();
 }
 
@@ -933,69 +959,98 @@ static size_t max_over(const PieceDev* P, int n, size_t (*fn)(const PieceDev&)) 
     return m;
 }
 
-int launch_rows_r2c(const PieceDev* P, int n, void* stream) {
-    const size_t sm = max_over(P, n, scatter_smem_bytes);
-    if (int e = set_smem((const void*)k_rows_r2c, sm)) return e;
-    PieceBatch B;
-    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
-    if (nb > 0) k_rows_r2c<<<nb, 512, sm, (cudaStream_t)stream>>>(B);
+size_t rows_smem_bytes(const PieceDev& P) { return scatter_smem_bytes(P); }
+size_t profile_smem_bytes(const PieceDev& P) { return (size_t)P.Nrho * sizeof(int); }
+
+// One stage over n <= kMaxBatch pieces (descriptors as a parameter) or over
+// a device-resident batch (descriptors and block map in device memory).
+template <class Src>
+static int set_and_launch(void (*kern)(Src), int nb, size_t sm, const Src& B, void* stream) {
+    if (int e = set_smem((const void*)kern, sm)) return e;
+    if (nb > 0) kern<<<nb, 512, sm, (cudaStream_t)stream>>>(B);
     return check_launch();
 }
 
+int launch_rows_r2c(const PieceDev* P, int n, void* stream) {
+    PieceBatch B;
+    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
+    return set_and_launch(k_rows_r2c<PieceBatch>, nb, max_over(P, n, rows_smem_bytes), B, stream);
+}
+
 int launch_col_profiles(const PieceDev* P, int n, const float* g, void* stream) {
-    const size_t sm = max_over(P, n, [](const PieceDev& q) { return (size_t)q.Nrho * sizeof(int); });
-    if (int e = set_smem((const void*)k_col_profiles, sm)) return e;
+    const size_t sm = max_over(P, n, profile_smem_bytes);
+    if (int e = set_smem((const void*)k_col_profiles<PieceBatch>, sm)) return e;
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.l_hi - q.l_lo + 1; });
-    if (nb > 0) k_col_profiles<<<nb, 256, sm, (cudaStream_t)stream>>>(B, g);
+    if (nb > 0) k_col_profiles<PieceBatch><<<nb, 256, sm, (cudaStream_t)stream>>>(B, g);
     return check_launch();
 }
 
 int launch_band_rows(const PieceDev* P, int n, void* stream) {
-    const size_t sm = max_over(P, n, scatter_smem_bytes);
-    if (int e = set_smem((const void*)k_band_rows, sm)) return e;
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
-    if (nb > 0) k_band_rows<<<nb, 512, sm, (cudaStream_t)stream>>>(B);
-    return check_launch();
+    return set_and_launch(k_band_rows<PieceBatch>, nb, max_over(P, n, rows_smem_bytes), B, stream);
 }
 
 int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream) {
     const size_t sm = max_over(P, n, colconv_smem_bytes);
-    if (int e = set_smem((const void*)k_colconv, sm)) return e;
+    if (int e = set_smem((const void*)k_colconv<PieceBatch>, sm)) return e;
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nkb; });
-    if (nb > 0) k_colconv<<<nb, 512, sm, (cudaStream_t)stream>>>(B, adjoint);
+    if (nb > 0) k_colconv<PieceBatch><<<nb, 512, sm, (cudaStream_t)stream>>>(B, adjoint);
     return check_launch();
 }
 
 int launch_rows_c2r(const PieceDev* P, int n, void* stream) {
-    const size_t sm = max_over(P, n, scatter_smem_bytes);
-    if (int e = set_smem((const void*)k_rows_c2r, sm)) return e;
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
-    if (nb > 0) k_rows_c2r<<<nb, 512, sm, (cudaStream_t)stream>>>(B);
+    return set_and_launch(k_rows_c2r<PieceBatch>, nb, max_over(P, n, rows_smem_bytes), B, stream);
+}
+
+int launch_grid_tiles_dev(const DevBatch& S, int nblocks, const void* f, int in_type, void* stream) {
+    if (nblocks <= 0) return 0;
+    if (in_type == kInBF16)
+        k_grid_tiles<DevBatch, __nv_bfloat16><<<nblocks, kUnitChunks, 0, (cudaStream_t)stream>>>(
+            S, (const __nv_bfloat16*)f);
+    else
+        k_grid_tiles<DevBatch, float><<<nblocks, kUnitChunks, 0, (cudaStream_t)stream>>>(S, (const float*)f);
     return check_launch();
 }
 
-int launch_interp_columns(const PieceDev* pieces, int npieces, const PieceDev* dev_pieces, int l_lo,
-                          int l_hi, float* g, void* stream) {
-    const int ncol = l_hi - l_lo + 1;
-    const int Ntau = pieces[0].Ntau;
-    int nrho_max = 0;
-    for (int p = 0; p < npieces; ++p) nrho_max = std::max(nrho_max, pieces[p].Nrho);
-    const size_t sm = ((size_t)nrho_max + Ntau) * sizeof(float);
+int launch_rows_r2c_dev(const DevBatch& S, int nblocks, size_t smem, void* stream) {
+    return set_and_launch(k_rows_r2c<DevBatch>, nblocks, smem, S, stream);
+}
+
+int launch_col_profiles_dev(const DevBatch& S, int nblocks, size_t smem, const float* g, void* stream) {
+    if (int e = set_smem((const void*)k_col_profiles<DevBatch>, smem)) return e;
+    if (nblocks > 0) k_col_profiles<DevBatch><<<nblocks, 256, smem, (cudaStream_t)stream>>>(S, g);
+    return check_launch();
+}
+
+int launch_band_rows_dev(const DevBatch& S, int nblocks, size_t smem, void* stream) {
+    return set_and_launch(k_band_rows<DevBatch>, nblocks, smem, S, stream);
+}
+
+int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream) {
+    if (int e = set_smem((const void*)k_colconv<DevBatch>, smem)) return e;
+    if (nblocks > 0) k_colconv<DevBatch><<<nblocks, 512, smem, (cudaStream_t)stream>>>(S, adjoint);
+    return check_launch();
+}
+
+int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* stream) {
+    return set_and_launch(k_rows_c2r<DevBatch>, nblocks, smem, S, stream);
+}
+
+int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int ntau_max,
+                          float* g, void* stream) {
+    const size_t sm = ((size_t)nrho_max + ntau_max) * sizeof(float);
     if (int e = set_smem((const void*)k_interp_columns, sm)) return e;
-    k_interp_columns<<<ncol, 256, sm, (cudaStream_t)stream>>>(dev_pieces, npieces, l_lo, Ntau, nrho_max, g);
+    if (ncols > 0) k_interp_columns<<<ncols, 256, sm, (cudaStream_t)stream>>>(pieces, cmap, nrho_max, g);
     return check_launch();
 }
 
-int launch_gather_samples(const PieceDev* dev_pieces, int npieces, int Nt, int Nx, float* f,
-                          void* stream) {
-    const long total = (long)Nt * Nx;
-    const int bs = 256;
-    const long nb = (total + bs - 1) / bs;
-    k_gather_samples<<<(unsigned)nb, bs, 0, (cudaStream_t)stream>>>(dev_pieces, npieces, Nt, Nx, f);
+int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, void* stream) {
+    if (nblocks > 0) k_gather_samples<<<nblocks, kSampleBlock, 0, (cudaStream_t)stream>>>(pieces, smap, f);
     return check_launch();
 }
 

@@ -197,6 +197,11 @@ struct radon_plan_s {
     PieceDev* dev_pieces = nullptr;
     float* lat_all = nullptr;                    // every piece's lattice, back to back
     size_t lat_bytes = 0;
+    const int4* cmap = nullptr;                  // output columns: (first piece, count, l, 0)
+    int ncols = 0;
+    const int4* smap = nullptr;                  // sample blocks: (first piece, count, first sample, 0)
+    int nsblocks = 0;
+    int nrho_max = 0;
     std::vector<void*> allocs;
     size_t bytes = 0;
     // per-stage timing
@@ -768,6 +773,22 @@ size_t piece_profile_bytes(const PieceDev& P) {
     return round256b((size_t)(P.l_hi - P.l_lo + 1) * P.hpitch * sizeof(float));
 }
 
+// Output columns of a plan for the interpolation kernel: every column of
+// every slowness piece with the range of its time pieces (piece indices
+// offset by `base`, the plan's first piece in a larger descriptor array).
+void column_map(const radon_plan_s* p, int base, std::vector<int4>& out) {
+    for (size_t qi = 0; qi < p->qpieces.size(); ++qi)
+        for (int l = p->qpieces[qi].first; l <= p->qpieces[qi].second; ++l)
+            out.push_back(int4{base + p->qfirst[qi], p->qcount[qi], l, 0});
+}
+
+// Sample blocks of a plan's gather for the adjoint gather kernel.
+void sample_map(const radon_plan_s* p, int base, int, std::vector<int4>& out) {
+    const long n = (long)p->d.Nt * p->d.Nx;
+    for (long b = 0; b < n; b += kSampleBlock)
+        out.push_back(int4{base, (int)p->pieces.size(), (int)b, 0});
+}
+
 void destroy_plan(radon_plan_s* p) {
     if (!p) return;
     for (void* a : p->allocs) cudaFree(a);
@@ -840,8 +861,9 @@ extern "C" radon_status radon_plan_create(radon_plan* out, int Nt, int Nx, int N
     return radon_plan_create_ex(out, &d);
 }
 
-extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* din) {
-    if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
+// Geometry, tables and kernel spectra of every piece of a plan, and the
+// column and sample maps of its two gathers; no work buffers.
+static radon_status plan_core(const radon_desc* din, radon_plan_s** out) {
     *out = nullptr;
     if (radon_status s = check_desc(din)) return s;
     radon_plan_s* p = new (std::nothrow) radon_plan_s();
@@ -884,6 +906,27 @@ extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* 
         }
         p->qcount.push_back((int)tps.size());
     }
+    std::vector<int4> cmap, smap;
+    column_map(p, 0, cmap);
+    sample_map(p, 0, 0, smap);
+    radon_status s = RADON_OK;
+    if ((s = dev_upload(p, cmap, &p->cmap)) || (s = dev_upload(p, smap, &p->smap))) {
+        destroy_plan(p);
+        return s;
+    }
+    p->ncols = (int)cmap.size();
+    p->nsblocks = (int)smap.size();
+    for (auto& h : p->pieces) p->nrho_max = std::max(p->nrho_max, h.dev.Nrho);
+    *out = p;
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* din) {
+    if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    radon_plan_s* p = nullptr;
+    if (radon_status s = plan_core(din, &p)) return s;
+    DeviceGuard guard(p->device);
     // per-piece work buffers: lattices back to back (one clear per forward),
     // spectra (the column pass works in place), adjoint column profiles
     size_t lat_b = 0, spec_b = 0, prof_b = 0;
@@ -937,7 +980,7 @@ static radon_status cuda_status(int e, const char* what) {
 // The forward chain over the pieces `P` (host copies; `dP` the same on the
 // device), lattices in [lat, lat + lat_bytes). Every stage is one launch per
 // group of at most kMaxBatch pieces; the output interpolation is one launch
-// per slowness piece.
+// over every output column.
 static radon_status run_forward(radon_plan_s* p, const PieceDev* P, const PieceDev* dP, float* lat,
                                 size_t lat_bytes, const float* f, float* g, void* stream) {
     const int np = (int)p->pieces.size();
@@ -976,20 +1019,12 @@ static radon_status run_forward(radon_plan_s* p, const PieceDev* P, const PieceD
                   [&] { return groups([&](const PieceDev* q, int n) { return launch_rows_c2r(q, n, stream); }); }),
             "inverse row FFT"))
         return s;
-    for (size_t qi = 0; qi < p->qpieces.size(); ++qi) {
-        const int first = p->qfirst[qi], count = p->qcount[qi];
-        double bl = 0;
-        for (int t = 0; t < count; ++t) bl += bytes_lattice(P[first + t]);
-        const double gb = 4.0 * p->d.Ntau * (p->qpieces[qi].second - p->qpieces[qi].first + 1);
-        if (radon_status s = cuda_status(
-                timed(p, 4, bl + gb, stream,
-                      [&] {
-                          return launch_interp_columns(P + first, count, dP + first, p->qpieces[qi].first,
-                                                       p->qpieces[qi].second, g, stream);
-                      }),
-                "interpolation"))
-            return s;
-    }
+    const double gb = 4.0 * p->d.Ntau * p->d.Nq;
+    if (radon_status s = cuda_status(
+            timed(p, 4, b_lat + gb, stream,
+                  [&] { return launch_interp_columns(dP, p->cmap, p->ncols, p->nrho_max, p->d.Ntau, g, stream); }),
+            "interpolation"))
+        return s;
     return RADON_OK;
 }
 
@@ -1047,9 +1082,7 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
             "inverse row FFT"))
         return s;
     return cuda_status(timed(p, 8, b_lat + 4.0 * p->d.Nt * p->d.Nx, stream,
-                             [&] {
-                                 return launch_gather_samples(p->dev_pieces, np, p->d.Nt, p->d.Nx, f, stream);
-                             }),
+                             [&] { return launch_gather_samples(p->dev_pieces, p->smap, p->nsblocks, f, stream); }),
                        "adjoint gridding");
 }
 
@@ -1189,6 +1222,197 @@ extern "C" radon_status radon_plan_profile_read(radon_plan p, double ms[RADON_NS
 extern "C" const char* radon_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char* radon_version(void) { return "hradon 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Batches of gathers of different sizes: every stage one launch over all
+// sub-problems of all gathers, descriptors and block maps in device memory.
+// ---------------------------------------------------------------------------
+struct radon_batch_s {
+    int device = 0;
+    std::vector<radon_plan_s*> plans;
+    radon_plan_s* store = nullptr;             // owns the batch's own device allocations
+    std::vector<long long> f_off, g_off;       // n + 1 prefix offsets (elements)
+    const PieceDev* pieces = nullptr;          // every piece of every gather
+    const int2 *map_units = nullptr, *map_bands = nullptr, *map_kb = nullptr, *map_cols = nullptr;
+    int n_units = 0, n_bands = 0, n_kb = 0, n_cols = 0;
+    const int4* cmap = nullptr;
+    const int4* smap = nullptr;
+    int ncols = 0, nsblocks = 0;
+    size_t smem_rows = 0, smem_cols = 0, smem_prof = 0;
+    int nrho_max = 0, ntau_max = 0;
+    float* lat_all = nullptr;
+    size_t lat_bytes = 0;
+};
+
+static void destroy_batch(radon_batch_s* b) {
+    if (!b) return;
+    for (radon_plan_s* p : b->plans) destroy_plan(p);
+    destroy_plan(b->store);
+    delete b;
+}
+
+extern "C" radon_status radon_batch_create(radon_batch* out, int n, const radon_desc* descs) {
+    if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !descs) return fail(RADON_ERR_INVALID_ARG, "a batch needs n >= 1 descriptors");
+    radon_batch_s* b = new (std::nothrow) radon_batch_s();
+    if (!b) return fail(RADON_ERR_OOM, "host allocation failed");
+    b->store = new (std::nothrow) radon_plan_s();
+    if (!b->store) {
+        delete b;
+        return fail(RADON_ERR_OOM, "host allocation failed");
+    }
+    b->f_off.push_back(0);
+    b->g_off.push_back(0);
+    for (int i = 0; i < n; ++i) {
+        radon_desc d = descs[i];
+        if (i > 0) d.device = b->device;
+        radon_plan_s* p = nullptr;
+        if (radon_status s = plan_core(&d, &p)) {
+            destroy_batch(b);
+            return s;
+        }
+        if (i == 0) b->device = p->device;
+        b->plans.push_back(p);
+        b->f_off.push_back(b->f_off.back() + (long long)p->d.Nt * p->d.Nx);
+        b->g_off.push_back(b->g_off.back() + (long long)p->d.Ntau * p->d.Nq);
+    }
+    DeviceGuard guard(b->device);
+    b->store->device = b->device;
+    // work buffers of every piece, lattices back to back (one clear per forward)
+    std::vector<PieceDev> host;
+    for (int i = 0; i < n; ++i)
+        for (auto& h : b->plans[i]->pieces) {
+            PieceDev P = h.dev;
+            P.f_off = b->f_off[i];
+            P.g_off = b->g_off[i];
+            host.push_back(P);
+        }
+    size_t lat_b = 0, spec_b = 0, prof_b = 0;
+    for (auto& P : host) {
+        lat_b += piece_lattice_bytes(P);
+        spec_b += piece_spectrum_bytes(P);
+        prof_b += piece_profile_bytes(P);
+    }
+    void *lat = nullptr, *spec = nullptr, *prof = nullptr;
+    radon_status s = RADON_OK;
+    if ((s = dev_alloc(b->store, lat_b, &lat)) || (s = dev_alloc(b->store, spec_b, &spec)) ||
+        (s = dev_alloc(b->store, prof_b, &prof))) {
+        destroy_batch(b);
+        return s;
+    }
+    b->lat_all = (float*)lat;
+    b->lat_bytes = lat_b;
+    for (auto& P : host) {
+        P.lat = (float*)lat;
+        P.spec = (cf*)spec;
+        P.prof = (float*)prof;
+        lat = (char*)lat + piece_lattice_bytes(P);
+        spec = (char*)spec + piece_spectrum_bytes(P);
+        prof = (char*)prof + piece_profile_bytes(P);
+        b->smem_rows = std::max(b->smem_rows, rows_smem_bytes(P));
+        b->smem_cols = std::max(b->smem_cols, colconv_smem_bytes(P));
+        b->smem_prof = std::max(b->smem_prof, profile_smem_bytes(P));
+        b->nrho_max = std::max(b->nrho_max, P.Nrho);
+        b->ntau_max = std::max(b->ntau_max, P.Ntau);
+    }
+    // block maps of the stage launches and the maps of the two gathers
+    std::vector<int2> mu, mb, mk, mc;
+    for (int gi = 0; gi < (int)host.size(); ++gi) {
+        const PieceDev& P = host[gi];
+        for (int u = 0; u < P.nunits; ++u) mu.push_back(int2{gi, u});
+        for (int u = 0; u < P.nbands; ++u) mb.push_back(int2{gi, u});
+        for (int u = 0; u < P.nkb; ++u) mk.push_back(int2{gi, u});
+        for (int u = 0; u < P.l_hi - P.l_lo + 1; ++u) mc.push_back(int2{gi, u});
+    }
+    std::vector<int4> cmap, smap;
+    int base = 0;
+    for (radon_plan_s* p : b->plans) {
+        column_map(p, base, cmap);
+        sample_map(p, base, 0, smap);
+        base += (int)p->pieces.size();
+    }
+    if ((s = dev_upload(b->store, host, &b->pieces)) || (s = dev_upload(b->store, mu, &b->map_units)) ||
+        (s = dev_upload(b->store, mb, &b->map_bands)) || (s = dev_upload(b->store, mk, &b->map_kb)) ||
+        (s = dev_upload(b->store, mc, &b->map_cols)) || (s = dev_upload(b->store, cmap, &b->cmap)) ||
+        (s = dev_upload(b->store, smap, &b->smap))) {
+        destroy_batch(b);
+        return s;
+    }
+    b->n_units = (int)mu.size();
+    b->n_bands = (int)mb.size();
+    b->n_kb = (int)mk.size();
+    b->n_cols = (int)mc.size();
+    b->ncols = (int)cmap.size();
+    b->nsblocks = (int)smap.size();
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        destroy_batch(b);
+        return fail(RADON_ERR_CUDA, "batch creation failed on the device");
+    }
+    *out = b;
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_batch_destroy(radon_batch b) {
+    if (!b) return RADON_OK;
+    DeviceGuard guard(b->device);
+    cudaDeviceSynchronize();
+    destroy_batch(b);
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_batch_layout(radon_batch b, int* n, long long* f_offsets, long long* g_offsets) {
+    if (!b) return fail(RADON_ERR_INVALID_ARG, "batch is NULL");
+    if (n) *n = (int)b->plans.size();
+    for (size_t i = 0; i < b->f_off.size(); ++i) {
+        if (f_offsets) f_offsets[i] = b->f_off[i];
+        if (g_offsets) g_offsets[i] = b->g_off[i];
+    }
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_batch_plan(radon_batch b, int i, radon_desc* d) {
+    if (!b || !d) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
+    if (i < 0 || i >= (int)b->plans.size()) return fail(RADON_ERR_INVALID_ARG, "gather index out of range");
+    *d = b->plans[i]->d;
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_batch_fwd(radon_batch b, const void* f, int in_type, float* g, void* stream) {
+    if (!b) return fail(RADON_ERR_INVALID_ARG, "batch is NULL");
+    if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    if (in_type != RADON_IN_F32 && in_type != RADON_IN_BF16) return fail(RADON_ERR_INVALID_ARG, "unknown input type");
+    DeviceGuard guard(b->device);
+    const DevBatch U{b->pieces, b->map_units}, Bd{b->pieces, b->map_bands}, K{b->pieces, b->map_kb};
+    if (cudaError_t e = cudaMemsetAsync(b->lat_all, 0, b->lat_bytes, (cudaStream_t)stream))
+        return cuda_status((int)e, "clearing the lattices");
+    if (radon_status s = cuda_status(launch_grid_tiles_dev(U, b->n_units, f, in_type, stream), "gridding")) return s;
+    if (radon_status s = cuda_status(launch_rows_r2c_dev(Bd, b->n_bands, b->smem_rows, stream), "row FFT")) return s;
+    if (radon_status s = cuda_status(launch_colconv_dev(K, b->n_kb, b->smem_cols, 0, stream), "convolution"))
+        return s;
+    if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
+        return s;
+    return cuda_status(launch_interp_columns(b->pieces, b->cmap, b->ncols, b->nrho_max, b->ntau_max, g, stream),
+                       "interpolation");
+}
+
+extern "C" radon_status radon_batch_adj(radon_batch b, const float* g, float* f, void* stream) {
+    if (!b) return fail(RADON_ERR_INVALID_ARG, "batch is NULL");
+    if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    DeviceGuard guard(b->device);
+    const DevBatch C{b->pieces, b->map_cols}, Bd{b->pieces, b->map_bands}, K{b->pieces, b->map_kb};
+    if (radon_status s = cuda_status(launch_col_profiles_dev(C, b->n_cols, b->smem_prof, g, stream),
+                                     "adjoint interpolation (profiles)"))
+        return s;
+    if (radon_status s = cuda_status(launch_band_rows_dev(Bd, b->n_bands, b->smem_rows, stream),
+                                     "adjoint interpolation (bands)"))
+        return s;
+    if (radon_status s = cuda_status(launch_colconv_dev(K, b->n_kb, b->smem_cols, 1, stream), "adjoint convolution"))
+        return s;
+    if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
+        return s;
+    return cuda_status(launch_gather_samples(b->pieces, b->smap, b->nsblocks, f, stream), "adjoint gridding");
+}
 
 // ---------------------------------------------------------------------------
 // Forward transform on caller-given work memory (used by radon_fwd_noalloc in

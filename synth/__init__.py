@@ -19,6 +19,7 @@ import numpy as np
 __all__ = [
     "Geometry", "ricker", "rng_for", "hyperbolic_gather", "gaussian_gather",
     "random_radon_image", "single_gather", "sweep_gather", "large_gather", "missing_trace_gather",
+    "batch_gather",
     "band_limited_gather", "batch_geometries",
 ]
 
@@ -196,6 +197,16 @@ def missing_trace_gather(tag: int = 3, Nt: int = 1024, Nx: int = 256, n_events: 
     mask = np.ones(Nx)
     mask[rng.choice(Nx, int(round(missing * Nx)), replace=False)] = 0.0
     return geo, f, mask
+
+
+def batch_gather(geo: Geometry, tag: int) -> np.ndarray:
+    """One gather of the uneven batch: 10-40 Ricker hyperbolas (tau0 ~
+    U[0.1, 0.9 T] s, q0 ~ U[0.25, 0.65] s/km, 10-25 Hz, A ~ N(0, 1))."""
+    rng = rng_for(4000 + tag)
+    n = int(rng.integers(10, 41))
+    T = (geo.Nt - 1) * geo.dt
+    return hyperbolic_gather(geo, rng.uniform(0.1, 0.9 * T, n), rng.uniform(0.25, 0.65, n),
+                             rng.uniform(10.0, 25.0, n), rng.standard_normal(n))
 
 
 def batch_geometries(n: int, tag: int = 4) -> list[Geometry]:
