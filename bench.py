@@ -227,6 +227,55 @@ def sparse_inversion(dev, stream) -> dict:
             "rel_l2_missing_traces": err, "opnorm_R2": lam}
 
 
+def batched_uneven(dev, n: int) -> dict:
+    """Uneven batch: n gathers with Nt ~ U{500..3000} (dt 4 ms), Nx ~
+    U{60..480} (dx 25 m), Nq = Nx, 10-40 Ricker events each, stored BF16,
+    computed FP32; forward + adjoint of the whole batch as one CUDA graph
+    (5 + 5 launches), timed over replays."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1604_07651_gb300 as hr
+    geos = synth.batch_geometries(n)
+    t0 = time.time()
+    batch = hr.Batch([dict(Nt=g.Nt, Nx=g.Nx, Ntau=g.Ntau, Nq=g.Nq, dt=g.dt, dx=g.dx, qmin=g.qmin,
+                           qmax=g.qmax) for g in geos])
+    t_plan = time.time() - t0
+    f = batch.pack([torch.tensor(synth.batch_gather(g, i), dtype=torch.float32) for i, g in enumerate(geos)],
+                   dtype=torch.bfloat16)
+    g = torch.empty(batch.g_offsets[-1], dtype=torch.float32, device=dev)
+    fa = torch.empty(batch.f_offsets[-1], dtype=torch.float32, device=dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            batch.forward(f, out=g)
+            batch.adjoint(g, out=fa)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.forward(f, out=g)
+        batch.adjoint(g, out=fa)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    reps = 10
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for _ in range(reps):
+        graph.replay()
+    a1.record()
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / reps
+    samples = int(sum(g_.Nt * g_.Nx for g_ in geos))
+    batch.close()
+    return {"workload": f"{n} uneven gathers, Nt 500-3000 (4 ms), Nx 60-480 (25 m), Nq = Nx, 10-40 events, "
+                        f"BF16 input, {samples / 1e6:.1f} M samples",
+            "gathers_per_s": n / (ms / 1e3), "ms_per_batch_fwd_adj": ms, "launches_per_batch": 10,
+            "plan_s": t_plan, "graph": True}
+
+
 def measured_traffic(kernel: str):
     import hashlib
     ent = MEASURED_TRAFFIC.get(kernel)
@@ -318,6 +367,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--no-solver", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-gathers", type=int, default=256)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -483,6 +534,8 @@ def main():
                                         "speedup_of_log_polar": value / world / (1e3 / dms)}
         if not args.no_solver:
             result["sparse_inversion"] = sparse_inversion(dev, stream)
+        if not args.no_batch:
+            result["batched_uneven"] = batched_uneven(dev, args.batch_gathers)
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(geo, f_np)
         print(json.dumps(result), flush=True)
