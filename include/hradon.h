@@ -260,6 +260,33 @@ radon_status radon_opnorm(radon_plan p, const float* v0, int iters, float* norm2
                           size_t work_bytes, void* stream);
 
 /*
+ * Radon-domain mute (Section 6, multiple attenuation): out = g with the
+ * outputs (tau_i, q_l) on one side of the line q = q0 + slope * tau set to
+ * zero. side RADON_KEEP_BELOW zeroes q > q0 + slope tau (keeps the
+ * primaries, smaller slowness), RADON_KEEP_ABOVE zeroes q <= q0 + slope tau
+ * (keeps the multiples). g, out: [Nq][Ntau] device FP32 (may be the same
+ * buffer). Asynchronous on `stream`.
+ */
+#define RADON_KEEP_BELOW 0
+#define RADON_KEEP_ABOVE 1
+radon_status radon_mute(radon_plan p, const float* g, float* out, double q0, double slope, int side,
+                        void* stream);
+
+/*
+ * Multiple attenuation: g = the sparse Radon image of f after `iters`
+ * soft-thresholding iterations (radon_ista with every trace; g is the
+ * starting iterate in and the image out), then
+ *   f_out = f - R_h*( g restricted to q > q0 + slope * tau ),
+ * the gather with the multiples' part of the image subtracted. f, f_out:
+ * [Nx][Nt] device FP32 (distinct); work: radon_demultiple_work_bytes bytes,
+ * 256-byte aligned. Errors as radon_ista.
+ */
+radon_status radon_demultiple_work_bytes(radon_plan p, size_t* bytes);
+radon_status radon_demultiple(radon_plan p, const float* f, double q0, double slope, int iters,
+                              float c2, float mu, int accelerate, float* g, float* f_out, void* work,
+                              size_t work_bytes, void* stream);
+
+/*
  * Forward transform that allocates nothing, for callers that cannot call
  * cudaMalloc when they run (a host framework that has reserved the whole
  * device for its own pool, deployments with a fixed device footprint, loops

@@ -73,3 +73,24 @@ def power_norm2(fwd, adj, v0, iters: int) -> float:
         lam = float(np.linalg.norm(z))
         v = z / lam
     return lam
+
+
+def mute(g, tau, q, q0: float, slope: float, keep: str = "below"):
+    """The Radon-domain mute of the multiple attenuation (Section 6): zero
+    the outputs (tau_i, q_l) of g[l][i] above the line q = q0 + slope * tau
+    (keep="below": the primaries) or on or below it (keep="above": the
+    multiples)."""
+    g = np.array(g, dtype=np.float64)
+    above = np.asarray(q, dtype=np.float64)[:, None] > q0 + slope * np.asarray(tau, dtype=np.float64)[None, :]
+    g[above if keep == "below" else ~above] = 0.0
+    return g
+
+
+def demultiple(fwd, adj, f, tau, q, q0: float, slope: float, iters: int, c2: float, mu: float,
+               accelerate: bool = False):
+    """Multiple attenuation as the paper describes it: sparse Radon image by
+    the soft-thresholding iteration, the multiples' part of it (beyond the
+    border line) taken back to (t, x) and subtracted from the gather.
+    Returns (f - multiples, sparse image)."""
+    g = ista(fwd, adj, f, mu, c2, iters, accelerate=accelerate)
+    return np.asarray(f, dtype=np.float64) - adj(mute(g, tau, q, q0, slope, keep="above")), g

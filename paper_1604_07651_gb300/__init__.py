@@ -201,6 +201,38 @@ class Plan:
         return out
 
 
+    def mute(self, g: torch.Tensor, q0: float, slope: float, keep: str = "below",
+             out: torch.Tensor | None = None) -> torch.Tensor:
+        """Radon-domain mute along the line q = q0 + slope * tau: keep the
+        part below it (primaries) or above it (multiples)."""
+        _check_tensor(g, (self.Nq, self.Ntau), "g", self.device)
+        if out is None:
+            out = torch.empty_like(g)
+        _check_tensor(out, (self.Nq, self.Ntau), "out", self.device)
+        side = {"below": 0, "above": 1}[keep]
+        _lib.check(_lib.load().radon_mute(self._handle, ctypes.c_void_p(g.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), float(q0), float(slope), side,
+                                          _stream_ptr(self.device)))
+        return out
+
+    def demultiple(self, f: torch.Tensor, q0: float, slope: float, mu: float, iters: int = 30, *,
+                   step: float | None = None, accelerate: bool = False):
+        """Multiple attenuation: returns (f minus the multiples, sparse image).
+        The multiples are the part of the sparse Radon image above the line
+        q = q0 + slope * tau, taken back with the adjoint."""
+        _check_tensor(f, (self.Nx, self.Nt), "f", self.device)
+        if step is None:
+            step = 0.95 / self.opnorm()
+        g = torch.zeros((self.Nq, self.Ntau), dtype=torch.float32, device=self.device)
+        f_out = torch.empty_like(f)
+        work = self._work("radon_demultiple_work_bytes")
+        _lib.check(_lib.load().radon_demultiple(
+            self._handle, ctypes.c_void_p(f.data_ptr()), float(q0), float(slope), int(iters), float(step),
+            float(mu), int(bool(accelerate)), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(f_out.data_ptr()),
+            ctypes.c_void_p(work.data_ptr()), work.numel(), _stream_ptr(self.device)))
+        return f_out, g
+
+
 def _desc(Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax, tau0=0.0, dtau=0.0, sigma=None, omega_c=None,
           tsplit=None, n_qsplit=1, device=0) -> RadonDesc:
     d = RadonDesc()

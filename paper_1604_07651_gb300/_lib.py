@@ -58,6 +58,10 @@ SIGNATURES = {
     "radon_ista": (_c_int, [_vp, _vp, _vp, _vp, _c_int, ctypes.c_float, ctypes.c_float, _c_int, _vp,
                             ctypes.c_size_t, _vp]),
     "radon_opnorm_work_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "radon_mute": (_c_int, [_vp, _vp, _vp, _c_double, _c_double, _c_int, _vp]),
+    "radon_demultiple_work_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "radon_demultiple": (_c_int, [_vp, _vp, _c_double, _c_double, _c_int, ctypes.c_float, ctypes.c_float,
+                                  _c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "radon_opnorm": (_c_int, [_vp, _vp, _c_int, _vp, _vp, ctypes.c_size_t, _vp]),
     "radon_direct_fwd": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_double,
                                   _c_double, _c_double, _c_double, _c_double, _c_double, _vp]),

@@ -13,6 +13,12 @@
 // Each iteration is radon_adj, one fused residual kernel, radon_fwd and one
 // fused threshold/extrapolation kernel, all on the caller's stream; the host
 // only computes the scalar momentum sequence.
+//
+// Multiple attenuation (Section 6, "Multiple attenuation"): primaries and
+// multiples separate by moveout in the sparse Radon image; the part of the
+// image beyond a border line in the (tau, q) plane (larger slowness: the
+// multiples) is taken back to (t, x) with R_h* and subtracted from the
+// gather.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -93,6 +99,28 @@ __global__ void __launch_bounds__(kThreads) k_normalize(const float* __restrict_
     if (norm_out && blockIdx.x == 0 && threadIdx.x == 0) *norm_out = (float)nrm;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         y[i] = x[i] * inv;
+}
+
+// Zero g[l][i] on one side of the line q = q0 + slope * tau in the (tau, q)
+// plane: side 0 zeroes q > q0 + slope tau (keeps the primaries), side 1
+// zeroes q <= q0 + slope tau (keeps the multiples). src may alias dst.
+__global__ void __launch_bounds__(kThreads) k_mute(const float* src, float* dst, int Ntau, long n, double tau0,
+                                                  double dtau, double qmin, double dq, double q0, double slope,
+                                                  int side) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const long l = i / Ntau;
+        const double tau = tau0 + dtau * (double)(i - l * Ntau);
+        const double q = qmin + dq * (double)l;
+        const bool above = q > q0 + slope * tau;
+        dst[i] = (above == (side == 0)) ? 0.f : src[i];
+    }
+}
+
+// out = a - b, elementwise.
+__global__ void __launch_bounds__(kThreads) k_subtract(const float* __restrict__ a, const float* __restrict__ b,
+                                                      float* __restrict__ out, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        out[i] = __ldg(a + i) - __ldg(b + i);
 }
 
 int grid_for(long n) {
@@ -204,5 +232,53 @@ extern "C" radon_status radon_opnorm(radon_plan p, const float* v0, int iters, f
         k_normalize<<<grid_for(ni), kThreads, 0, s>>>(z, v, ni, part, kNormBlocks, norm2);
         if (int e = last_cuda()) return cuda_fail(e, "power iteration");
     }
+    return RADON_OK;
+}
+
+static double q_step(const radon_desc& d) { return d.Nq > 1 ? (d.qmax - d.qmin) / (d.Nq - 1) : 0.0; }
+
+extern "C" radon_status radon_mute(radon_plan p, const float* g, float* out, double q0, double slope, int side,
+                                   void* stream) {
+    if (!p) return (radon_status)set_error(RADON_ERR_INVALID_ARG, "plan is NULL");
+    if (!g || !out) return (radon_status)set_error(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    if (side != RADON_KEEP_BELOW && side != RADON_KEEP_ABOVE)
+        return (radon_status)set_error(RADON_ERR_INVALID_ARG, "side must be RADON_KEEP_BELOW or RADON_KEEP_ABOVE");
+    radon_desc d;
+    radon_plan_desc(p, &d);
+    const long ni = (long)d.Nq * d.Ntau;
+    k_mute<<<grid_for(ni), kThreads, 0, (cudaStream_t)stream>>>(g, out, d.Ntau, ni, d.tau0, d.dtau, d.qmin, q_step(d),
+                                                                 q0, slope, side);
+    if (int e = last_cuda()) return cuda_fail(e, "mute");
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_demultiple_work_bytes(radon_plan p, size_t* bytes) {
+    if (radon_status s = radon_ista_work_bytes(p, bytes)) return s;
+    radon_desc d;
+    radon_plan_desc(p, &d);
+    *bytes += align256((size_t)d.Nq * d.Ntau * sizeof(float)) + align256((size_t)d.Nt * d.Nx * sizeof(float));
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_demultiple(radon_plan p, const float* f, double q0, double slope, int iters,
+                                         float c2, float mu, int accelerate, float* g, float* f_out, void* work,
+                                         size_t work_bytes, void* stream) {
+    if (!p) return (radon_status)set_error(RADON_ERR_INVALID_ARG, "plan is NULL");
+    if (!f || !g || !f_out || !work) return (radon_status)set_error(RADON_ERR_INVALID_ARG, "NULL data pointer");
+    size_t need = 0, ista_b = 0;
+    radon_demultiple_work_bytes(p, &need);
+    radon_ista_work_bytes(p, &ista_b);
+    if (work_bytes < need || ((uintptr_t)work & 255))
+        return (radon_status)set_error(RADON_ERR_INVALID_ARG, "work area too small or not 256-byte aligned");
+    radon_desc d;
+    radon_plan_desc(p, &d);
+    const long nd = (long)d.Nt * d.Nx, ni = (long)d.Nq * d.Ntau;
+    float* gm = (float*)((char*)work + ista_b);                                   // multiples' image
+    float* fm = (float*)((char*)gm + align256((size_t)ni * sizeof(float)));       // multiples' gather
+    if (radon_status st = radon_ista(p, f, nullptr, g, iters, c2, mu, accelerate, work, ista_b, stream)) return st;
+    if (radon_status st = radon_mute(p, g, gm, q0, slope, RADON_KEEP_ABOVE, stream)) return st;
+    if (radon_status st = radon_adj(p, gm, fm, stream)) return st;
+    k_subtract<<<grid_for(nd), kThreads, 0, (cudaStream_t)stream>>>(f, fm, f_out, nd);
+    if (int e = last_cuda()) return cuda_fail(e, "subtraction of the multiples");
     return RADON_OK;
 }

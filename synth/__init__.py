@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "Geometry", "ricker", "rng_for", "hyperbolic_gather", "gaussian_gather",
     "random_radon_image", "single_gather", "sweep_gather", "large_gather", "missing_trace_gather",
-    "batch_gather",
+    "batch_gather", "primaries_multiples",
     "band_limited_gather", "batch_geometries",
 ]
 
@@ -197,6 +197,20 @@ def missing_trace_gather(tag: int = 3, Nt: int = 1024, Nx: int = 256, n_events: 
     mask = np.ones(Nx)
     mask[rng.choice(Nx, int(round(missing * Nx)), replace=False)] = 0.0
     return geo, f, mask
+
+
+def primaries_multiples(geo: Geometry, tag: int = 6, n_events: int = 8) -> tuple[np.ndarray, np.ndarray]:
+    """Gather of n_events primaries (q0 ~ U[0.25, 0.40] s/km) and as many
+    slower multiples (q0 ~ U[0.50, 0.65] s/km), tau0 ~ U[0.1, 0.8 T],
+    10-20 Hz Ricker wavelets, A ~ N(0, 1): the two separate by moveout in
+    the Radon domain along q = 0.45 s/km. Returns (gather, primaries only)."""
+    rng = rng_for(6000 + tag)
+    T = (geo.Nt - 1) * geo.dt
+    prim = hyperbolic_gather(geo, rng.uniform(0.1, 0.8 * T, n_events), rng.uniform(0.25, 0.40, n_events),
+                             rng.uniform(10.0, 20.0, n_events), rng.standard_normal(n_events))
+    mult = hyperbolic_gather(geo, rng.uniform(0.1, 0.8 * T, n_events), rng.uniform(0.50, 0.65, n_events),
+                             rng.uniform(10.0, 20.0, n_events), rng.standard_normal(n_events))
+    return prim + mult, prim
 
 
 def batch_gather(geo: Geometry, tag: int) -> np.ndarray:

@@ -8,7 +8,9 @@
 * the power iteration against the largest singular value from an SVD;
 * on the oracle's log-polar operator: the objective never increases along the
   paper's iteration, and torch's gradient check of the operator (forward with
-  the adjoint as its backward, FP64, a 128 x 32 gather).
+  the adjoint as its backward, FP64, a 128 x 32 gather);
+* the Radon-domain mute on hand values and the limits of the multiple
+  attenuation (border above or below every slowness).
 """
 import numpy as np
 import pytest
@@ -128,3 +130,25 @@ def test_fp64_gradient_check_of_the_operator(small_logpolar):
 
     f = torch.from_numpy(np.random.default_rng(9).standard_normal((geo.Nx, geo.Nt))).requires_grad_(True)
     assert torch.autograd.gradcheck(Op.apply, (f,), eps=1e-6, atol=1e-7, rtol=1e-6, fast_mode=True)
+
+
+def test_mute_hand_values():
+    tau = np.array([0.0, 1.0, 2.0])
+    q = np.array([0.1, 0.3, 0.5])
+    g = np.arange(9, dtype=float).reshape(3, 3) + 1.0
+    # line q = 0.2 + 0.1 tau: q=0.1 below everywhere, q=0.3 above at tau 0 only, q=0.5 above everywhere
+    np.testing.assert_array_equal(solvers.mute(g, tau, q, 0.2, 0.1, "below"), [[1, 2, 3], [0, 5, 6], [0, 0, 0]])
+    np.testing.assert_array_equal(solvers.mute(g, tau, q, 0.2, 0.1, "above"), [[0, 0, 0], [4, 0, 0], [7, 8, 9]])
+
+
+def test_demultiple_limits(small_logpolar):
+    """A border above every slowness leaves the gather untouched; a border
+    below every slowness subtracts the whole sparse model (f - R* g)."""
+    geo, lp = small_logpolar
+    f = synth.band_limited_gather(geo, 33, n_events=4, nu=8.0)
+    lam = solvers.power_norm2(lp.forward, lp.adjoint, np.ones((geo.Nq, geo.Ntau)), 30)
+    c2, mu = 0.9 / lam, 0.05 * np.abs(lp.forward(f)).max()
+    fo, g = solvers.demultiple(lp.forward, lp.adjoint, f, geo.tau(), geo.q(), 10.0, 0.0, 5, c2, mu)
+    np.testing.assert_array_equal(fo, f)
+    fo, g = solvers.demultiple(lp.forward, lp.adjoint, f, geo.tau(), geo.q(), -10.0, 0.0, 5, c2, mu)
+    np.testing.assert_allclose(fo, f - lp.adjoint(g), rtol=0, atol=1e-12)
