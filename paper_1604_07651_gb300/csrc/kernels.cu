@@ -358,9 +358,31 @@ __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int Pr = P.Prho, Nr = P.Nrho;
-    for (int idx = threadIdx.x; idx < nrows * Pr; idx += blockDim.x) {
-        const int m = idx / Pr, n = idx - m * Pr;
-        smem_f[m * Pr + swr(n)] = n < Nr ? P.lat[(size_t)(mb + m) * Nr + n] : 0.f;
+    // zero padding of every row, then the band's rows (contiguous in P.lat)
+    // with every load of a chunk issued before the first is stored
+    const int pad = Pr - Nr;
+    for (int idx = threadIdx.x; idx < nrows * pad; idx += blockDim.x) {
+        const int m = idx / pad;
+        smem_f[m * Pr + swr(Nr + idx - m * pad)] = 0.f;
+    }
+    const float* __restrict__ src = P.lat + (size_t)mb * Nr;
+    const int tot = nrows * Nr;
+    constexpr int L = 8;
+    for (int i0 = 0; i0 < tot; i0 += L * (int)blockDim.x) {
+        float v[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const int idx = i0 + q * (int)blockDim.x + threadIdx.x;
+            v[q] = idx < tot ? __ldg(src + idx) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const int idx = i0 + q * (int)blockDim.x + threadIdx.x;
+            if (idx < tot) {
+                const int m = idx / Nr;
+                smem_f[m * Pr + swr(idx - m * Nr)] = v[q];
+            }
+        }
     }
     __syncthreads();
     rows_r2c_write(P, mb, nrows);
@@ -496,6 +518,7 @@ __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Sr
 #pragma unroll
         for (int r = 0; r < kMaxBandRows; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (4 * n4 < hp) {
+#pragma unroll 4
             for (int l = lr.x; l <= lr.y; ++l) {
                 const int lc = l - P.l_lo;
                 const int a0 = mb - __ldg(P.colm0 + lc);     // tap of the band's first row
@@ -545,12 +568,24 @@ __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src 
     cf* A = reinterpret_cast<cf*>(smem_f);
     const cf* src = in + (size_t)kb * Nth * CB;
     if (CB == 2) {
-        // one 16-byte load per lattice row: both columns of the block
-        for (int m = threadIdx.x; m < Pt; m += blockDim.x) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (m < Nth) v = __ldg(reinterpret_cast<const float4*>(src) + m);
-            A[sw(m)] = {v.x, v.y};
-            A[Pt + sw(m)] = {v.z, v.w};
+        // one 16-byte load per lattice row: both columns of the block; every
+        // load of a chunk is issued before the first is stored
+        constexpr int L = 8;
+        for (int m0 = 0; m0 < Pt; m0 += L * (int)blockDim.x) {
+            float4 v[L];
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                const int m = m0 + q * (int)blockDim.x + threadIdx.x;
+                v[q] = m < Nth ? __ldg(reinterpret_cast<const float4*>(src) + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < L; ++q) {
+                const int m = m0 + q * (int)blockDim.x + threadIdx.x;
+                if (m < Pt) {
+                    A[sw(m)] = {v[q].x, v[q].y};
+                    A[Pt + sw(m)] = {v[q].z, v[q].w};
+                }
+            }
         }
     } else {
         for (int idx = threadIdx.x; idx < Pt * CB; idx += blockDim.x) {
@@ -612,12 +647,30 @@ __global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ Src
         if (k >= nk) X[m * M + sw(k)] = cf{0.f, 0.f};
     }
     const int per_kb = nrows * P.CB;
-    for (int idx = threadIdx.x; idx < P.nkb * per_kb; idx += blockDim.x) {
-        const int kb = idx / per_kb;
-        const int rem = idx - kb * per_kb;
-        const int m = rem / P.CB, c = rem - m * P.CB;
-        const int k = kb * P.CB + c;
-        if (k < nk) X[m * M + sw(k)] = ldcf(spec + ((size_t)kb * P.Ntheta + mb) * P.CB + rem);
+    const int tot = P.nkb * per_kb;
+    constexpr int L = 8;   // loads in flight per thread
+    for (int i0 = 0; i0 < tot; i0 += L * (int)blockDim.x) {
+        cf v[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const int idx = i0 + q * (int)blockDim.x + threadIdx.x;
+            v[q] = cf{0.f, 0.f};
+            if (idx < tot) {
+                const int kb = idx / per_kb;
+                v[q] = ldcf(spec + ((size_t)kb * P.Ntheta + mb) * P.CB + (idx - kb * per_kb));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+            const int idx = i0 + q * (int)blockDim.x + threadIdx.x;
+            if (idx < tot) {
+                const int kb = idx / per_kb;
+                const int rem = idx - kb * per_kb;
+                const int m = rem / P.CB, c = rem - m * P.CB;
+                const int k = kb * P.CB + c;
+                if (k < nk) X[m * M + sw(k)] = v[q];
+            }
+        }
     }
     __syncthreads();
     const int half = M / 2;
