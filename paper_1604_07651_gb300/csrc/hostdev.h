@@ -250,45 +250,36 @@ HD_UNROLL
 // One Stockham autosort butterfly (Govindaraju et al., SC'08 formulation),
 // split in its two halves so that a caller can keep all loads of a stage
 // before all stores (in-place stages): stage of radix R with
-// Ns = product of the radices already applied, butterfly index j in
-// [0, n/R). tw[k] = exp(-2 pi i k / n), k < n (the forward twiddles; the
-// inverse, dir = +1, uses their conjugates).
-// Multiplies v[r] by w^r (conj(w)^r for dir = +1), r = 1..R-1, with
-// w = tw[t1] = exp(-2 pi i t1 / n). Radix 16, 12 and 8 read only w and w^4 from
-// the table and form w^(4a+b) = (w^4)^a w^b with at most three complex
-// products each (relative error a few ulp), as does radix 12; smaller
-// radices read every power.
-template <int R>
-HD void apply_twiddles(const cf* tw, int t1, int dir, cf v[R]) {
-    if (R == 16 || R == 12 || R == 8) {
-        const cf w1 = tw[t1], w4 = tw[4 * t1];
-        const cf w2 = cmul(w1, w1);
-        const cf w3 = cmul(w2, w1);
-        const cf wb[4] = {{1.f, 0.f}, w1, w2, w3};
-        cf wa = w4;                              // w^(4a), a >= 1
-        HD_UNROLL
-        for (int b = 1; b < 4; ++b) v[b] = dir < 0 ? cmul(v[b], wb[b]) : cmulc(v[b], wb[b]);
-        HD_UNROLL
-        for (int a = 1; a < R / 4; ++a) {
-            HD_UNROLL
-            for (int b = 0; b < 4; ++b) {
-                const cf w = b ? cmul(wa, wb[b]) : wa;
-                v[4 * a + b] = dir < 0 ? cmul(v[4 * a + b], w) : cmulc(v[4 * a + b], w);
-            }
-            wa = cmul(wa, w4);
+// Ns = product of the radices already applied (a power of two), butterfly
+// index j in [0, n/R). The twiddles of a stage depend only on Ns, R and
+// jm = j mod Ns: v[r] is multiplied by exp(-2 pi i r jm / (Ns R)) (its
+// conjugate for dir = +1), read from the stage's table T[(r - 1) Ns + jm]
+// (stage_twiddles); the first stage (Ns = 1) has none. The tables of
+// consecutive stages lie back to back, Ns (R - 1) entries each.
+HD int stage_table_len(int Ns, int R) { return Ns > 1 ? Ns * (R - 1) : 0; }
+
+// One stage's table, computed in FP64 and rounded once.
+inline void stage_twiddles(int Ns, int R, cf* T) {
+    if (Ns <= 1) return;
+    for (int r = 1; r < R; ++r)
+        for (int jm = 0; jm < Ns; ++jm) {
+            const double a = -2.0 * 3.14159265358979323846 * (double)((r * jm) % (Ns * R)) / (double)(Ns * R);
+            T[(r - 1) * Ns + jm] = {(float)cos(a), (float)sin(a)};
         }
-    } else {
-        HD_UNROLL
-        for (int r = 1; r < R; ++r) v[r] = dir < 0 ? cmul(v[r], tw[r * t1]) : cmulc(v[r], tw[r * t1]);
-    }
 }
 
 template <int R>
-HD void stockham_load(const cf* in, int n, int Ns, int j, const cf* tw, int dir, cf v[R]) {
+HD void stockham_load(const cf* in, int n, int Ns, int j, const cf* T, int dir, cf v[R]) {
     HD_UNROLL
     for (int r = 0; r < R; ++r) v[r] = in[sw(j + r * (n / R))];
-    if (Ns > 1)                                 // the first stage's twiddles are all 1
-        apply_twiddles<R>(tw, (j & (Ns - 1)) * (n / (Ns * R)), dir, v);   // Ns is a power of two
+    if (Ns > 1) {
+        const int jm = j & (Ns - 1);
+        HD_UNROLL
+        for (int r = 1; r < R; ++r) {
+            const cf w = T[(r - 1) * Ns + jm];
+            v[r] = dir < 0 ? cmul(v[r], w) : cmulc(v[r], w);
+        }
+    }
 }
 
 template <int R>
@@ -301,9 +292,9 @@ HD_UNROLL
 }
 
 template <int R>
-HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int lgNs, int j, const cf* tw, int dir) {
+HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int lgNs, int j, const cf* T, int dir) {
     cf v[R];
-    stockham_load<R>(in, n, Ns, j, tw, dir, v);
+    stockham_load<R>(in, n, Ns, j, T, dir, v);
     stockham_store<R>(out, Ns, lgNs, j, dir, v);
 }
 
@@ -336,6 +327,20 @@ HD int fft_radices(int n, int rad[32]) {
         rad[k++] = n;   // 2, 3, 4, 5, 6, 8, 10 or 12
     }
     return k;
+}
+
+// Every stage's twiddle table of an FFT of length n, back to back in stage
+// order; returns the number of entries (T may be null to query it).
+inline int fft_stage_tables(int n, cf* T) {
+    int rad[32];
+    const int nst = fft_radices(n, rad);
+    int len = 0, Ns = 1;
+    for (int s = 0; s < nst; ++s) {
+        if (T) stage_twiddles(Ns, rad[s], T + len);
+        len += stage_table_len(Ns, rad[s]);
+        Ns *= rad[s];
+    }
+    return len;
 }
 
 // Butterflies of one radix a thread of the block FFT holds at once (the

@@ -62,9 +62,9 @@ struct PieceDev {
     const int* colm0;       // [ncol] first theta tap of each column
     const float* colscale;  // [ncol] output scale 2 X cos(psi) / a
     const cf* K;            // [nkb][k1max+1][CB] kernel spectrum (normalised)
-    const cf* twM;          // [Prho/2]  exp(-2 pi i k / (Prho/2))
+    const cf* twM;          // stage twiddle tables of the row FFT (length Prho/2)
     const cf* twP;          // [Prho/2+1] exp(-2 pi i k / Prho)
-    const cf* twT;          // [Ptheta]  exp(-2 pi i k / Ptheta)
+    const cf* twT;          // stage twiddle tables of the column FFT (length Ptheta)
     FftPlan fftM;           // row FFT (length Prho/2)
     FftPlan fftT;           // column FFT (length Ptheta)
     float* lat;             // [Ntheta][Nrho] real lattice (Q forward, G' adjoint)

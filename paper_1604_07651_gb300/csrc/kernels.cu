@@ -100,30 +100,34 @@ __device__ __forceinline__ void fft_stage_q(cf* buf, int n, int nrows, int Ns, i
 template <int DIR>
 __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* __restrict__ tw,
                                           const FftPlan& fp) {
+    // tw: the stage twiddle tables of length n back to back (fft_stage_tables)
     int Ns = 1, lg = 0;
     int s = 0;
+    const cf* T = tw;
     for (; s < fp.nst && fp.rad[s] == 16; ++s) {
-        fft_stage<16, 1, DIR>(buf, n, nrows, Ns, lg, tw);
+        fft_stage<16, 1, DIR>(buf, n, nrows, Ns, lg, T);
+        T += stage_table_len(Ns, 16);
         Ns <<= 4;
         lg += 4;
     }
     if (s < fp.nst) {
         const int R = fp.rad[s];
-        if (R == 12) fft_stage_q<12, 1, DIR>(buf, n, nrows, Ns, lg, tw);
-        else if (R == 10) fft_stage_q<10, 1, DIR>(buf, n, nrows, Ns, lg, tw);
-        else if (R == 8) fft_stage_q<8, 1, DIR>(buf, n, nrows, Ns, lg, tw);
-        else if (R == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, tw);
-        else if (R == 5) fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, tw);
-        else if (R == 4) fft_stage_q<4, 3, DIR>(buf, n, nrows, Ns, lg, tw);
-        else if (R == 3) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, tw);
-        else fft_stage_q<2, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        if (R == 12) fft_stage_q<12, 1, DIR>(buf, n, nrows, Ns, lg, T);
+        else if (R == 10) fft_stage_q<10, 1, DIR>(buf, n, nrows, Ns, lg, T);
+        else if (R == 8) fft_stage_q<8, 1, DIR>(buf, n, nrows, Ns, lg, T);
+        else if (R == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, T);
+        else if (R == 5) fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, T);
+        else if (R == 4) fft_stage_q<4, 3, DIR>(buf, n, nrows, Ns, lg, T);
+        else if (R == 3) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, T);
+        else fft_stage_q<2, 2, DIR>(buf, n, nrows, Ns, lg, T);
+        T += stage_table_len(Ns, R);
         Ns *= R;
         lg = 31 - __clz(Ns);
         ++s;
     }
     if (s < fp.nst) {   // after radix 4 or 8 (n / 16^k = 24, 20, 40): radix 6 or 5
-        if (fp.rad[s] == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, tw);
-        else fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, tw);
+        if (fp.rad[s] == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, T);
+        else fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, T);
     }
 }
 

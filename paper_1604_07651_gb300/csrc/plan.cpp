@@ -681,13 +681,11 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     }
     // twiddles
     const int M = h.Prho / 2;
-    std::vector<cf> twM(M), twP(M + 1), twT(h.Ptheta);
-    for (int k = 0; k < M; ++k)
-        twM[k] = {(float)std::cos(-2 * kPi * k / M), (float)std::sin(-2 * kPi * k / M)};
+    std::vector<cf> twM(fft_stage_tables(M, nullptr) + 1), twP(M + 1), twT(fft_stage_tables(h.Ptheta, nullptr) + 1);
+    fft_stage_tables(M, twM.data());
+    fft_stage_tables(h.Ptheta, twT.data());
     for (int k = 0; k <= M; ++k)
         twP[k] = {(float)std::cos(-2 * kPi * k / h.Prho), (float)std::sin(-2 * kPi * k / h.Prho)};
-    for (int k = 0; k < h.Ptheta; ++k)
-        twT[k] = {(float)std::cos(-2 * kPi * k / h.Ptheta), (float)std::sin(-2 * kPi * k / h.Ptheta)};
     std::vector<cf> K;
     if (radon_status s = kernel_spectrum(p, h, CB, P.nkb, K)) return s;
 

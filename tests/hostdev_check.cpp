@@ -36,20 +36,23 @@ static std::vector<cf> fft_emul_sw(std::vector<cf> a, int dir) {
     const int n = (int)a.size();
     int rad[32];
     const int nst = fft_radices(n, rad);
-    std::vector<cf> b(n), tw = twiddles(n);
-    int Ns = 1, lg = 0;
+    std::vector<cf> b(n), T(fft_stage_tables(n, nullptr) + 1);
+    fft_stage_tables(n, T.data());
+    int Ns = 1, lg = 0, ofs = 0;
     for (int s = 0; s < nst; ++s) {
         const int R = rad[s];
+        const cf* tw = T.data() + ofs;
+        ofs += stage_table_len(Ns, R);
         for (int j = 0; j < n / R; ++j) {
-            if (R == 16) stockham_butterfly<16>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
-            else if (R == 12) stockham_butterfly<12>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
-            else if (R == 6) stockham_butterfly<6>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
-            else if (R == 10) stockham_butterfly<10>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
-            else if (R == 5) stockham_butterfly<5>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
-            else if (R == 8) stockham_butterfly<8>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
-            else if (R == 4) stockham_butterfly<4>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
-            else if (R == 2) stockham_butterfly<2>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
-            else stockham_butterfly<3>(a.data(), b.data(), n, Ns, lg, j, tw.data(), dir);
+            if (R == 16) stockham_butterfly<16>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else if (R == 12) stockham_butterfly<12>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else if (R == 6) stockham_butterfly<6>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else if (R == 10) stockham_butterfly<10>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else if (R == 5) stockham_butterfly<5>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else if (R == 8) stockham_butterfly<8>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else if (R == 4) stockham_butterfly<4>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else if (R == 2) stockham_butterfly<2>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else stockham_butterfly<3>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
         }
         std::swap(a, b);
         Ns *= R;
