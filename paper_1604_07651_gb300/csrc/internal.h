@@ -120,14 +120,19 @@ int launch_band_rows_dev(const DevBatch& S, int nblocks, size_t smem, void* stre
 int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream);
 int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
 // Output interpolation: one CTA per output column; cmap[b] = (first piece,
-// number of time pieces, column l, 0) in `pieces` (device). Shared memory
+// number of time pieces, column l, 0) in `pieces` (device), or, when
+// np_all > 0 (one gather, one slowness piece of np_all time pieces, ntau_all
+// outputs per column), column b of pieces[0..np_all). Shared memory
 // (nrho_max + ntau_max) floats.
 int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int ntau_max,
-                          float* g, void* stream);
+                          int ntau_all, int np_all, float* g, void* stream);
 // Adjoint gather: one CTA per kSampleBlock samples of one gather;
-// smap[b] = (first piece, number of pieces, first sample, 0).
+// smap[b] = (first piece, number of pieces, first sample, 0), or, when
+// np_all > 0 (one gather of Nt_all x Nx_all samples in np_all pieces),
+// samples [b kSampleBlock, (b + 1) kSampleBlock).
 constexpr int kSampleBlock = 256;
-int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, void* stream);
+int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, int np_all, int Nt_all,
+                          int Nx_all, void* stream);
 size_t rows_smem_bytes(const PieceDev& P);
 size_t profile_smem_bytes(const PieceDev& P);
 int launch_sample_table(const TableArgs& A, const double* cj, const double* wk, const int* jfirst,

@@ -651,30 +651,12 @@ __global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ Src
         if (k >= nk) X[m * M + sw(k)] = cf{0.f, 0.f};
     }
     const int per_kb = nrows * P.CB;
-    const int tot = P.nkb * per_kb;
-    constexpr int L = 8;   // loads in flight per thread
-    for (int i0 = 0; i0 < tot; i0 += L * (int)blockDim.x) {
-        cf v[L];
-#pragma unroll
-        for (int q = 0; q < L; ++q) {
-            const int idx = i0 + q * (int)blockDim.x + threadIdx.x;
-            v[q] = cf{0.f, 0.f};
-            if (idx < tot) {
-                const int kb = idx / per_kb;
-                v[q] = ldcf(spec + ((size_t)kb * P.Ntheta + mb) * P.CB + (idx - kb * per_kb));
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < L; ++q) {
-            const int idx = i0 + q * (int)blockDim.x + threadIdx.x;
-            if (idx < tot) {
-                const int kb = idx / per_kb;
-                const int rem = idx - kb * per_kb;
-                const int m = rem / P.CB, c = rem - m * P.CB;
-                const int k = kb * P.CB + c;
-                if (k < nk) X[m * M + sw(k)] = v[q];
-            }
-        }
+    for (int idx = threadIdx.x; idx < P.nkb * per_kb; idx += blockDim.x) {
+        const int kb = idx / per_kb;
+        const int rem = idx - kb * per_kb;
+        const int m = rem / P.CB, c = rem - m * P.CB;
+        const int k = kb * P.CB + c;
+        if (k < nk) X[m * M + sw(k)] = ldcf(spec + ((size_t)kb * P.Ntheta + mb) * P.CB + rem);
     }
     __syncthreads();
     const int half = M / 2;
@@ -724,10 +706,12 @@ __device__ __forceinline__ float taps16(const float* __restrict__ lat, int Nr, i
 // a fixed order (shared memory: [nrho_max] profile, [ntau_max] sums).
 __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restrict__ pieces,
                                                         const int4* __restrict__ cmap, int nrho_max,
-                                                        float* __restrict__ g) {
-    const int4 c = __ldg(cmap + blockIdx.x);
+                                                        int ntau_all, int np_all, float* __restrict__ g) {
+    // np_all > 0: one gather with one slowness piece of np_all time pieces and
+    // ntau_all outputs per column, column = block (no map load before the work)
+    const int4 c = np_all > 0 ? make_int4(0, np_all, (int)blockIdx.x, 0) : __ldg(cmap + blockIdx.x);
     const int l = c.z, np = c.y;
-    const int Ntau = pieces[c.x].Ntau;
+    const int Ntau = np_all > 0 ? ntau_all : pieces[c.x].Ntau;
     float* prof = smem_f;
     float* acc = smem_f + nrho_max;
     for (int i = threadIdx.x; i < Ntau; i += blockDim.x) acc[i] = 0.f;
@@ -755,7 +739,7 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
             acc[i] += sc * (wr[0] * r[0] + wr[1] * r[1] + wr[2] * r[2] + wr[3] * r[3]);
         }
     }
-    float* gl = g + pieces[c.x].g_off + (size_t)l * Ntau;
+    float* gl = g + (np_all > 0 ? 0 : pieces[c.x].g_off) + (size_t)l * Ntau;
     for (int i = threadIdx.x; i < Ntau; i += blockDim.x) gl[i] = acc[i];
 }
 
@@ -763,14 +747,17 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
 // the 4x4 taps of each sub-problem that holds it. One CTA per kSampleBlock
 // samples of one gather: smap[b] = (first piece, number of pieces, first
 // sample of the block within the gather).
-__global__ void __launch_bounds__(kSampleBlock) k_gather_samples(const PieceDev* __restrict__ pieces,
-                                                                 const int4* __restrict__ smap,
-                                                                 float* __restrict__ f) {
-    const int4 m = __ldg(smap + blockIdx.x);
-    const PieceDev& P0 = pieces[m.x];
-    const int Nt = P0.Nt;
+__global__ void __launch_bounds__(kSampleBlock, 8) k_gather_samples(const PieceDev* __restrict__ pieces,
+                                                                    const int4* __restrict__ smap,
+                                                                    float* __restrict__ f, int np_all, int Nt_all,
+                                                                    int Nx_all) {
+    // np_all > 0: one gather of Nt_all x Nx_all samples in np_all pieces,
+    // samples = blocks in order (no map load before the work)
+    const int4 m = np_all > 0 ? make_int4(0, np_all, (int)blockIdx.x * kSampleBlock, 0) : __ldg(smap + blockIdx.x);
+    const int Nt = np_all > 0 ? Nt_all : pieces[m.x].Nt;
+    const int Nx = np_all > 0 ? Nx_all : pieces[m.x].Nx;
     const long idx = (long)m.z + threadIdx.x;
-    if (idx >= (long)Nt * P0.Nx) return;
+    if (idx >= (long)Nt * Nx) return;
     const int k = (int)(idx / Nt);
     const int j = (int)(idx - (long)k * Nt);
     float acc = 0.f;
@@ -785,7 +772,7 @@ __global__ void __launch_bounds__(kSampleBlock) k_gather_samples(const PieceDev*
         b3_weights(__int_as_float(e.z), wr);
         acc += w * taps16(P.lat, P.Nrho, e.x >> 16, e.x & 0xffff, wt, wr);
     }
-    f[P0.f_off + idx] = acc;
+    f[(np_all > 0 ? 0 : pieces[m.x].f_off) + idx] = acc;
 }
 
 // --------------------------------------------------------------------------
@@ -1099,15 +1086,18 @@ int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
 }
 
 int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int ntau_max,
-                          float* g, void* stream) {
+                          int ntau_all, int np_all, float* g, void* stream) {
     const size_t sm = ((size_t)nrho_max + ntau_max) * sizeof(float);
     if (int e = set_smem((const void*)k_interp_columns, sm)) return e;
-    if (ncols > 0) k_interp_columns<<<ncols, 256, sm, (cudaStream_t)stream>>>(pieces, cmap, nrho_max, g);
+    if (ncols > 0)
+        k_interp_columns<<<ncols, 256, sm, (cudaStream_t)stream>>>(pieces, cmap, nrho_max, ntau_all, np_all, g);
     return check_launch();
 }
 
-int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, void* stream) {
-    if (nblocks > 0) k_gather_samples<<<nblocks, kSampleBlock, 0, (cudaStream_t)stream>>>(pieces, smap, f);
+int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, int np_all, int Nt_all,
+                          int Nx_all, void* stream) {
+    if (nblocks > 0)
+        k_gather_samples<<<nblocks, kSampleBlock, 0, (cudaStream_t)stream>>>(pieces, smap, f, np_all, Nt_all, Nx_all);
     return check_launch();
 }
 

@@ -859,8 +859,9 @@ extern "C" radon_status radon_plan_create(radon_plan* out, int Nt, int Nx, int N
     return radon_plan_create_ex(out, &d);
 }
 
-// Geometry, tables and kernel spectra of every piece of a plan, and the
-// column and sample maps of its two gathers; no work buffers.
+// Geometry, tables and kernel spectra of every piece of a plan; no work
+// buffers and no gather maps (a single plan and a batch lay those out
+// differently).
 static radon_status plan_core(const radon_desc* din, radon_plan_s** out) {
     *out = nullptr;
     if (radon_status s = check_desc(din)) return s;
@@ -904,16 +905,6 @@ static radon_status plan_core(const radon_desc* din, radon_plan_s** out) {
         }
         p->qcount.push_back((int)tps.size());
     }
-    std::vector<int4> cmap, smap;
-    column_map(p, 0, cmap);
-    sample_map(p, 0, 0, smap);
-    radon_status s = RADON_OK;
-    if ((s = dev_upload(p, cmap, &p->cmap)) || (s = dev_upload(p, smap, &p->smap))) {
-        destroy_plan(p);
-        return s;
-    }
-    p->ncols = (int)cmap.size();
-    p->nsblocks = (int)smap.size();
     for (auto& h : p->pieces) p->nrho_max = std::max(p->nrho_max, h.dev.Nrho);
     *out = p;
     return RADON_OK;
@@ -954,6 +945,16 @@ extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* 
     const PieceDev* dp = nullptr;
     if ((s = dev_upload(p, devs, &dp))) { destroy_plan(p); return s; }
     p->dev_pieces = const_cast<PieceDev*>(dp);
+    // column and sample maps of the two gathers
+    std::vector<int4> cmap, smap;
+    column_map(p, 0, cmap);
+    sample_map(p, 0, 0, smap);
+    if ((s = dev_upload(p, cmap, &p->cmap)) || (s = dev_upload(p, smap, &p->smap))) {
+        destroy_plan(p);
+        return s;
+    }
+    p->ncols = (int)cmap.size();
+    p->nsblocks = (int)smap.size();
     if (cudaDeviceSynchronize() != cudaSuccess) {
         destroy_plan(p);
         return fail(RADON_ERR_CUDA, "plan creation failed on the device");
@@ -1020,7 +1021,8 @@ static radon_status run_forward(radon_plan_s* p, const PieceDev* P, const PieceD
     const double gb = 4.0 * p->d.Ntau * p->d.Nq;
     if (radon_status s = cuda_status(
             timed(p, 4, b_lat + gb, stream,
-                  [&] { return launch_interp_columns(dP, p->cmap, p->ncols, p->nrho_max, p->d.Ntau, g, stream); }),
+                  [&] { return launch_interp_columns(dP, p->cmap, p->ncols, p->nrho_max, p->d.Ntau, p->d.Ntau,
+                                               p->qpieces.size() == 1 ? np : 0, g, stream); }),
             "interpolation"))
         return s;
     return RADON_OK;
@@ -1080,7 +1082,10 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
             "inverse row FFT"))
         return s;
     return cuda_status(timed(p, 8, b_lat + 4.0 * p->d.Nt * p->d.Nx, stream,
-                             [&] { return launch_gather_samples(p->dev_pieces, p->smap, p->nsblocks, f, stream); }),
+                             [&] {
+                                 return launch_gather_samples(p->dev_pieces, p->smap, p->nsblocks, f, np, p->d.Nt,
+                                                              p->d.Nx, stream);
+                             }),
                        "adjoint gridding");
 }
 
@@ -1390,7 +1395,7 @@ extern "C" radon_status radon_batch_fwd(radon_batch b, const void* f, int in_typ
         return s;
     if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
         return s;
-    return cuda_status(launch_interp_columns(b->pieces, b->cmap, b->ncols, b->nrho_max, b->ntau_max, g, stream),
+    return cuda_status(launch_interp_columns(b->pieces, b->cmap, b->ncols, b->nrho_max, b->ntau_max, 0, 0, g, stream),
                        "interpolation");
 }
 
@@ -1409,7 +1414,7 @@ extern "C" radon_status radon_batch_adj(radon_batch b, const float* g, float* f,
         return s;
     if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
         return s;
-    return cuda_status(launch_gather_samples(b->pieces, b->smap, b->nsblocks, f, stream), "adjoint gridding");
+    return cuda_status(launch_gather_samples(b->pieces, b->smap, b->nsblocks, f, 0, 0, 0, stream), "adjoint gridding");
 }
 
 // ---------------------------------------------------------------------------
