@@ -239,7 +239,7 @@ def batched_uneven(dev, n: int) -> dict:
     geos = synth.batch_geometries(n)
     t0 = time.time()
     batch = hr.Batch([dict(Nt=g.Nt, Nx=g.Nx, Ntau=g.Ntau, Nq=g.Nq, dt=g.dt, dx=g.dx, qmin=g.qmin,
-                           qmax=g.qmax) for g in geos])
+                           qmax=g.qmax, rows_per_band=0) for g in geos])   # tuned over the batch
     t_plan = time.time() - t0
     f = batch.pack([torch.tensor(synth.batch_gather(g, i), dtype=torch.float32) for i, g in enumerate(geos)],
                    dtype=torch.bfloat16)
@@ -273,7 +273,7 @@ def batched_uneven(dev, n: int) -> dict:
     return {"workload": f"{n} uneven gathers, Nt 500-3000 (4 ms), Nx 60-480 (25 m), Nq = Nx, 10-40 events, "
                         f"BF16 input, {samples / 1e6:.1f} M samples",
             "gathers_per_s": n / (ms / 1e3), "ms_per_batch_fwd_adj": ms, "launches_per_batch": 10,
-            "plan_s": t_plan, "graph": True}
+            "plan_s": t_plan, "graph": True, "rows_per_band": "tuned over the batch at creation"}
 
 
 def measured_traffic(kernel: str):
@@ -391,7 +391,8 @@ def main():
     import paper_1604_07651_gb300 as hr
     geo, f_np = make_workload(rank)
     dev = torch.device("cuda", local)
-    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, device=local)
+    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, rows_per_band=0,
+                   device=local)   # rows per band timed at plan creation
     f = torch.tensor(f_np, dtype=torch.float32, device=dev)
     g = torch.empty((geo.Nq, geo.Ntau), dtype=torch.float32, device=dev)
     fa = torch.empty_like(f)
@@ -452,7 +453,7 @@ def main():
         "config": {"workload": WORKLOAD, "l2": "flushed before each step (256 MiB write)",
                    "method": {"sigma": plan.desc.sigma, "omega_c": plan.desc.omega_c,
                               "tsplit": [plan.desc.tsplit[i] for i in range(plan.desc.n_tsplit)],
-                              "n_qsplit": plan.desc.n_qsplit},
+                              "n_qsplit": plan.desc.n_qsplit, "rows_per_band": plan.desc.rows_per_band},
                    "lattices": [(p["Ntheta"], p["Nrho"], p["Ptheta"], p["Prho"]) for p in plan.pieces()]},
         "roofline": roofline(dom, d, per_kernel, hbm, peak_kind, plan, clk.summary(), dev, args.steps),
         "stages": stages,

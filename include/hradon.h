@@ -67,6 +67,11 @@ typedef struct radon_plan_s* radon_plan;
  *   n_qsplit: number of slowness pieces (Section 5), >= 1; each gets its
  *             own log-polar setup.
  *   device  : CUDA device ordinal, or -1 for the calling thread's current device.
+ *   rows_per_band: lattice rows one CTA of the row-FFT kernels holds, 1..4,
+ *             or 0 to have radon_plan_create_ex (and radon_batch_create, when
+ *             every descriptor asks for it) time each feasible value on the
+ *             device and keep the fastest; radon_plan_desc reports the choice.
+ *             It changes the work split only, not the results.
  */
 typedef struct {
     int Nt, Nx, Ntau, Nq;
@@ -78,6 +83,7 @@ typedef struct {
     double tsplit[RADON_MAX_TSPLIT];
     int n_qsplit;
     int device;
+    int rows_per_band;
 } radon_desc;
 
 /* Geometry of one sub-problem of a plan (for tests and diagnostics). */
@@ -98,7 +104,8 @@ typedef struct {
 /*
  * Fill *d with the default method parameters for the given problem:
  * tau0 = 0, dtau = (Nt-1) dt/(Ntau-1), sigma = 1.25, omega_c = 0.35,
- * time splits at 0.25 T and 0.5 T, one slowness piece, current device.
+ * time splits at 0.25 T and 0.5 T, one slowness piece, current device,
+ * 3 rows per band.
  * Returns RADON_ERR_INVALID_ARG for a NULL d.
  */
 radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau, int Nq, double dt,

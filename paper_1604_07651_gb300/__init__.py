@@ -45,14 +45,16 @@ class Plan:
     ``dt``, ``dx``; image ``Ntau`` x ``Nq`` with ``tau_i = tau0 + i*dtau``
     (``dtau=0``: ``(Nt-1) dt/(Ntau-1)``) and ``q`` evenly on
     ``[qmin, qmax]``; method parameters ``sigma``, ``omega_c``, ``tsplit``
-    (split points of Eq. (19) as fractions of T), ``n_qsplit``.
+    (split points of Eq. (19) as fractions of T), ``n_qsplit``;
+    ``rows_per_band`` (1..4, or 0 to time them at plan creation; the plan's
+    ``desc.rows_per_band`` reports the value in use).
     """
 
     def __init__(self, Nt: int, Nx: int, Ntau: int, Nq: int, dt: float, dx: float,
                  qmin: float = 0.0, qmax: float = 1.0, *, tau0: float = 0.0, dtau: float = 0.0,
                  sigma: float | None = None, omega_c: float | None = None,
                  tsplit: Sequence[float] | None = None, n_qsplit: int = 1,
-                 device: int | torch.device | None = None):
+                 rows_per_band: int | None = None, device: int | torch.device | None = None):
         lib = _lib.load()
         d = RadonDesc()
         _lib.check(lib.radon_desc_init(ctypes.byref(d), Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax))
@@ -68,6 +70,8 @@ class Plan:
             d.n_tsplit = len(ts)
             for i, v in enumerate(ts):
                 d.tsplit[i] = v
+        if rows_per_band is not None:
+            d.rows_per_band = rows_per_band
         if device is None:
             dev = torch.cuda.current_device()
         else:
@@ -234,7 +238,7 @@ class Plan:
 
 
 def _desc(Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax, tau0=0.0, dtau=0.0, sigma=None, omega_c=None,
-          tsplit=None, n_qsplit=1, device=0) -> RadonDesc:
+          tsplit=None, n_qsplit=1, rows_per_band=None, device=0) -> RadonDesc:
     d = RadonDesc()
     _lib.check(_lib.load().radon_desc_init(ctypes.byref(d), Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax))
     d.tau0, d.dtau, d.n_qsplit, d.device = tau0, dtau, n_qsplit, device
@@ -249,6 +253,8 @@ def _desc(Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax, tau0=0.0, dtau=0.0, sigma=None, 
         d.n_tsplit = len(ts)
         for i, v in enumerate(ts):
             d.tsplit[i] = v
+    if rows_per_band is not None:
+        d.rows_per_band = rows_per_band
     return d
 
 
@@ -259,7 +265,8 @@ class Batch:
     ``geometries``: a list of dicts with the ``Plan`` arguments (``Nt``,
     ``Nx``, ``Ntau``, ``Nq``, ``dt``, ``dx``, ``qmin``, ``qmax`` and
     optionally ``tau0``, ``dtau``, ``sigma``, ``omega_c``, ``tsplit``,
-    ``n_qsplit``). Data are packed back to back (``f_offsets``,
+    ``n_qsplit``, ``rows_per_band``; 0 in every geometry times the feasible
+    values over the whole batch). Data are packed back to back (``f_offsets``,
     ``g_offsets``): gather i is ``f[f_offsets[i]:f_offsets[i+1]]`` viewed as
     [Nx][Nt]; ``forward`` accepts float32 or bfloat16 gathers."""
 

@@ -75,7 +75,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with ThreadPoolExecutor(len(cmds)) as ex:
         list(ex.map(run, cmds))
     tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-L", os.path.join(cuda, "lib64"), "-lcudart"])
+    run([nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-L", os.path.join(cuda, "lib64"), "-lcudart", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -157,6 +157,15 @@ __device__ __forceinline__ const PieceDev& piece_of(const DevBatch& B, int& bx) 
     return B.p[m.x];
 }
 
+// Dynamic shared memory of the launch: the row and column kernels check it
+// against what their piece needs and leave the block untouched (never write
+// past it) if a launch gave too little.
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+    unsigned r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
 __device__ __forceinline__ float load_in(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float load_in(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 
@@ -359,6 +368,7 @@ template <class Src>
 __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src B) {
     int bx;
     const PieceDev& P = piece_of(B, bx);
+    if ((size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int Pr = P.Prho, Nr = P.Nrho;
@@ -453,6 +463,7 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
     __shared__ float red[8];
     int lc;
     const PieceDev& P = piece_of(B, lc);
+    if ((size_t)P.Nrho * sizeof(int) > dyn_smem_bytes()) return;
     const int hp = P.hpitch;
     const float* gl = g + P.g_off + (size_t)(P.l_lo + lc) * P.Ntau;
     const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * P.Ntau);
@@ -511,6 +522,7 @@ template <class Src>
 __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Src B) {
     int band;
     const PieceDev& P = piece_of(B, band);
+    if ((size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
     const float* __restrict__ h = P.prof;
     const int hp = P.hpitch;
     const int mb = band * P.R;
@@ -566,6 +578,7 @@ template <class Src>
 __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src B, int adjoint) {
     int kb;
     const PieceDev& P = piece_of(B, kb);
+    if ((size_t)P.CB * P.Ptheta * sizeof(cf) > dyn_smem_bytes()) return;
     const cf* in = P.spec;   // in place: the CTA owns its column block
     cf* out = P.spec;
     const int CB = P.CB, Pt = P.Ptheta, Nth = P.Ntheta;
@@ -638,6 +651,7 @@ template <class Src>
 __global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ Src B) {
     int bx;
     const PieceDev& P = piece_of(B, bx);
+    if ((size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
     const cf* __restrict__ spec = P.spec;
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
@@ -712,6 +726,7 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
     const int4 c = np_all > 0 ? make_int4(0, np_all, (int)blockIdx.x, 0) : __ldg(cmap + blockIdx.x);
     const int l = c.z, np = c.y;
     const int Ntau = np_all > 0 ? ntau_all : pieces[c.x].Ntau;
+    if ((size_t)(nrho_max + Ntau) * sizeof(float) > dyn_smem_bytes()) return;
     float* prof = smem_f;
     float* acc = smem_f + nrho_max;
     for (int i = threadIdx.x; i < Ntau; i += blockDim.x) acc[i] = 0.f;

@@ -7,12 +7,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hradon.h"
@@ -185,8 +188,17 @@ struct HostPiece {
     int n_theta = 0, n_rho = 0, Ntheta = 0, Nrho = 0, Ptheta = 0, Prho = 0, k1max = 0, k2max = 0;
     double dtheta = 0, drho = 0, theta0 = 0, rho0 = 0, theta_m = 0;
     std::vector<int> jfirst;
+    int Rmax = 1;                                  // most rows per band shared memory allows
+    const int2* lband_R[kMaxBandRows + 1] = {};    // band column ranges for each rows-per-band
     PieceDev dev{};
 };
+
+// Rows per band of a piece: the band count and column ranges follow.
+static void set_rows(HostPiece& h, int R) {
+    h.dev.R = R;
+    h.dev.nbands = (h.Ntheta + R - 1) / R;
+    h.dev.lband = h.lband_R[R];
+}
 
 struct radon_plan_s {
     radon_desc d{};
@@ -280,6 +292,8 @@ radon_status check_desc(const radon_desc* d) {
         return fail(RADON_ERR_INVALID_ARG, "n_tsplit out of range");
     if (d->n_qsplit < 1 || d->n_qsplit > 64)
         return fail(RADON_ERR_INVALID_ARG, "need 1 <= n_qsplit <= 64");
+    if (d->rows_per_band < 0 || d->rows_per_band > kMaxBandRows)
+        return fail(RADON_ERR_INVALID_ARG, "need 0 <= rows_per_band <= 4");
     return RADON_OK;
 }
 
@@ -601,18 +615,12 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
         return fail(RADON_ERR_UNSUPPORTED,
                     "FFT length " + std::to_string(std::max(h.Prho / 2, h.Ptheta)) +
                         " above the block FFT's limit (4096, 6144 = 3*2048 or 5120 = 5*1024)");
-    // rows per band: 3 (more rows mean fewer, longer CTAs and worse balance,
-    // fewer leave threads of the radix-16 stages idle)
-    int R = (int)std::min<size_t>(3, (size_t)smem_max / (h.Prho * sizeof(float)));   // <= kMaxBandRows
-    if (const char* env = std::getenv("HRADON_ROWS_PER_BAND")) {   // tuning knob
-        const int r = std::atoi(env);
-        if (r >= 1 && r <= kMaxBandRows && (size_t)r * h.Prho * sizeof(float) <= (size_t)smem_max) R = r;
-    }
-    if (R < 1) {
-        R = 1;
-        if ((size_t)h.Prho * sizeof(float) > (size_t)smem_max)
-            return fail(RADON_ERR_UNSUPPORTED, "row FFT length too large for shared memory");
-    }
+    // rows per band: any value up to what shared memory allows gives the same
+    // results; the descriptor's choice, else 3 until the plan times them
+    const int Rmax = (int)std::min<size_t>(kMaxBandRows, (size_t)smem_max / (h.Prho * sizeof(float)));
+    if (Rmax < 1) return fail(RADON_ERR_UNSUPPORTED, "row FFT length too large for shared memory");
+    h.Rmax = Rmax;
+    const int R = std::min(Rmax, d.rows_per_band > 0 ? d.rows_per_band : 3);
     int CB = 2;
     while (CB > 1 && (size_t)CB * h.Ptheta * sizeof(cf) > (size_t)smem_max) --CB;
     if ((size_t)CB * h.Ptheta * sizeof(cf) > (size_t)smem_max)
@@ -648,7 +656,6 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     std::vector<int> colm0(ncol);
     std::vector<float> colscale(ncol);
     std::vector<double> qb2(ncol);
-    std::vector<int2> lband(P.nbands, int2{1, 0});
     const double dtau = d.dtau > 0 ? d.dtau : T / (d.Ntau - 1);
     for (int lc = 0; lc < ncol; ++lc) {
         const double qb = q[h.l_lo + lc] * X / T;
@@ -664,21 +671,29 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
         colw[lc] = make_float4((float)b3(fr + 1.0), (float)b3(fr), (float)b3(fr - 1.0), (float)b3(fr - 2.0));
         colscale[lc] = (float)(2.0 * X * std::cos(psi) / h.a);
         qb2[lc] = m;
-        const int flc = m0 + 1;
-        int b0 = (int)std::ceil((double)(flc - R) / R);
-        int b1 = (int)std::floor((double)(flc + 2) / R);
-        b0 = std::max(b0, 0);
-        b1 = std::min(b1, P.nbands - 1);
-        for (int b = b0; b <= b1; ++b) {
-            int2& r = lband[b];
-            const int l = h.l_lo + lc;
-            if (r.x > r.y) r = int2{l, l};
-            else {
-                r.x = std::min(r.x, l);
-                r.y = std::max(r.y, l);
+    }
+    // candidate output columns of every band of rb rows: those whose four
+    // theta taps m0 .. m0+3 meet the band
+    for (int rb = 1; rb <= Rmax; ++rb) {
+        const int nbands = (h.Ntheta + rb - 1) / rb;
+        std::vector<int2> lband(nbands, int2{1, 0});
+        for (int lc = 0; lc < ncol; ++lc) {
+            const int m0 = colm0[lc];                        // >= 0
+            const int first = (m0 + rb) / rb - 1;             // ceil((m0 + 1) / rb) - 1
+            const int last = std::min(nbands - 1, (m0 + 3) / rb);
+            for (int b = first; b <= last; ++b) {
+                int2& r = lband[b];
+                const int l = h.l_lo + lc;
+                if (r.x > r.y) r = int2{l, l};
+                else {
+                    r.x = std::min(r.x, l);
+                    r.y = std::max(r.y, l);
+                }
             }
         }
+        if (radon_status s = dev_upload(p, lband, &h.lband_R[rb])) return s;
     }
+    set_rows(h, R);
     // twiddles
     const int M = h.Prho / 2;
     std::vector<cf> twM(fft_stage_tables(M, nullptr) + 1), twP(M + 1), twT(fft_stage_tables(h.Ptheta, nullptr) + 1);
@@ -690,8 +705,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     if (radon_status s = kernel_spectrum(p, h, CB, P.nkb, K)) return s;
 
     radon_status s = RADON_OK;
-    if ((s = dev_upload(p, lband, &P.lband)) ||
-        (s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
+    if ((s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
         (s = dev_upload(p, colscale, &P.colscale)) || (s = dev_upload(p, K, &P.K)) ||
         (s = dev_upload(p, twM, &P.twM)) || (s = dev_upload(p, twP, &P.twP)) ||
         (s = dev_upload(p, twT, &P.twT)))
@@ -849,6 +863,7 @@ extern "C" radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau,
     d->tsplit[1] = 0.5;
     d->n_qsplit = 1;
     d->device = -1;
+    d->rows_per_band = 3;
     return RADON_OK;
 }
 
@@ -910,6 +925,38 @@ static radon_status plan_core(const radon_desc* din, radon_plan_s** out) {
     return RADON_OK;
 }
 
+// Rows-per-band tuner: every feasible value is timed on the plan's own
+// (cleared) work buffers with the three row-FFT kernels, and the fastest
+// kept. The value changes the work split only, not the results.
+template <class Run>
+static int tune_rows(int rmax, Run&& run, void* stream) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int best = 0;
+    float best_ms = 0.f;
+    for (int R = 1; R <= rmax; ++R) {
+        if (run(R) != 0) break;                     // warm-up (shared-memory attributes, caches)
+        cudaEventRecord(a, (cudaStream_t)stream);
+        for (int rep = 0; rep < 3; ++rep)
+            if (run(R) != 0) break;
+        cudaEventRecord(b, (cudaStream_t)stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (best == 0 || ms < best_ms) {
+            best = R;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaGetLastError();
+    return best;
+}
+
 extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* din) {
     if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -932,6 +979,8 @@ extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* 
     }
     p->lat_all = (float*)lat;
     p->lat_bytes = lat_b;
+    void* const spec_base = spec;
+    void* const prof_base = prof;
     for (auto& h : p->pieces) {
         h.dev.lat = (float*)lat;
         h.dev.spec = (cf*)spec;
@@ -939,6 +988,34 @@ extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* 
         lat = (char*)lat + piece_lattice_bytes(h.dev);
         spec = (char*)spec + piece_spectrum_bytes(h.dev);
         prof = (char*)prof + piece_profile_bytes(h.dev);
+    }
+    if (p->d.rows_per_band == 0) {
+        int rmax = kMaxBandRows;
+        for (auto& h : p->pieces) rmax = std::min(rmax, h.Rmax);
+        cudaMemset(p->lat_all, 0, lat_b);
+        cudaMemset(spec_base, 0, spec_b);
+        cudaMemset(prof_base, 0, prof_b);
+        const int np = (int)p->pieces.size();
+        const int best = tune_rows(
+            rmax,
+            [&](int R) {
+                std::vector<PieceDev> P;
+                for (auto& h : p->pieces) {
+                    set_rows(h, R);
+                    P.push_back(h.dev);
+                }
+                for (int i = 0; i < np; i += kMaxBatch) {
+                    const int n = std::min(kMaxBatch, np - i);
+                    if (int e = launch_rows_r2c(P.data() + i, n, nullptr)) return e;
+                    if (int e = launch_band_rows(P.data() + i, n, nullptr)) return e;
+                    if (int e = launch_rows_c2r(P.data() + i, n, nullptr)) return e;
+                }
+                return 0;
+            },
+            nullptr);
+        const int R = best > 0 ? best : std::min(3, rmax);
+        for (auto& h : p->pieces) set_rows(h, R);
+        p->d.rows_per_band = R;
     }
     std::vector<PieceDev> devs;
     for (auto& h : p->pieces) devs.push_back(h.dev);
@@ -1249,7 +1326,8 @@ struct radon_batch_s {
 
 static void destroy_batch(radon_batch_s* b) {
     if (!b) return;
-    for (radon_plan_s* p : b->plans) destroy_plan(p);
+    for (radon_plan_s* p : b->plans)
+        if (p) destroy_plan(p);
     destroy_plan(b->store);
     delete b;
 }
@@ -1265,18 +1343,49 @@ extern "C" radon_status radon_batch_create(radon_batch* out, int n, const radon_
         delete b;
         return fail(RADON_ERR_OOM, "host allocation failed");
     }
+    // every gather on the first descriptor's device (the calling thread's
+    // current device when it names none)
+    b->device = descs[0].device;
+    if (b->device < 0 && cudaGetDevice(&b->device) != cudaSuccess) {
+        destroy_batch(b);
+        return fail(RADON_ERR_CUDA, "no CUDA device");
+    }
+    // the plans are independent: build them on several host threads (their
+    // host-side table work dominates), keeping the first failure
+    b->plans.assign(n, nullptr);
+    std::atomic<int> next{0};
+    std::mutex err_mutex;
+    radon_status first_err = RADON_OK;
+    std::string first_msg;
+    auto worker = [&]() {
+        for (int i = next++; i < n; i = next++) {
+            radon_desc d = descs[i];
+            d.device = b->device;
+            radon_plan_s* p = nullptr;
+            if (radon_status s = plan_core(&d, &p)) {
+                std::lock_guard<std::mutex> lock(err_mutex);
+                if (first_err == RADON_OK) {
+                    first_err = s;
+                    first_msg = "gather " + std::to_string(i) + ": " + g_err;
+                }
+                next = n;
+                return;
+            }
+            b->plans[i] = p;
+        }
+    };
+    const int nthreads = std::max(1, std::min<int>(n, std::min(16u, std::max(1u, std::thread::hardware_concurrency()))));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+    if (first_err != RADON_OK) {
+        destroy_batch(b);
+        return fail(first_err, first_msg);
+    }
     b->f_off.push_back(0);
     b->g_off.push_back(0);
-    for (int i = 0; i < n; ++i) {
-        radon_desc d = descs[i];
-        if (i > 0) d.device = b->device;
-        radon_plan_s* p = nullptr;
-        if (radon_status s = plan_core(&d, &p)) {
-            destroy_batch(b);
-            return s;
-        }
-        if (i == 0) b->device = p->device;
-        b->plans.push_back(p);
+    for (radon_plan_s* p : b->plans) {
         b->f_off.push_back(b->f_off.back() + (long long)p->d.Nt * p->d.Nx);
         b->g_off.push_back(b->g_off.back() + (long long)p->d.Ntau * p->d.Nq);
     }
@@ -1306,6 +1415,8 @@ extern "C" radon_status radon_batch_create(radon_batch* out, int n, const radon_
     }
     b->lat_all = (float*)lat;
     b->lat_bytes = lat_b;
+    void* const spec_base = spec;
+    void* const prof_base = prof;
     for (auto& P : host) {
         P.lat = (float*)lat;
         P.spec = (cf*)spec;
@@ -1348,6 +1459,56 @@ extern "C" radon_status radon_batch_create(radon_batch* out, int n, const radon_
     b->n_cols = (int)mc.size();
     b->ncols = (int)cmap.size();
     b->nsblocks = (int)smap.size();
+    // rows per band tuned over the whole batch when every descriptor asks
+    bool tune = true;
+    int rmax = kMaxBandRows;
+    for (int i = 0; i < n; ++i) tune = tune && descs[i].rows_per_band == 0;
+    for (radon_plan_s* p : b->plans)
+        for (auto& h : p->pieces) rmax = std::min(rmax, h.Rmax);
+    if (tune) {
+        cudaMemset(b->lat_all, 0, b->lat_bytes);
+        cudaMemset(spec_base, 0, spec_b);
+        cudaMemset(prof_base, 0, prof_b);
+        // descriptors and band map for R rows per band (new device copies)
+        auto apply = [&](int R) -> radon_status {
+            int gi = 0;
+            mb.clear();
+            b->smem_rows = 0;
+            for (radon_plan_s* p : b->plans)
+                for (auto& h : p->pieces) {
+                    set_rows(h, R);
+                    host[gi].R = h.dev.R;
+                    host[gi].nbands = h.dev.nbands;
+                    host[gi].lband = h.dev.lband;
+                    // the row kernels' shared memory grows with R
+                    b->smem_rows = std::max(b->smem_rows, rows_smem_bytes(host[gi]));
+                    for (int u = 0; u < host[gi].nbands; ++u) mb.push_back(int2{gi, u});
+                    ++gi;
+                }
+            radon_status st = RADON_OK;
+            if ((st = dev_upload(b->store, host, &b->pieces)) || (st = dev_upload(b->store, mb, &b->map_bands)))
+                return st;
+            b->n_bands = (int)mb.size();
+            return RADON_OK;
+        };
+        radon_status st = RADON_OK;
+        const int best = tune_rows(
+            rmax,
+            [&](int R) {
+                if ((st = apply(R))) return 1;
+                const DevBatch Bd{b->pieces, b->map_bands};
+                if (int e = launch_rows_r2c_dev(Bd, b->n_bands, b->smem_rows, nullptr)) return e;
+                if (int e = launch_band_rows_dev(Bd, b->n_bands, b->smem_rows, nullptr)) return e;
+                if (int e = launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, nullptr)) return e;
+                return 0;
+            },
+            nullptr);
+        if (st || (st = apply(best > 0 ? best : std::min(3, rmax)))) {
+            destroy_batch(b);
+            return st;
+        }
+        for (radon_plan_s* p : b->plans) p->d.rows_per_band = host.empty() ? 3 : host[0].R;
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) {
         destroy_batch(b);
         return fail(RADON_ERR_CUDA, "batch creation failed on the device");

@@ -109,3 +109,18 @@ def test_batch_replays_from_a_cuda_graph(hr, uneven):
     torch.cuda.synchronize()
     assert _rel(g.cpu().numpy(), ref_g.cpu().numpy().astype(np.float64)) < 1e-6
     assert _rel(fa.cpu().numpy(), ref_f.cpu().numpy().astype(np.float64)) < 1e-6
+
+
+def test_batch_rows_per_band_tuning(hr, uneven):
+    """The batch-wide rows-per-band tuner (every descriptor asks for 0) picks a
+    feasible value and changes the work split only, not the results."""
+    geos, gathers, batch = uneven
+    tuned = hr.Batch([dict(_geo_dict(g), rows_per_band=0) for g in geos])
+    f = batch.pack([torch.tensor(x, dtype=torch.float32) for x in gathers])
+    g_ref = batch.forward(f)
+    g = tuned.forward(f)
+    assert _rel(g.cpu().numpy(), g_ref.cpu().numpy().astype(np.float64)) < 1e-6
+    fa = tuned.adjoint(g_ref)
+    fa_ref = batch.adjoint(g_ref)
+    assert _rel(fa.cpu().numpy(), fa_ref.cpu().numpy().astype(np.float64)) < 1e-6
+    tuned.close()

@@ -268,3 +268,22 @@ def test_non_finite_input_gives_non_finite_output(hr):
         g[5, 60] = bad
         assert not np.isfinite(plan.adjoint(_cuda(g)).cpu().numpy()).all()
     assert _rel(plan.forward(_cuda(f)).cpu().numpy(), LogPolar(desc).forward(f)) < PARITY_TOL
+
+
+def test_rows_per_band_choices_and_tuner(hr):
+    """Every rows-per-band value, and the plan-time tuner (0), give the same
+    transforms: the value only splits the row-FFT work among CTAs."""
+    geo = synth.Geometry(300, 120, 280, 100, 0.005, 0.015, 0.2, 0.7)
+    f = synth.band_limited_gather(geo, 71, n_events=5, nu=10.0)
+    g_in = synth.random_radon_image(geo, 72)
+    outs = {}
+    for R in (0, 1, 2, 3, 4):
+        plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, rows_per_band=R)
+        assert 1 <= plan.desc.rows_per_band <= 4
+        if R:
+            assert plan.desc.rows_per_band == R
+        outs[R] = (plan.forward(_cuda(f)).cpu().numpy(), plan.adjoint(_cuda(g_in)).cpu().numpy())
+        plan.close()
+    for R in (0, 1, 2, 4):
+        assert _rel(outs[R][0], outs[3][0].astype(np.float64)) < 1e-6
+        assert _rel(outs[R][1], outs[3][1].astype(np.float64)) < 1e-6
