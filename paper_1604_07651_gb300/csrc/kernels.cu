@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -983,9 +985,27 @@ int max_smem_optin() {
     return v;
 }
 
+// Dynamic shared-memory limit of a kernel: raised only when a launch needs
+// more than the largest value already set on this device (the attribute call
+// costs host time on every launch otherwise).
 static int set_smem(const void* fn, size_t bytes) {
+    struct Entry { const void* fn; int dev; size_t bytes; };
+    static std::mutex mu;
+    static std::vector<Entry> set;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : set)
+        if (e.fn == fn && e.dev == dev && e.bytes >= bytes) return 0;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return e == cudaSuccess ? 0 : (int)e;
+    if (e != cudaSuccess) return (int)e;
+    for (Entry& en : set)
+        if (en.fn == fn && en.dev == dev) {
+            en.bytes = bytes;
+            return 0;
+        }
+    set.push_back(Entry{fn, dev, bytes});
+    return 0;
 }
 
 // Batch descriptor of n pieces with count(piece) blocks each; returns the

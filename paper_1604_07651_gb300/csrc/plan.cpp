@@ -209,6 +209,7 @@ struct radon_plan_s {
     PieceDev* dev_pieces = nullptr;
     float* lat_all = nullptr;                    // every piece's lattice, back to back
     size_t lat_bytes = 0;
+    std::vector<PieceDev> host_devs;             // host copies of the descriptors (launch parameters)
     const int4* cmap = nullptr;                  // output columns: (first piece, count, l, 0)
     int ncols = 0;
     const int4* smap = nullptr;                  // sample blocks: (first piece, count, first sample, 0)
@@ -1019,6 +1020,7 @@ extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* 
     }
     std::vector<PieceDev> devs;
     for (auto& h : p->pieces) devs.push_back(h.dev);
+    p->host_devs = devs;
     const PieceDev* dp = nullptr;
     if ((s = dev_upload(p, devs, &dp))) { destroy_plan(p); return s; }
     p->dev_pieces = const_cast<PieceDev*>(dp);
@@ -1105,17 +1107,13 @@ static radon_status run_forward(radon_plan_s* p, const PieceDev* P, const PieceD
     return RADON_OK;
 }
 
-static std::vector<PieceDev> host_pieces(const radon_plan_s* p) {
-    std::vector<PieceDev> v;
-    for (auto& h : p->pieces) v.push_back(h.dev);
-    return v;
-}
+static const std::vector<PieceDev>& host_pieces(const radon_plan_s* p) { return p->host_devs; }
 
 extern "C" radon_status radon_fwd(radon_plan p, const float* f, float* g, void* stream) {
     if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
     if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
     DeviceGuard guard(p->device);
-    const std::vector<PieceDev> P = host_pieces(p);
+    const std::vector<PieceDev>& P = host_pieces(p);
     return run_forward(p, P.data(), p->dev_pieces, p->lat_all, p->lat_bytes, f, g, stream);
 }
 
@@ -1123,7 +1121,7 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
     if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
     if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
     DeviceGuard guard(p->device);
-    const std::vector<PieceDev> P = host_pieces(p);
+    const std::vector<PieceDev>& P = host_pieces(p);
     const int np = (int)P.size();
     double b_lat = 0, b_spec = 0, b_ker = 0, b_g = 0, b_h = 0;
     for (const PieceDev& q : P) {
