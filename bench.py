@@ -135,14 +135,14 @@ STAGE_KERNEL = {"grid_fwd": "k_grid_tiles", "rows_r2c_fwd": "k_rows_r2c", "colco
 # on: the entry is dropped (traffic null) when csrc/kernels.cu changes.
 MEASURED_TRAFFIC = {
     # kernel: (sha256 prefix of csrc/kernels.cu, bytes per launch averaged over a step's launches)
-    "k_grid_tiles": ("be3290ad43fa9ac8", 127.77e6),
-    "k_rows_r2c": ("be3290ad43fa9ac8", 28.28e6),
-    "k_colconv": ("be3290ad43fa9ac8", 51.29e6),
-    "k_rows_c2r": ("be3290ad43fa9ac8", 29.35e6),
-    "k_interp_columns": ("be3290ad43fa9ac8", 130.16e6),
-    "k_col_profiles": ("be3290ad43fa9ac8", 141.06e6),
-    "k_band_rows": ("be3290ad43fa9ac8", 45.90e6),
-    "k_gather_samples": ("be3290ad43fa9ac8", 105.25e6),
+    "k_grid_tiles": ("fa1a438a9571d4a8", 127.83e6),
+    "k_rows_r2c": ("fa1a438a9571d4a8", 28.30e6),
+    "k_colconv": ("fa1a438a9571d4a8", 51.31e6),
+    "k_rows_c2r": ("fa1a438a9571d4a8", 29.37e6),
+    "k_interp_columns": ("fa1a438a9571d4a8", 130.09e6),
+    "k_col_profiles": ("fa1a438a9571d4a8", 142.45e6),
+    "k_band_rows": ("fa1a438a9571d4a8", 45.62e6),
+    "k_gather_samples": ("fa1a438a9571d4a8", 105.18e6),
 }
 
 # FFT kernels run out of shared memory and are limited by instruction issue,
@@ -368,6 +368,8 @@ def main():
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--no-solver", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--rows-per-band", type=int, default=0,
+                    help="rows per band of the row-FFT kernels; 0 times them at plan creation")
     ap.add_argument("--batch-gathers", type=int, default=256)
     args = ap.parse_args()
 
@@ -391,8 +393,8 @@ def main():
     import paper_1604_07651_gb300 as hr
     geo, f_np = make_workload(rank)
     dev = torch.device("cuda", local)
-    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, rows_per_band=0,
-                   device=local)   # rows per band timed at plan creation
+    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+                   rows_per_band=args.rows_per_band, device=local)   # 0: timed at plan creation
     f = torch.tensor(f_np, dtype=torch.float32, device=dev)
     g = torch.empty((geo.Nq, geo.Ntau), dtype=torch.float32, device=dev)
     fa = torch.empty_like(f)
