@@ -52,6 +52,8 @@ struct PieceDev {
     // tables (device pointers)
     const SampleEnt* stab;  // [Nx][nj] position and weight of every sample of the piece
     const RadonEnt* rtab;   // [ncol][Ntau] rho position of every output of the piece
+    const int2* rrange;     // [ncol] first and last output of the column with a valid rtab entry
+                            // (x > y: none); every valid entry lies inside
     int ntr, ntc;           // lattice tiles of the forward gridding: rows, columns
     int nunits;             // work units of the forward gridding
     const int4* units;      // (tile, first chunk, end chunk, 28 - ilogb(cell weight bound)), heaviest first
@@ -78,6 +80,8 @@ struct PieceDev {
 // Up to kMaxBatch sub-problems launched as one grid: the blocks of piece k
 // are [first[k], first[k+1]); passed by value (about 3.3 KB of parameters).
 constexpr int kMaxBatch = 8;
+// Time pieces of one output column at most (RADON_MAX_TSPLIT + 1).
+constexpr int kMaxColPieces = 9;
 struct PieceBatch {
     int n;
     int first[kMaxBatch + 1];
@@ -122,9 +126,10 @@ int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
 // Output interpolation: one CTA per output column; cmap[b] = (first piece,
 // number of time pieces, column l, 0) in `pieces` (device), or, when
 // np_all > 0 (one gather, one slowness piece of np_all time pieces, ntau_all
-// outputs per column), column b of pieces[0..np_all). Shared memory
-// (nrho_max + ntau_max) floats.
-int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int ntau_max,
+// outputs per column), column b of pieces[0..np_all). np_max: the largest
+// number of time pieces of a column (<= kMaxColPieces); shared memory
+// np_max * nrho_max floats.
+int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,
                           int ntau_all, int np_all, float* g, void* stream);
 // Adjoint gather: one CTA per kSampleBlock samples of one gather;
 // smap[b] = (first piece, number of pieces, first sample, 0), or, when

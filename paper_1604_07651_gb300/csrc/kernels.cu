@@ -18,8 +18,10 @@
 // Lattice positions do not depend on the data: the plan computes them once in
 // FP64 (k_sample_table, k_radon_table) and stores first tap and fractional
 // part, so the transforms themselves are FP32 loads, B-spline weights and
-// sums. Shared-memory accumulation uses FP32 atomics, so the last bits of the
-// gridding depend on the order in which warps arrive.
+// sums. Shared-memory accumulation is fixed point (integer atomics, order
+// independent); the gridding's work units meet on the lattice through FP32
+// global atomics, so the last bits of the forward lattice depend on the order
+// in which units finish. The adjoint has no floating-point atomics.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -496,7 +498,10 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
     const Pow2Scale scl(__ldg(P.colsh + lc) - ilogbf(vmax));
     const float sc = __ldg(P.colscale + lc);
     const int lane = threadIdx.x & 31;
-    for (int i0 = 0; i0 < P.Ntau; i0 += chunk) {   // uniform over the block: every lane takes part
+    // only the column's valid outputs (the max above still sees every output,
+    // so a non-finite value anywhere in the column poisons the profile)
+    const int2 rg = __ldg(P.rrange + lc);
+    for (int i0 = rg.x & ~31; i0 <= rg.y; i0 += chunk) {   // uniform over the block: every lane takes part
         int2 e[Q];
         float v[Q];
 #pragma unroll
@@ -504,7 +509,7 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
             const int i = i0 + q * (int)blockDim.x + threadIdx.x;   // a warp: 32 consecutive outputs
             e[q] = make_int2(-1, 0);
             v[q] = 0.f;
-            if (i < P.Ntau) {
+            if (i <= rg.y) {
                 e[q] = __ldg(rt + i);
                 v[q] = __ldg(gl + i);
             }
@@ -718,8 +723,9 @@ __device__ __forceinline__ float taps16(const float* __restrict__ lat, int Nr, i
 // theta taps, so the 4x4 taps separate: the CTA first spreads the four
 // lattice rows of the column's angle into a rho profile in shared memory,
 //   r[n] = sum_a B3(theta_l - theta_{m0+a}) H[m0 + a][n],
-// then every output takes 4 taps of it; the pieces are summed per output in
-// a fixed order (shared memory: [nrho_max] profile, [ntau_max] sums).
+// for every time piece at once (shared memory: [np][nrho_max] profiles),
+// then every output takes 4 taps of each piece's profile and sums the pieces
+// in a fixed order. Outputs outside a piece's valid range skip its table.
 __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restrict__ pieces,
                                                         const int4* __restrict__ cmap, int nrho_max,
                                                         int ntau_all, int np_all, float* __restrict__ g) {
@@ -728,36 +734,56 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
     const int4 c = np_all > 0 ? make_int4(0, np_all, (int)blockIdx.x, 0) : __ldg(cmap + blockIdx.x);
     const int l = c.z, np = c.y;
     const int Ntau = np_all > 0 ? ntau_all : pieces[c.x].Ntau;
-    if ((size_t)(nrho_max + Ntau) * sizeof(float) > dyn_smem_bytes()) return;
-    float* prof = smem_f;
-    float* acc = smem_f + nrho_max;
-    for (int i = threadIdx.x; i < Ntau; i += blockDim.x) acc[i] = 0.f;
-    for (int p = c.x; p < c.x + np; ++p) {
-        const PieceDev& P = pieces[p];
+    if (np > kMaxColPieces || (size_t)np * nrho_max * sizeof(float) > dyn_smem_bytes()) return;
+    // per-piece column data, loaded for all pieces at once
+    __shared__ float4 s_w4[kMaxColPieces];
+    __shared__ const float* s_r0[kMaxColPieces];
+    __shared__ const int2* s_rt[kMaxColPieces];
+    __shared__ float s_sc[kMaxColPieces];
+    __shared__ int2 s_rg[kMaxColPieces];
+    __shared__ int s_nr[kMaxColPieces];
+    if ((int)threadIdx.x < np) {
+        const PieceDev& P = pieces[c.x + threadIdx.x];
         const int lc = l - P.l_lo;
-        const int Nr = P.Nrho;
-        const float4 w4 = __ldg(P.colw + lc);
-        const float sc = __ldg(P.colscale + lc);
-        const float* r0 = P.lat + (size_t)__ldg(P.colm0 + lc) * Nr;
-        __syncthreads();   // the previous piece's taps are read
+        s_w4[threadIdx.x] = __ldg(P.colw + lc);
+        s_sc[threadIdx.x] = __ldg(P.colscale + lc);
+        s_r0[threadIdx.x] = P.lat + (size_t)__ldg(P.colm0 + lc) * P.Nrho;
+        s_rt[threadIdx.x] = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * Ntau);
+        s_rg[threadIdx.x] = __ldg(P.rrange + lc);
+        s_nr[threadIdx.x] = P.Nrho;
+    }
+    __syncthreads();
+    // theta taps (the column's four lattice rows) of every piece: the rho
+    // profiles, np * nrho_max floats; all pieces' loads in flight together
+    for (int p = 0; p < np; ++p) {
+        const int Nr = s_nr[p];
+        const float4 w4 = s_w4[p];
+        const float* r0 = s_r0[p];
+        float* prof = smem_f + p * nrho_max;
+#pragma unroll 2
         for (int n = threadIdx.x; n < Nr; n += blockDim.x) {
             const float a0 = __ldg(r0 + n), a1 = __ldg(r0 + Nr + n);
             const float a2 = __ldg(r0 + 2 * Nr + n), a3 = __ldg(r0 + 3 * Nr + n);
             prof[n] = w4.x * a0 + w4.y * a1 + w4.z * a2 + w4.w * a3;
         }
-        __syncthreads();
-        const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * Ntau);
-        for (int i = threadIdx.x; i < Ntau; i += blockDim.x) {
-            const int2 e = __ldg(rt + i);
+    }
+    __syncthreads();
+    // rho taps: every output sums its pieces in piece order
+    float* gl = g + (np_all > 0 ? 0 : pieces[c.x].g_off) + (size_t)l * Ntau;
+    for (int i = threadIdx.x; i < Ntau; i += blockDim.x) {
+        float acc = 0.f;
+        for (int p = 0; p < np; ++p) {
+            const int2 rg = s_rg[p];
+            if (i < rg.x || i > rg.y) continue;
+            const int2 e = __ldg(s_rt[p] + i);
             if (e.x < 0) continue;
             float wr[4];
             b3_weights(__int_as_float(e.y), wr);
-            const float* r = prof + e.x;
-            acc[i] += sc * (wr[0] * r[0] + wr[1] * r[1] + wr[2] * r[2] + wr[3] * r[3]);
+            const float* r = smem_f + p * nrho_max + e.x;
+            acc += s_sc[p] * (wr[0] * r[0] + wr[1] * r[1] + wr[2] * r[2] + wr[3] * r[3]);
         }
+        gl[i] = acc;
     }
-    float* gl = g + (np_all > 0 ? 0 : pieces[c.x].g_off) + (size_t)l * Ntau;
-    for (int i = threadIdx.x; i < Ntau; i += blockDim.x) gl[i] = acc[i];
 }
 
 // Adjoint of the gridding (transpose of Eq. (15)): every gather sample reads
@@ -1120,9 +1146,10 @@ int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
     return set_and_launch(k_rows_c2r<DevBatch>, nblocks, smem, S, stream);
 }
 
-int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int ntau_max,
+int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,
                           int ntau_all, int np_all, float* g, void* stream) {
-    const size_t sm = ((size_t)nrho_max + ntau_max) * sizeof(float);
+    if (np_max > kMaxColPieces) return (int)cudaErrorInvalidValue;
+    const size_t sm = (size_t)np_max * nrho_max * sizeof(float);
     if (int e = set_smem((const void*)k_interp_columns, sm)) return e;
     if (ncols > 0)
         k_interp_columns<<<ncols, 256, sm, (cudaStream_t)stream>>>(pieces, cmap, nrho_max, ntau_all, np_all, g);

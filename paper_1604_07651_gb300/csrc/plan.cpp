@@ -212,6 +212,7 @@ struct radon_plan_s {
     std::vector<PieceDev> host_devs;             // host copies of the descriptors (launch parameters)
     const int4* cmap = nullptr;                  // output columns: (first piece, count, l, 0)
     int ncols = 0;
+    int col_pieces = 0;                          // largest count of cmap
     const int4* smap = nullptr;                  // sample blocks: (first piece, count, first sample, 0)
     int nsblocks = 0;
     int nrho_max = 0;
@@ -761,11 +762,15 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
             return fail(RADON_ERR_CUDA, "reading back the output position table failed");
         std::vector<double> prof(h.Nrho);
         std::vector<int> colsh(ncol);
+        std::vector<int2> rrange(ncol);
         for (int lc = 0; lc < ncol; ++lc) {
             std::fill(prof.begin(), prof.end(), 0.0);
+            rrange[lc] = int2{d.Ntau, -1};
             for (int i = 0; i < d.Ntau; ++i) {
                 const RadonEnt e = rt[(size_t)lc * d.Ntau + i];
                 if (e.n0 < 0) continue;
+                rrange[lc].x = std::min(rrange[lc].x, i);
+                rrange[lc].y = std::max(rrange[lc].y, i);
                 float wr[4];
                 b3_weights(e.fr, wr);
                 for (int c = 0; c < 4; ++c) prof[e.n0 + c] += (double)colscale[lc] * wr[c];
@@ -773,7 +778,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
             const double cmax = *std::max_element(prof.begin(), prof.end());
             colsh[lc] = 28 - std::ilogb(cmax > 0 ? cmax : 1.0);
         }
-        if ((s = dev_upload(p, colsh, &P.colsh))) return s;
+        if ((s = dev_upload(p, colsh, &P.colsh)) || (s = dev_upload(p, rrange, &P.rrange))) return s;
     }
     P.hpitch = (h.Nrho + 3) & ~3;
     return RADON_OK;
@@ -1033,6 +1038,7 @@ extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* 
         return s;
     }
     p->ncols = (int)cmap.size();
+    for (const int4& c : cmap) p->col_pieces = std::max(p->col_pieces, c.y);
     p->nsblocks = (int)smap.size();
     if (cudaDeviceSynchronize() != cudaSuccess) {
         destroy_plan(p);
@@ -1100,7 +1106,7 @@ static radon_status run_forward(radon_plan_s* p, const PieceDev* P, const PieceD
     const double gb = 4.0 * p->d.Ntau * p->d.Nq;
     if (radon_status s = cuda_status(
             timed(p, 4, b_lat + gb, stream,
-                  [&] { return launch_interp_columns(dP, p->cmap, p->ncols, p->nrho_max, p->d.Ntau, p->d.Ntau,
+                  [&] { return launch_interp_columns(dP, p->cmap, p->ncols, p->nrho_max, p->col_pieces, p->d.Ntau,
                                                p->qpieces.size() == 1 ? np : 0, g, stream); }),
             "interpolation"))
         return s;
@@ -1315,9 +1321,9 @@ struct radon_batch_s {
     int n_units = 0, n_bands = 0, n_kb = 0, n_cols = 0;
     const int4* cmap = nullptr;
     const int4* smap = nullptr;
-    int ncols = 0, nsblocks = 0;
+    int ncols = 0, nsblocks = 0, col_pieces = 0;
     size_t smem_rows = 0, smem_cols = 0, smem_prof = 0;
-    int nrho_max = 0, ntau_max = 0;
+    int nrho_max = 0;
     float* lat_all = nullptr;
     size_t lat_bytes = 0;
 };
@@ -1426,7 +1432,6 @@ extern "C" radon_status radon_batch_create(radon_batch* out, int n, const radon_
         b->smem_cols = std::max(b->smem_cols, colconv_smem_bytes(P));
         b->smem_prof = std::max(b->smem_prof, profile_smem_bytes(P));
         b->nrho_max = std::max(b->nrho_max, P.Nrho);
-        b->ntau_max = std::max(b->ntau_max, P.Ntau);
     }
     // block maps of the stage launches and the maps of the two gathers
     std::vector<int2> mu, mb, mk, mc;
@@ -1456,6 +1461,7 @@ extern "C" radon_status radon_batch_create(radon_batch* out, int n, const radon_
     b->n_kb = (int)mk.size();
     b->n_cols = (int)mc.size();
     b->ncols = (int)cmap.size();
+    for (const int4& c : cmap) b->col_pieces = std::max(b->col_pieces, c.y);
     b->nsblocks = (int)smap.size();
     // rows per band tuned over the whole batch when every descriptor asks
     bool tune = true;
@@ -1554,7 +1560,7 @@ extern "C" radon_status radon_batch_fwd(radon_batch b, const void* f, int in_typ
         return s;
     if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
         return s;
-    return cuda_status(launch_interp_columns(b->pieces, b->cmap, b->ncols, b->nrho_max, b->ntau_max, 0, 0, g, stream),
+    return cuda_status(launch_interp_columns(b->pieces, b->cmap, b->ncols, b->nrho_max, b->col_pieces, 0, 0, g, stream),
                        "interpolation");
 }
 
