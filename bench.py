@@ -5,7 +5,9 @@ T = 2 s, X = 2 km, q in [0.2, 0.7] s/km, 32 Ricker events 20-40 Hz plus 5 %
 noise), default method parameters. One step = radon_fwd then radon_adj on
 device-resident data (the pair one iteration of Eq. (18) needs). L2 is
 flushed (a 256 MiB write) before every timed step; only the step itself is
-timed, with CUDA events on the launching stream.
+timed, with CUDA events on the launching stream. Kernel durations come from
+per-stage events on every fourth timed step (launched eagerly); the other
+timed steps replay the step as a CUDA graph (--no-graph: all eager).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -133,6 +135,8 @@ STAGE_KERNEL = {"grid_fwd": "k_grid_tiles", "rows_r2c_fwd": "k_rows_r2c", "colco
 # DRAM bytes (read + write) per launch from one ncu capture of the benchmark
 # workload (profiles/*.md), valid only for the kernel source they were taken
 # on: the entry is dropped (traffic null) when csrc/kernels.cu changes.
+PROFILE_EVERY = 4   # one timed step in PROFILE_EVERY records per-stage kernel events
+
 MEASURED_TRAFFIC = {
     # kernel: (sha256 prefix of csrc/kernels.cu, bytes per launch averaged over a step's launches)
     "k_grid_tiles": ("fa1a438a9571d4a8", 127.83e6),
@@ -368,6 +372,7 @@ def main():
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--no-solver", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch every timed step eagerly")
     ap.add_argument("--rows-per-band", type=int, default=0,
                     help="rows per band of the row-FFT kernels; 0 times them at plan creation")
     ap.add_argument("--batch-gathers", type=int, default=256)
@@ -408,10 +413,25 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
+    # the step as one CUDA graph (its 10 launches and the lattice memset),
+    # captured after the warm-up; the steps with per-stage events run eagerly
+    graph = None
+    if not args.no_graph:
+        plan.set_profiling(False)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
 
-    # timed region: per-step CUDA events, L2 flushed before each step
-    plan.set_profiling(True)
+    # timed region: per-step CUDA events, L2 flushed before each step. The
+    # per-stage events (kernel durations for the roofline) are recorded on
+    # every PROFILE_EVERY-th step only: an event between two launches costs
+    # the stream about 2 us, 40 us over a step's 20
+    plan.set_profiling(False)
     plan.profile_read()
+    profiled = [s for s in range(args.steps) if s % PROFILE_EVERY == PROFILE_EVERY - 1] or [args.steps - 1]
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -419,8 +439,10 @@ def main():
     with ClockSampler(local) as clk:
         for s in range(args.steps):
             flush.fill_(float(s))
+            eager = graph is None or s in profiled
+            plan.set_profiling(s in profiled)
             starts[s].record(stream)
-            step()
+            step() if eager else graph.replay()
             ends[s].record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -443,11 +465,11 @@ def main():
     d = per_kernel[dom]
     achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
     stages = {k: {"ms_per_launch": (v["ms"] / v["launches"]) if v["launches"] else 0.0,
-                  "launches_per_step": v["launches"] / args.steps,
+                  "launches_per_step": v["launches"] / len(profiled),
                   "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0,
                   "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
               for k, v in prof.items()}
-    launches = int(round(sum(v["launches"] for v in prof.values()) / args.steps)) * args.steps
+    launches = int(round(sum(v["launches"] for v in prof.values()) / len(profiled))) * args.steps
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -457,8 +479,12 @@ def main():
                               "tsplit": [plan.desc.tsplit[i] for i in range(plan.desc.n_tsplit)],
                               "n_qsplit": plan.desc.n_qsplit, "rows_per_band": plan.desc.rows_per_band},
                    "lattices": [(p["Ntheta"], p["Nrho"], p["Ptheta"], p["Prho"]) for p in plan.pieces()]},
-        "roofline": roofline(dom, d, per_kernel, hbm, peak_kind, plan, clk.summary(), dev, args.steps),
+        "roofline": roofline(dom, d, per_kernel, hbm, peak_kind, plan, clk.summary(), dev, len(profiled)),
         "stages": stages,
+        "kernel_timing": f"per-stage CUDA events on {len(profiled)} of the {args.steps} timed steps "
+                         f"(every {PROFILE_EVERY}th, launched eagerly)",
+        "launch": "eager" if graph is None else
+                  f"CUDA graph replay of the step on {args.steps - len(profiled)} of the {args.steps} timed steps",
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
@@ -477,6 +503,14 @@ def main():
     xin, xout = torch.cuda.Stream(dev), torch.cuda.Stream(dev)   # one copy stream per direction
     ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "done", "out")}
     used = [False, False]
+    pair_graphs = [None, None]                      # forward + adjoint on buffer set b
+    if graph is not None:
+        for b in range(2):
+            pair_graphs[b] = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(pair_graphs[b]):
+                plan.forward(fd[b], out=gd[b])
+                plan.adjoint(gd[b], out=fad[b])
+        torch.cuda.synchronize()
 
     def e2e_step(s):
         b = s & 1
@@ -488,8 +522,11 @@ def main():
         stream.wait_event(ev["in"][b])
         if used[b]:
             stream.wait_event(ev["out"][b])         # step s-2's results are copied out
-        plan.forward(fd[b], out=gd[b])
-        plan.adjoint(gd[b], out=fad[b])
+        if pair_graphs[b] is None:
+            plan.forward(fd[b], out=gd[b])
+            plan.adjoint(gd[b], out=fad[b])
+        else:
+            pair_graphs[b].replay()
         ev["done"][b].record(stream)
         with torch.cuda.stream(xout):
             xout.wait_event(ev["done"][b])
@@ -515,7 +552,8 @@ def main():
     result["e2e"] = {"value": job_value(args.steps, world, e2e_ms), "unit": UNIT,
                      "h2d_bytes_per_step": f.numel() * 4,
                      "d2h_bytes_per_step": (g.numel() + fa.numel()) * 4,
-                     "copies": "pinned host buffers, one copy stream per direction overlapped with the transforms"}
+                     "copies": "pinned host buffers, one copy stream per direction overlapped with the transforms",
+                     "launch": "eager" if graph is None else "CUDA graph replay of the transforms"}
 
     if rank == 0:
         # accuracy of this run's results against the FP64 oracle (sampled points)
