@@ -42,6 +42,10 @@ def _load():
         lib.oracle_direct_adj.argtypes = [_dp, i, i, d, d, d, d, i, _dp, i, _dp]
         lib.oracle_direct_adj_points.argtypes = [_dp, i, i, d, d, d, d, i, _dp, i, _ip, _ip, i, _dp]
         lib.oracle_direct_adj_brute.argtypes = [_dp, i, i, d, d, _dp, i, _dp, i, _dp]
+        lib.oracle_direct_fwd_x.argtypes = [_dp, i, i, d, _dp, _dp, i, _dp, i, _dp]
+        lib.oracle_direct_fwd_x_points.argtypes = [_dp, i, i, d, _dp, _dp, _dp, _ip, _ip, i, _dp]
+        lib.oracle_direct_adj_x.argtypes = [_dp, i, i, d, _dp, d, d, i, _dp, i, _dp]
+        lib.oracle_direct_adj_x_points.argtypes = [_dp, i, d, _dp, d, d, i, _dp, i, _ip, _ip, i, _dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -123,3 +127,70 @@ def adj_brute(g, Nt, Nx, dt, dx, tau, q):
     f = np.zeros((Nx, Nt))
     lib.oracle_direct_adj_brute(gp, Nt, Nx, dt, dx, tp, Ntau, qp, Nq, f.ctypes.data_as(_dp))
     return f
+
+
+# ---- unequally spaced offsets (trapezoid weights on the given offsets) ----
+
+def _offsets(x, Nx):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.shape != (Nx,) or Nx < 2 or not np.all(np.diff(x) > 0):
+        raise ValueError("need Nx >= 2 strictly increasing offsets")
+    return x, x.ctypes.data_as(_dp)
+
+
+def fwd_x(f, dt, x, tau, q):
+    """Forward on offsets ``x[Nx]`` (km): ``f[Nx][Nt]`` -> ``g[Nq][Ntau]``."""
+    lib = _load()
+    f, fp = _d(f)
+    Nx, Nt = f.shape
+    x, xp = _offsets(x, Nx)
+    tau, tp = _d(tau)
+    q, qp = _d(q)
+    g = np.zeros((q.size, tau.size))
+    lib.oracle_direct_fwd_x(fp, Nt, Nx, dt, xp, tp, tau.size, qp, q.size, g.ctypes.data_as(_dp))
+    return g
+
+
+def fwd_x_points(f, dt, x, tau, q, ii, li):
+    """Forward on offsets ``x`` at sampled outputs ``g[li[p], ii[p]]``."""
+    lib = _load()
+    f, fp = _d(f)
+    Nx, Nt = f.shape
+    x, xp = _offsets(x, Nx)
+    tau, tp = _d(tau)
+    q, qp = _d(q)
+    ii, iip = _i(ii)
+    li, lip = _i(li)
+    out = np.zeros(ii.size)
+    lib.oracle_direct_fwd_x_points(fp, Nt, Nx, dt, xp, tp, qp, iip, lip, ii.size, out.ctypes.data_as(_dp))
+    return out
+
+
+def adj_x(g, Nt, dt, x, tau0, dtau, q):
+    """Adjoint on offsets ``x[Nx]``: ``g[Nq][Ntau]`` -> ``f[Nx][Nt]``."""
+    lib = _load()
+    g, gp = _d(g)
+    x = np.asarray(x, dtype=np.float64)
+    Nx = x.size
+    x, xp = _offsets(x, Nx)
+    q, qp = _d(q)
+    Nq, Ntau = g.shape
+    f = np.zeros((Nx, Nt))
+    lib.oracle_direct_adj_x(gp, Nt, Nx, dt, xp, tau0, dtau, Ntau, qp, Nq, f.ctypes.data_as(_dp))
+    return f
+
+
+def adj_x_points(g, dt, x, tau0, dtau, q, jj, kk):
+    """Adjoint on offsets ``x`` at sampled gather points ``f[kk[p], jj[p]]``."""
+    lib = _load()
+    g, gp = _d(g)
+    x = np.asarray(x, dtype=np.float64)
+    x, xp = _offsets(x, x.size)
+    q, qp = _d(q)
+    jj, jp = _i(jj)
+    kk, kp = _i(kk)
+    Nq, Ntau = g.shape
+    out = np.zeros(jj.size)
+    lib.oracle_direct_adj_x_points(gp, x.size, dt, xp, tau0, dtau, Ntau, qp, Nq, jp, kp, jj.size,
+                                   out.ctypes.data_as(_dp))
+    return out

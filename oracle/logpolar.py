@@ -60,6 +60,12 @@ class Desc:
     of the frequency rectangle L in cycles per lattice cell; ``tsplits`` are
     the split points of Eq. (19) as fractions of T; ``n_qsplit`` is the
     number of slowness pieces.
+
+    Unequally spaced grids (Section 4: the method carries over to them):
+    ``x`` lists the Nx offsets (km, strictly increasing, x_0 >= 0; X is the
+    largest) in place of ``k dx``, and ``q_values`` the Nq slownesses (s/km,
+    strictly increasing, >= 0) in place of the regular q grid. Time and
+    intercept time stay regular.
     """
     Nt: int
     Nx: int
@@ -75,6 +81,18 @@ class Desc:
     omega_c: float = 0.25
     tsplits: tuple = ()
     n_qsplit: int = 1
+    x: tuple | None = None
+    q_values: tuple | None = None
+
+    def __post_init__(self):
+        if self.x is not None:
+            x = np.asarray(self.x, dtype=np.float64)
+            if x.shape != (self.Nx,) or self.Nx < 2 or x[0] < 0 or not np.all(np.diff(x) > 0):
+                raise ValueError("x: need Nx strictly increasing offsets >= 0")
+        if self.q_values is not None:
+            q = np.asarray(self.q_values, dtype=np.float64)
+            if q.shape != (self.Nq,) or q[0] < 0 or not np.all(np.diff(q) > 0):
+                raise ValueError("q_values: need Nq strictly increasing slownesses >= 0")
 
     @property
     def T(self):
@@ -82,7 +100,44 @@ class Desc:
 
     @property
     def X(self):
+        if self.x is not None:
+            return float(self.x[-1])
         return (self.Nx - 1) * self.dx
+
+    def xb(self):
+        """Rescaled offsets x_k / X of Eq. (12)."""
+        if self.x is None:
+            return np.arange(self.Nx) / (self.Nx - 1)
+        return np.asarray(self.x, dtype=np.float64) / self.X
+
+    def xb_spacing(self):
+        """Rescaled offsets the lattice spacing of Eq. (18) is taken over:
+        the offsets themselves on a regular grid; on given offsets, equally
+        spaced ones over the same range [x_0, X]. Reading (Section 4 only
+        treats regular sampling): the gridding treats the samples as a
+        quadrature, so the lattice has to resolve the band of the data, which
+        the mean spacing sets; the largest gap would coarsen the lattice and
+        raise the error tenfold at 40 % jitter."""
+        if self.x is None:
+            return self.xb()
+        x0 = float(self.x[0])
+        return (x0 + np.arange(self.Nx) * ((self.X - x0) / (self.Nx - 1))) / self.X
+
+    def x_weights(self):
+        """Trapezoid weights of the offsets in units of the mean rescaled
+        spacing 1/(Nx-1): 1/2 at the ends and 1 inside on a regular grid;
+        (xb_{k+1} - xb_{k-1}) / 2 times (Nx-1) inside and the half gaps at the
+        ends on given offsets."""
+        n_x = self.Nx - 1
+        if self.x is None:
+            k = np.arange(self.Nx)
+            return np.where((k == 0) | (k == n_x), 0.5, 1.0)
+        xb = self.xb()
+        w = np.empty(self.Nx)
+        w[0] = 0.5 * (xb[1] - xb[0])
+        w[-1] = 0.5 * (xb[-1] - xb[-2])
+        w[1:-1] = 0.5 * (xb[2:] - xb[:-2])
+        return w * n_x
 
     @property
     def dtau_eff(self):
@@ -92,6 +147,8 @@ class Desc:
         return self.tau0 + np.arange(self.Ntau) * self.dtau_eff
 
     def q(self):
+        if self.q_values is not None:
+            return np.asarray(self.q_values, dtype=np.float64)
         if self.Nq == 1:
             return np.array([self.qmin], dtype=np.float64)
         return self.qmin + np.arange(self.Nq) * ((self.qmax - self.qmin) / (self.Nq - 1))
@@ -325,7 +382,7 @@ def make_partition(desc: Desc, jt: tuple[int, int, int], lq: tuple[int, int]) ->
     taub_min = desc.tau0 / T
     c_min = taub_min * taub_min
     k2 = float(qb[0] ** 2)
-    xb2 = (np.arange(desc.Nx) / n_x) ** 2
+    xb2 = desc.xb() ** 2
     tb2 = (np.arange(j0, j1 + 1) / n_t) ** 2
     jfirst = np.empty(desc.Nx, dtype=np.int64)
     for k in range(desc.Nx):
@@ -345,8 +402,9 @@ def make_partition(desc: Desc, jt: tuple[int, int, int], lq: tuple[int, int]) ->
                    for th in (-beta / 2, beta / 2))
     part.r_max = float(np.max(np.sqrt(u1 * u1 + u2 * u2)))
 
-    # Sample spacing of Eq. (18), over all samples of the time piece.
-    U1, U2 = map_T(part, tb2[None, :], xb2[:, None])
+    # Sample spacing of Eq. (18), over all samples of the time piece (on
+    # given offsets: over equally spaced offsets of the same range).
+    U1, U2 = map_T(part, tb2[None, :], (desc.xb_spacing() ** 2)[:, None])
     phi, eta = map_P1(U1, U2)
     dphi = max(float(np.max(np.abs(np.diff(phi, axis=1)))) if phi.shape[1] > 1 else 0.0,
                float(np.max(np.abs(np.diff(phi, axis=0)))) if phi.shape[0] > 1 else 0.0)
@@ -493,7 +551,8 @@ def data_points(desc: Desc, part: Partition):
     (the xb cancels, as the paper notes after Eq. (14)); psi_p is the window
     of the time piece.
     Reading: rectangle weights in t (matching the interpolating cubic in t of
-    the reference direct sum) and trapezoid weights in x (end traces 1/2).
+    the reference direct sum) and trapezoid weights in x (end traces 1/2; on
+    given offsets, the trapezoid weights of those offsets, Desc.x_weights).
     """
     n_t, n_x = desc.Nt - 1, desc.Nx - 1
     jj, kk = [], []
@@ -504,10 +563,10 @@ def data_points(desc: Desc, part: Partition):
     jj = np.concatenate(jj) if jj else np.zeros(0, np.int64)
     kk = np.concatenate(kk) if kk else np.zeros(0, np.int64)
     tb = jj / n_t
-    xb = kk / n_x
+    xb = desc.xb()[kk]
     u1, u2 = map_T(part, tb * tb, xb * xb)
     phi, eta = map_P1(u1, u2)
-    wk = np.where((kk == 0) | (kk == n_x), 0.5, 1.0)
+    wk = desc.x_weights()[kk]
     wt = t_window(desc, part.tpiece, tb)
     wfac = 2.0 * part.a ** 2 * tb * wt * np.exp(-eta) * wk / (n_t * n_x)
     xth = (phi - part.theta0) / part.dtheta

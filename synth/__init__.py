@@ -20,13 +20,17 @@ __all__ = [
     "Geometry", "ricker", "rng_for", "hyperbolic_gather", "gaussian_gather",
     "random_radon_image", "single_gather", "sweep_gather", "large_gather", "missing_trace_gather",
     "batch_gather", "primaries_multiples",
-    "band_limited_gather", "batch_geometries",
+    "band_limited_gather", "batch_geometries", "irregular_geometry",
 ]
 
 
 @dataclasses.dataclass(frozen=True)
 class Geometry:
-    """Sampling of one gather and of its Radon image (physical units)."""
+    """Sampling of one gather and of its Radon image (physical units).
+
+    ``offsets`` / ``slownesses``, when given, replace the regular offset grid
+    ``k dx`` / slowness grid (unequally spaced geometries); X is then the
+    largest offset."""
     Nt: int
     Nx: int
     Ntau: int
@@ -35,6 +39,8 @@ class Geometry:
     dx: float
     qmin: float
     qmax: float
+    offsets: tuple | None = None
+    slownesses: tuple | None = None
 
     @property
     def T(self) -> float:
@@ -42,6 +48,8 @@ class Geometry:
 
     @property
     def X(self) -> float:
+        if self.offsets is not None:
+            return float(self.offsets[-1])
         return (self.Nx - 1) * self.dx
 
     @property
@@ -52,12 +60,16 @@ class Geometry:
         return np.arange(self.Nt) * self.dt
 
     def x(self) -> np.ndarray:
+        if self.offsets is not None:
+            return np.asarray(self.offsets, dtype=np.float64)
         return np.arange(self.Nx) * self.dx
 
     def tau(self) -> np.ndarray:
         return np.arange(self.Ntau) * self.dtau
 
     def q(self) -> np.ndarray:
+        if self.slownesses is not None:
+            return np.asarray(self.slownesses, dtype=np.float64)
         if self.Nq == 1:
             return np.array([self.qmin])
         return self.qmin + np.arange(self.Nq) * (self.qmax - self.qmin) / (self.Nq - 1)
@@ -233,3 +245,23 @@ def batch_geometries(n: int, tag: int = 4) -> list[Geometry]:
         Nx = int(rng.integers(60, 481))
         out.append(Geometry(Nt, Nx, Nt, Nx, 0.004, 0.025, 0.2, 0.7))
     return out
+
+
+def irregular_geometry(Nt: int, Nx: int, Ntau: int, Nq: int, dt: float, X: float,
+                       qmin: float, qmax: float, tag: int, jitter: float = 0.4,
+                       near: float = 0.0, q_power: float = 1.0) -> Geometry:
+    """Unequally spaced offsets and slownesses.
+
+    Offsets: Nx regular nodes on [near, X], the inner ones moved by
+    U(-jitter, jitter) of the node spacing (jitter < 1/2 keeps them strictly
+    increasing; the end nodes stay). Slownesses: qmin + (qmax - qmin) u^q_power
+    on a regular u grid in [0, 1] (denser towards qmin for q_power > 1).
+    ``dx`` holds the mean offset spacing."""
+    rng = rng_for(700 + tag)
+    h = (X - near) / (Nx - 1)
+    x = near + np.arange(Nx) * h
+    x[1:-1] += rng.uniform(-jitter, jitter, Nx - 2) * h
+    u = np.linspace(0.0, 1.0, Nq) if Nq > 1 else np.zeros(1)
+    q = qmin + (qmax - qmin) * u ** q_power
+    return Geometry(Nt, Nx, Ntau, Nq, dt, h, qmin, qmax, tuple(float(v) for v in x),
+                    tuple(float(v) for v in q))
