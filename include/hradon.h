@@ -130,6 +130,27 @@ radon_status radon_plan_create(radon_plan* out, int Nt, int Nx, int Ntau, int Nq
  */
 radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* d);
 
+/*
+ * Plan on unequally spaced offsets and/or slownesses (Section 4: the
+ * log-polar method carries over to unequally spaced grids; the gridding
+ * takes every sample at its own position). x: d->Nx offsets in km, strictly
+ * increasing, x[0] >= 0 (the largest is X of Eq. (12)), in place of k * dx;
+ * q: d->Nq slownesses in s/km, strictly increasing, q[0] >= 0, in place of
+ * the regular grid from qmin to qmax. Host arrays, copied; either may be
+ * NULL (the descriptor's regular grid); time and intercept time stay
+ * regular. d->dx, d->qmin and d->qmax must still pass the descriptor checks;
+ * with q given the plan's descriptor (radon_plan_desc) reports
+ * qmin = q[0] and qmax = q[Nq-1]. The gridding weight of sample (t_j, x_k)
+ * takes the trapezoid weight of x_k among the given offsets, and the lattice
+ * spacing of Eq. (18) is taken over equally spaced offsets of the same range
+ * [x_0, X] (the largest gap would coarsen the lattice). The adjoint is the
+ * exact transpose as before; radon_mute applies its line to the given
+ * slownesses. Errors as radon_plan_create_ex, plus RADON_ERR_INVALID_ARG for
+ * offsets or slownesses that are not finite, negative or not strictly
+ * increasing, given offsets with Nx < 2, or a single given slowness <= 0.
+ */
+radon_status radon_plan_create_grid(radon_plan* out, const radon_desc* d, const double* x, const double* q);
+
 /* Release everything the plan owns. NULL is accepted. Synchronises the plan's device. */
 radon_status radon_plan_destroy(radon_plan p);
 
@@ -222,6 +243,11 @@ typedef struct radon_batch_s* radon_batch;
 #define RADON_IN_F32 0
 #define RADON_IN_BF16 1
 radon_status radon_batch_create(radon_batch* out, int n, const radon_desc* descs);
+/* As radon_batch_create on given grids: x[i] / q[i] are gather i's offsets /
+ * slownesses as in radon_plan_create_grid (x or q itself, or any entry, may
+ * be NULL: the regular grid). */
+radon_status radon_batch_create_grid(radon_batch* out, int n, const radon_desc* descs, const double* const* x,
+                                     const double* const* q);
 radon_status radon_batch_destroy(radon_batch b);
 radon_status radon_batch_layout(radon_batch b, int* n, long long* f_offsets, long long* g_offsets);
 radon_status radon_batch_plan(radon_batch b, int i, radon_desc* d);
@@ -271,7 +297,8 @@ radon_status radon_opnorm(radon_plan p, const float* v0, int iters, float* norm2
  * outputs (tau_i, q_l) on one side of the line q = q0 + slope * tau set to
  * zero. side RADON_KEEP_BELOW zeroes q > q0 + slope tau (keeps the
  * primaries, smaller slowness), RADON_KEEP_ABOVE zeroes q <= q0 + slope tau
- * (keeps the multiples). g, out: [Nq][Ntau] device FP32 (may be the same
+ * (keeps the multiples); q_l is the plan's slowness grid (regular or given),
+ * the comparison in FP64. g, out: [Nq][Ntau] device FP32 (may be the same
  * buffer). Asynchronous on `stream`.
  */
 #define RADON_KEEP_BELOW 0

@@ -47,14 +47,17 @@ class Plan:
     ``[qmin, qmax]``; method parameters ``sigma``, ``omega_c``, ``tsplit``
     (split points of Eq. (19) as fractions of T), ``n_qsplit``;
     ``rows_per_band`` (1..4, or 0 to time them at plan creation; the plan's
-    ``desc.rows_per_band`` reports the value in use).
+    ``desc.rows_per_band`` reports the value in use). Unequally spaced grids
+    (``radon_plan_create_grid``): ``x`` gives the Nx offsets (km) in place of
+    ``k*dx``, ``q`` the Nq slownesses (s/km) in place of the regular grid.
     """
 
     def __init__(self, Nt: int, Nx: int, Ntau: int, Nq: int, dt: float, dx: float,
                  qmin: float = 0.0, qmax: float = 1.0, *, tau0: float = 0.0, dtau: float = 0.0,
                  sigma: float | None = None, omega_c: float | None = None,
                  tsplit: Sequence[float] | None = None, n_qsplit: int = 1,
-                 rows_per_band: int | None = None, device: int | torch.device | None = None):
+                 rows_per_band: int | None = None, device: int | torch.device | None = None,
+                 x: Sequence[float] | None = None, q: Sequence[float] | None = None):
         lib = _lib.load()
         d = RadonDesc()
         _lib.check(lib.radon_desc_init(ctypes.byref(d), Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax))
@@ -80,7 +83,8 @@ class Plan:
         d.device = dev
         self.device = torch.device("cuda", dev)
         self._handle = ctypes.c_void_p()
-        _lib.check(lib.radon_plan_create_ex(ctypes.byref(self._handle), ctypes.byref(d)))
+        xa, qa = _grid_array(x, Nx, "x"), _grid_array(q, Nq, "q")
+        _lib.check(lib.radon_plan_create_grid(ctypes.byref(self._handle), ctypes.byref(d), xa, qa))
         out = RadonDesc()
         _lib.check(lib.radon_plan_desc(self._handle, ctypes.byref(out)))
         self.desc = out
@@ -237,6 +241,16 @@ class Plan:
         return f_out, g
 
 
+def _grid_array(v, n, name):
+    """A given offset / slowness list as a C double array (None: regular)."""
+    if v is None:
+        return None
+    vals = [float(a) for a in v]
+    if len(vals) != n:
+        raise ValueError(f"{name} has {len(vals)} values, expected {n}")
+    return (ctypes.c_double * n)(*vals)
+
+
 def _desc(Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax, tau0=0.0, dtau=0.0, sigma=None, omega_c=None,
           tsplit=None, n_qsplit=1, rows_per_band=None, device=0) -> RadonDesc:
     d = RadonDesc()
@@ -266,7 +280,8 @@ class Batch:
     ``Nx``, ``Ntau``, ``Nq``, ``dt``, ``dx``, ``qmin``, ``qmax`` and
     optionally ``tau0``, ``dtau``, ``sigma``, ``omega_c``, ``tsplit``,
     ``n_qsplit``, ``rows_per_band``; 0 in every geometry times the feasible
-    values over the whole batch). Data are packed back to back (``f_offsets``,
+    values over the whole batch; ``x`` / ``q``: given offsets / slownesses as
+    in ``Plan``). Data are packed back to back (``f_offsets``,
     ``g_offsets``): gather i is ``f[f_offsets[i]:f_offsets[i+1]]`` viewed as
     [Nx][Nt]; ``forward`` accepts float32 or bfloat16 gathers."""
 
@@ -275,9 +290,15 @@ class Batch:
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = torch.device("cuda", dev)
         n = len(geometries)
-        arr = (RadonDesc * n)(*[_desc(device=dev, **g) for g in geometries])
+        base = [{k: v for k, v in g.items() if k not in ("x", "q")} for g in geometries]
+        arr = (RadonDesc * n)(*[_desc(device=dev, **g) for g in base])
+        xs = [_grid_array(g.get("x"), g["Nx"], "x") for g in geometries]
+        qs = [_grid_array(g.get("q"), g["Nq"], "q") for g in geometries]
+        dp = ctypes.POINTER(ctypes.c_double)
+        xp = (dp * n)(*[ctypes.cast(a, dp) if a is not None else dp() for a in xs])
+        qp = (dp * n)(*[ctypes.cast(a, dp) if a is not None else dp() for a in qs])
         self._handle = ctypes.c_void_p()
-        _lib.check(lib.radon_batch_create(ctypes.byref(self._handle), n, arr))
+        _lib.check(lib.radon_batch_create_grid(ctypes.byref(self._handle), n, arr, xp, qp))
         fo = (ctypes.c_longlong * (n + 1))()
         go = (ctypes.c_longlong * (n + 1))()
         _lib.check(lib.radon_batch_layout(self._handle, None, fo, go))

@@ -39,6 +39,8 @@ SIGNATURES = {
     "radon_plan_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _c_int,
                                    _c_double, _c_double, _c_double]),
     "radon_plan_create_ex": (_c_int, [ctypes.POINTER(_vp), ctypes.POINTER(RadonDesc)]),
+    "radon_plan_create_grid": (_c_int, [ctypes.POINTER(_vp), ctypes.POINTER(RadonDesc),
+                                        ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)]),
     "radon_plan_destroy": (_c_int, [_vp]),
     "radon_fwd": (_c_int, [_vp, _vp, _vp, _vp]),
     "radon_adj": (_c_int, [_vp, _vp, _vp, _vp]),
@@ -49,6 +51,9 @@ SIGNATURES = {
                                 ctypes.POINTER(RadonPieceInfo), _c_int]),
     "radon_plan_device_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "radon_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(RadonDesc)]),
+    "radon_batch_create_grid": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(RadonDesc),
+                                         ctypes.POINTER(ctypes.POINTER(_c_double)),
+                                         ctypes.POINTER(ctypes.POINTER(_c_double))]),
     "radon_batch_destroy": (_c_int, [_vp]),
     "radon_batch_layout": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(ctypes.c_longlong)]),

@@ -8,6 +8,9 @@
 #include "hostdev.h"
 
 struct radon_plan_s;  // defined in plan.cpp
+// The plan's given slownesses on its device ([Nq], s/km), or NULL when it
+// samples the regular slowness grid of its descriptor.
+const double* plan_q_values(const radon_plan_s* p);
 
 namespace hr {
 
@@ -30,7 +33,8 @@ struct __align__(8) RadonEnt { int n0; float fr; };
 struct TableArgs {
     double a, ca, sa, O1, O2, alpha;
     double theta0, dtheta, rho0, drho, a_r, r_max;
-    double n_t, n_x, T, tau0, dtau;
+    double n_t, T, tau0, dtau;
+    const double* xb;       // [Nx] rescaled offsets x_k / X (device)
     int jt_lo, nj, Nx, Ntheta, Nrho, Ntau, ncol;
 };
 

@@ -829,7 +829,7 @@ __global__ void k_sample_table(TableArgs A, const double* __restrict__ cj, const
     const int k = (int)(idx / A.nj);
     const int jl = (int)(idx - (long)k * A.nj);
     const int j = A.jt_lo + jl;
-    const double tb = j / A.n_t, xb = k / A.n_x;
+    const double tb = j / A.n_t, xb = A.xb[k];
     const double ds = tb * tb - 0.5, dy = xb * xb - 0.5;
     const double u1 = A.a * (A.ca * ds - A.sa * dy) + A.O1;
     const double u2 = A.a * (A.sa * ds + A.ca * dy) + A.O2;

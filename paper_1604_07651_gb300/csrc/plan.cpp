@@ -98,7 +98,56 @@ double t_window(const std::vector<double>& bs, int p, double tb) {
     return lo - hi;
 }
 
-std::vector<double> q_grid(const radon_desc& d) {
+// Offsets of the gather and slownesses of the output: the descriptor's
+// regular grids (empty vectors) or given lists (unequally spaced grids,
+// Section 4); time and intercept time stay regular.
+struct Grid {
+    std::vector<double> x;   // [Nx] offsets, km, strictly increasing, x[0] >= 0
+    std::vector<double> q;   // [Nq] slownesses, s/km, strictly increasing, q[0] >= 0
+};
+
+// X of the rescaling Eq. (12): the largest offset.
+double offset_X(const radon_desc& d, const Grid& g) { return g.x.empty() ? (d.Nx - 1) * d.dx : g.x.back(); }
+
+// Rescaled offsets x_k / X.
+std::vector<double> offsets_bar(const radon_desc& d, const Grid& g) {
+    std::vector<double> xb(d.Nx);
+    const double n_x = d.Nx - 1;
+    for (int k = 0; k < d.Nx; ++k) xb[k] = g.x.empty() ? k / n_x : g.x[k] / g.x.back();
+    return xb;
+}
+
+// Rescaled offsets the lattice spacing of Eq. (18) is taken over: on given
+// offsets, equally spaced ones over the same range [x_0, X] (the gridding
+// treats the samples as a quadrature, so the lattice resolves the band of
+// the data, which the mean spacing sets; the largest gap would coarsen it).
+std::vector<double> spacing_offsets_bar(const radon_desc& d, const Grid& g) {
+    if (g.x.empty()) return offsets_bar(d, g);
+    std::vector<double> xb(d.Nx);
+    const double X = g.x.back(), x0 = g.x[0];
+    for (int k = 0; k < d.Nx; ++k) xb[k] = (x0 + k * ((X - x0) / (d.Nx - 1))) / X;
+    return xb;
+}
+
+// Trapezoid weights of the offsets in units of 1/(Nx - 1) of the rescaled
+// range: 1/2 at the ends and 1 inside on the regular grid.
+std::vector<double> offset_weights(const radon_desc& d, const Grid& g) {
+    std::vector<double> w(d.Nx);
+    if (g.x.empty()) {
+        for (int k = 0; k < d.Nx; ++k) w[k] = (k == 0 || k == d.Nx - 1) ? 0.5 : 1.0;
+        return w;
+    }
+    const std::vector<double> xb = offsets_bar(d, g);
+    const double n_x = d.Nx - 1;
+    for (int k = 0; k < d.Nx; ++k) {
+        const double lo = xb[k > 0 ? k - 1 : 0], hi = xb[k < d.Nx - 1 ? k + 1 : d.Nx - 1];
+        w[k] = 0.5 * (hi - lo) * n_x;
+    }
+    return w;
+}
+
+std::vector<double> q_grid(const radon_desc& d, const Grid& g) {
+    if (!g.q.empty()) return g.q;
     std::vector<double> q(d.Nq);
     if (d.Nq == 1) {
         q[0] = d.qmin;
@@ -109,9 +158,9 @@ std::vector<double> q_grid(const radon_desc& d) {
     return q;
 }
 
-std::vector<std::pair<int, int>> slowness_pieces(const radon_desc& d) {
-    const double T = (d.Nt - 1) * d.dt, X = (d.Nx - 1) * d.dx;
-    std::vector<double> q = q_grid(d);
+std::vector<std::pair<int, int>> slowness_pieces(const radon_desc& d, const Grid& g) {
+    const double T = (d.Nt - 1) * d.dt, X = offset_X(d, g);
+    std::vector<double> q = q_grid(d, g);
     int n = std::max(1, d.n_qsplit);
     if (n == 1 || d.Nq < 2) return {{0, d.Nq - 1}};
     std::vector<double> psi(d.Nq);
@@ -202,6 +251,8 @@ static void set_rows(HostPiece& h, int R) {
 
 struct radon_plan_s {
     radon_desc d{};
+    Grid grid;                                   // given offsets / slownesses (empty: regular)
+    const double* q_dev = nullptr;               // [Nq] given slownesses on the device (mute)
     int device = 0;
     std::vector<HostPiece> pieces;               // slowness-piece major
     std::vector<std::pair<int, int>> qpieces;    // columns of each slowness piece
@@ -325,11 +376,12 @@ std::vector<std::pair<double, double>> clip_region(double s0, double s1, double 
 
 // FP64 geometry of one sub-problem (same definitions as the paper's
 // Sections 2.1, 2.2 and 4; readings documented with the descriptor).
-radon_status make_geometry(const radon_desc& d, const TPiece& tp, std::pair<int, int> lq,
+radon_status make_geometry(const radon_desc& d, const Grid& g, const TPiece& tp, std::pair<int, int> lq,
                            HostPiece& h, std::vector<double>& phi_all) {
-    const double n_t = d.Nt - 1, n_x = d.Nx - 1;
-    const double T = n_t * d.dt, X = n_x * d.dx;
-    const std::vector<double> q = q_grid(d);
+    const double n_t = d.Nt - 1;
+    const double T = n_t * d.dt, X = offset_X(d, g);
+    const std::vector<double> q = q_grid(d, g);
+    const std::vector<double> xbar = offsets_bar(d, g);
     h.tpiece = tp.idx;
     h.jt_lo = tp.lo;
     h.jt_hi = tp.hi;
@@ -362,7 +414,7 @@ radon_status make_geometry(const radon_desc& d, const TPiece& tp, std::pair<int,
     h.k2 = qb0 * qb0;
     h.jfirst.assign(d.Nx, tp.hi + 1);
     for (int k = 0; k < d.Nx; ++k) {
-        const double xb = k / n_x;
+        const double xb = xbar[k];
         const double lim = h.c_min + h.k2 * (xb * xb);
         for (int j = tp.lo; j <= tp.hi; ++j) {
             const double tb = j / n_t;
@@ -390,13 +442,15 @@ radon_status make_geometry(const radon_desc& d, const TPiece& tp, std::pair<int,
     if (!(ar > 0)) return fail(RADON_ERR_INVALID_ARG, "degenerate log-polar setup (inner radius <= 0)");
     h.a_r = ar;
     h.r_max = rmax;
-    // Spacing of Eq. (18) over every sample of the time piece.
+    // Spacing of Eq. (18) over every sample of the time piece (given offsets:
+    // over equally spaced offsets of the same range).
+    const std::vector<double> xsp = spacing_offsets_bar(d, g);
     const int nj = tp.hi - tp.lo + 1;
     phi_all.assign((size_t)nj * d.Nx, 0.0);
     std::vector<double> eta_prev(nj), eta_cur(nj);
     double dphi = 0.0, deta = 0.0;
     for (int k = 0; k < d.Nx; ++k) {
-        const double xb = k / n_x;
+        const double xb = xsp[k];
         const double y = xb * xb;
         double* ph = &phi_all[(size_t)k * nj];
         for (int jj = 0; jj < nj; ++jj) {
@@ -600,7 +654,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
                                 const std::vector<double>& phi_all, int smem_max) {
     const radon_desc& d = p->d;
     const double n_t = d.Nt - 1, n_x = d.Nx - 1;
-    const double T = n_t * d.dt, X = n_x * d.dx;
+    const double T = n_t * d.dt, X = offset_X(d, p->grid);
     PieceDev& P = h.dev;
     P.Ntheta = h.Ntheta;
     P.Nrho = h.Nrho;
@@ -650,9 +704,9 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
         const double w = t_window(bs, h.tpiece, tb);
         cj[jl] = w * 2.0 * h.a * h.a * tb / (n_t * n_x * h.dtheta * h.drho);
     }
-    for (int k = 0; k < d.Nx; ++k) wk[k] = (k == 0 || k == d.Nx - 1) ? 0.5 : 1.0;
+    wk = offset_weights(d, p->grid);
     // output columns: theta taps, scale, e^rho polynomial; band column ranges
-    const std::vector<double> q = q_grid(d);
+    const std::vector<double> q = q_grid(d, p->grid);
     const int ncol = h.l_hi - h.l_lo + 1;
     std::vector<float4> colw(ncol);
     std::vector<int> colm0(ncol);
@@ -727,7 +781,6 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     A.a_r = h.a_r;
     A.r_max = h.r_max;
     A.n_t = n_t;
-    A.n_x = n_x;
     A.T = T;
     A.tau0 = d.tau0;
     A.dtau = dtau;
@@ -738,12 +791,14 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     A.Nrho = h.Nrho;
     A.Ntau = d.Ntau;
     A.ncol = ncol;
-    const double *dcj = nullptr, *dwk = nullptr, *dqb2 = nullptr;
+    const double *dcj = nullptr, *dwk = nullptr, *dqb2 = nullptr, *dxb = nullptr;
     const int* djf = nullptr;
     void* tab = nullptr;
     if ((s = dev_upload(p, cj, &dcj)) || (s = dev_upload(p, wk, &dwk)) ||
-        (s = dev_upload(p, h.jfirst, &djf)) || (s = dev_upload(p, qb2, &dqb2)))
+        (s = dev_upload(p, h.jfirst, &djf)) || (s = dev_upload(p, qb2, &dqb2)) ||
+        (s = dev_upload(p, offsets_bar(d, p->grid), &dxb)))
         return s;
+    A.xb = dxb;
     if ((s = dev_alloc(p, (size_t)P.nj * d.Nx * sizeof(SampleEnt), &tab))) return s;
     P.stab = (const SampleEnt*)tab;
     if (int e = launch_sample_table(A, dcj, dwk, djf, (SampleEnt*)tab))
@@ -883,13 +938,41 @@ extern "C" radon_status radon_plan_create(radon_plan* out, int Nt, int Nx, int N
 // Geometry, tables and kernel spectra of every piece of a plan; no work
 // buffers and no gather maps (a single plan and a batch lay those out
 // differently).
-static radon_status plan_core(const radon_desc* din, radon_plan_s** out) {
+// Given offsets / slownesses (NULL: the regular grid): finite, strictly
+// increasing, non-negative; copied into g.
+static radon_status check_grid(const radon_desc& d, const double* x, const double* q, Grid& g) {
+    g = Grid{};
+    if (x) {
+        if (d.Nx < 2) return fail(RADON_ERR_INVALID_ARG, "given offsets need Nx >= 2");
+        for (int k = 0; k < d.Nx; ++k)
+            if (!std::isfinite(x[k]) || (k == 0 ? !(x[0] >= 0) : !(x[k] > x[k - 1])))
+                return fail(RADON_ERR_INVALID_ARG, "offsets must be finite, >= 0 and strictly increasing");
+        g.x.assign(x, x + d.Nx);
+    }
+    if (q) {
+        for (int l = 0; l < d.Nq; ++l)
+            if (!std::isfinite(q[l]) || (l == 0 ? !(q[0] >= 0) : !(q[l] > q[l - 1])))
+                return fail(RADON_ERR_INVALID_ARG, "slownesses must be finite, >= 0 and strictly increasing");
+        if (d.Nq == 1 && !(q[0] > 0)) return fail(RADON_ERR_INVALID_ARG, "a single slowness must be > 0");
+        g.q.assign(q, q + d.Nq);
+    }
+    return RADON_OK;
+}
+
+static radon_status plan_core(const radon_desc* din, const double* x, const double* q, radon_plan_s** out) {
     *out = nullptr;
     if (radon_status s = check_desc(din)) return s;
+    Grid grid;
+    if (radon_status s = check_grid(*din, x, q, grid)) return s;
     radon_plan_s* p = new (std::nothrow) radon_plan_s();
     if (!p) return fail(RADON_ERR_OOM, "host allocation failed");
     p->d = *din;
+    p->grid = std::move(grid);
     radon_desc& d = p->d;
+    if (!p->grid.q.empty()) {            // the descriptor reports the given range
+        d.qmin = p->grid.q.front();
+        d.qmax = p->grid.q.back();
+    }
     if (d.dtau <= 0) d.dtau = (d.Nt - 1) * d.dt / (d.Ntau - 1);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -910,13 +993,13 @@ static radon_status plan_core(const radon_desc* din, radon_plan_s** out) {
     const int smem_max = max_smem_optin();
     const std::vector<double> bs = accepted_splits(d);
     const std::vector<TPiece> tps = time_pieces(d, bs);
-    p->qpieces = slowness_pieces(d);
+    p->qpieces = slowness_pieces(d, p->grid);
     std::vector<double> phi_all;
     for (auto& lq : p->qpieces) {
         p->qfirst.push_back((int)p->pieces.size());
         for (auto& tp : tps) {
             HostPiece h;
-            radon_status s = make_geometry(d, tp, lq, h, phi_all);
+            radon_status s = make_geometry(d, p->grid, tp, lq, h, phi_all);
             if (s == RADON_OK) s = build_piece_tables(p, h, bs, phi_all, smem_max);
             if (s != RADON_OK) {
                 destroy_plan(p);
@@ -927,6 +1010,12 @@ static radon_status plan_core(const radon_desc* din, radon_plan_s** out) {
         p->qcount.push_back((int)tps.size());
     }
     for (auto& h : p->pieces) p->nrho_max = std::max(p->nrho_max, h.dev.Nrho);
+    if (!p->grid.q.empty()) {
+        if (radon_status s = dev_upload(p, p->grid.q, &p->q_dev)) {
+            destroy_plan(p);
+            return s;
+        }
+    }
     *out = p;
     return RADON_OK;
 }
@@ -964,10 +1053,15 @@ static int tune_rows(int rmax, Run&& run, void* stream) {
 }
 
 extern "C" radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* din) {
+    return radon_plan_create_grid(out, din, nullptr, nullptr);
+}
+
+extern "C" radon_status radon_plan_create_grid(radon_plan* out, const radon_desc* din, const double* x,
+                                               const double* q) {
     if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     radon_plan_s* p = nullptr;
-    if (radon_status s = plan_core(din, &p)) return s;
+    if (radon_status s = plan_core(din, x, q, &p)) return s;
     DeviceGuard guard(p->device);
     // per-piece work buffers: lattices back to back (one clear per forward),
     // spectra (the column pass works in place), adjoint column profiles
@@ -1220,16 +1314,19 @@ extern "C" radon_status radon_geometry(const radon_desc* din, int* npieces, rado
     const std::vector<TPiece> tps = time_pieces(d, bs);
     std::vector<double> phi_all;
     int n = 0;
-    for (auto& lq : slowness_pieces(d))
+    const Grid g;
+    for (auto& lq : slowness_pieces(d, g))
         for (auto& tp : tps) {
             HostPiece h;
-            if (radon_status s = make_geometry(d, tp, lq, h, phi_all)) return s;
+            if (radon_status s = make_geometry(d, g, tp, lq, h, phi_all)) return s;
             if (infos && n < max_infos) fill_info(h, infos + n);
             ++n;
         }
     *npieces = n;
     return RADON_OK;
 }
+
+const double* plan_q_values(const radon_plan_s* p) { return p ? p->q_dev : nullptr; }
 
 extern "C" radon_status radon_plan_desc(radon_plan p, radon_desc* d) {
     if (!p || !d) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
@@ -1337,6 +1434,11 @@ static void destroy_batch(radon_batch_s* b) {
 }
 
 extern "C" radon_status radon_batch_create(radon_batch* out, int n, const radon_desc* descs) {
+    return radon_batch_create_grid(out, n, descs, nullptr, nullptr);
+}
+
+extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const radon_desc* descs,
+                                                const double* const* x, const double* const* q) {
     if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || !descs) return fail(RADON_ERR_INVALID_ARG, "a batch needs n >= 1 descriptors");
@@ -1366,7 +1468,7 @@ extern "C" radon_status radon_batch_create(radon_batch* out, int n, const radon_
             radon_desc d = descs[i];
             d.device = b->device;
             radon_plan_s* p = nullptr;
-            if (radon_status s = plan_core(&d, &p)) {
+            if (radon_status s = plan_core(&d, x ? x[i] : nullptr, q ? q[i] : nullptr, &p)) {
                 std::lock_guard<std::mutex> lock(err_mutex);
                 if (first_err == RADON_OK) {
                     first_err = s;

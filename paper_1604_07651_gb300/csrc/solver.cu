@@ -105,12 +105,12 @@ __global__ void __launch_bounds__(kThreads) k_normalize(const float* __restrict_
 // plane: side 0 zeroes q > q0 + slope tau (keeps the primaries), side 1
 // zeroes q <= q0 + slope tau (keeps the multiples). src may alias dst.
 __global__ void __launch_bounds__(kThreads) k_mute(const float* src, float* dst, int Ntau, long n, double tau0,
-                                                  double dtau, double qmin, double dq, double q0, double slope,
-                                                  int side) {
+                                                  double dtau, double qmin, double dq, const double* qv,
+                                                  double q0, double slope, int side) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const long l = i / Ntau;
         const double tau = tau0 + dtau * (double)(i - l * Ntau);
-        const double q = qmin + dq * (double)l;
+        const double q = qv ? qv[l] : qmin + dq * (double)l;
         const bool above = q > q0 + slope * tau;
         dst[i] = (above == (side == 0)) ? 0.f : src[i];
     }
@@ -247,7 +247,7 @@ extern "C" radon_status radon_mute(radon_plan p, const float* g, float* out, dou
     radon_plan_desc(p, &d);
     const long ni = (long)d.Nq * d.Ntau;
     k_mute<<<grid_for(ni), kThreads, 0, (cudaStream_t)stream>>>(g, out, d.Ntau, ni, d.tau0, d.dtau, d.qmin, q_step(d),
-                                                                 q0, slope, side);
+                                                                 plan_q_values(p), q0, slope, side);
     if (int e = last_cuda()) return cuda_fail(e, "mute");
     return RADON_OK;
 }

@@ -57,6 +57,18 @@ def test_host_side_argument_checks(lib):
         assert L.radon_last_error().decode()
         assert not h.value
     assert L.radon_plan_create_ex(ctypes.byref(h), None) == 1
+    # given offsets / slownesses: checked on the host as well
+    x = [0.025 * k for k in range(64)]
+    q = [0.2 + 0.5 * l / 63 for l in range(64)]
+    arr = lambda v: (ctypes.c_double * len(v))(*v)
+    for bx, bq in [(x[:5] + [x[3]] + x[6:], None), ([-0.01] + x[1:], None), (x[:9] + [float("inf")] + x[10:], None),
+                   (None, q[::-1]), (None, [q[0]] + q[:-1])]:
+        rc = L.radon_plan_create_grid(ctypes.byref(h), ctypes.byref(d), arr(bx) if bx else None,
+                                      arr(bq) if bq else None)
+        assert rc == 1 and not h.value and L.radon_last_error().decode()
+    one = _lib.RadonDesc.from_buffer_copy(d)
+    one.Nx = 1
+    assert L.radon_plan_create_grid(ctypes.byref(h), ctypes.byref(one), arr([0.5]), None) == 1
     assert L.radon_plan_destroy(None) == 0
     assert L.radon_fwd(None, None, None, None) == 1
     assert L.radon_adj(None, None, None, None) == 1
