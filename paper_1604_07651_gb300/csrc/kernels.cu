@@ -268,17 +268,62 @@ __device__ __forceinline__ float block_max_abs(float v, float* red) {
 // largest total B-spline weight one of its cells can collect. A CTA takes one
 // unit, each thread one chunk: neighbouring threads are 8 samples apart, so
 // their footprints rarely meet, and a thread sums its samples in registers
-// while their first tap (m0, n0) stays the same, adding to the fixed-point
-// shared tile only when it moves. The tile's touched cells are then added to
-// P.lat. A non-finite sample makes the unit's tile NaN (the FFTs that follow
-// would spread it over the whole piece in any case).
-__device__ __forceinline__ void flush_tile(int mn, int m_lo, int n_lo, int* tile, const float acc[16]) {
-    if (mn < 0) return;
-    int* t = tile + ((mn >> 16) - m_lo + kHalo) * kTilePitch + (mn & 0xffff) - n_lo + kHalo;
+// in a 4x4 register window over the cells of its current footprint. When the
+// first tap (m0, n0) moves by one cell along either axis (consecutive samples
+// of a trace mostly do), only the row or column that leaves the window goes
+// to the fixed-point shared tile and the window slides; a longer jump flushes
+// the whole window. The tile's touched cells are then added to P.lat. A
+// non-finite sample makes the unit's tile NaN (the FFTs that follow would
+// spread it over the whole piece in any case).
+// The window acc[4 a + c] holds cells (wm + a, wn + c); t points at (wm, wn)
+// in the shared tile.
+__device__ __forceinline__ void flush_window(int* t, const float acc[16]) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) red_fixed(t + a * kTilePitch + c, acc[4 * a + c]);
+}
+// window one row down (row wm leaves) / up (row wm + 3 leaves)
+__device__ __forceinline__ void slide_rows_down(int* t, float acc[16]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        red_fixed(t + c, acc[c]);
+        acc[c] = acc[4 + c];
+        acc[4 + c] = acc[8 + c];
+        acc[8 + c] = acc[12 + c];
+        acc[12 + c] = 0.f;
+    }
+}
+__device__ __forceinline__ void slide_rows_up(int* t, float acc[16]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        red_fixed(t + 3 * kTilePitch + c, acc[12 + c]);
+        acc[12 + c] = acc[8 + c];
+        acc[8 + c] = acc[4 + c];
+        acc[4 + c] = acc[c];
+        acc[c] = 0.f;
+    }
+}
+// window one column right (column wn leaves) / left (column wn + 3 leaves)
+__device__ __forceinline__ void slide_cols_right(int* t, float acc[16]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        red_fixed(t + a * kTilePitch, acc[4 * a]);
+        acc[4 * a] = acc[4 * a + 1];
+        acc[4 * a + 1] = acc[4 * a + 2];
+        acc[4 * a + 2] = acc[4 * a + 3];
+        acc[4 * a + 3] = 0.f;
+    }
+}
+__device__ __forceinline__ void slide_cols_left(int* t, float acc[16]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        red_fixed(t + a * kTilePitch + 3, acc[4 * a + 3]);
+        acc[4 * a + 3] = acc[4 * a + 2];
+        acc[4 * a + 2] = acc[4 * a + 1];
+        acc[4 * a + 1] = acc[4 * a];
+        acc[4 * a] = 0.f;
+    }
 }
 
 template <class Src, class T>
@@ -336,17 +381,30 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
     float acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-    int cur = -1;
+    int* win = nullptr;                                  // shared-tile address of the window's (wm, wn)
+    int wm = 0, wn = 0;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
         const int4 e = ent[s];
         if (v[s] == 0.f) continue;
-        if (e.x != cur) {
-            flush_tile(cur, m_lo, n_lo, tile, acc);
+        const int m0 = e.x >> 16, n0 = e.x & 0xffff;
+        const int dm = m0 - wm, dn = n0 - wn;
+        if (win == nullptr || dm < -1 || dm > 1 || dn < -1 || dn > 1) {
+            if (win != nullptr) {
+                flush_window(win, acc);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-            cur = e.x;
+                for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+            }
+        } else {
+            if (dm == 1) slide_rows_down(win, acc);
+            else if (dm == -1) slide_rows_up(win, acc);
+            win += dm * kTilePitch;
+            if (dn == 1) slide_cols_right(win, acc);
+            else if (dn == -1) slide_cols_left(win, acc);
         }
+        wm = m0;
+        wn = n0;
+        win = tile + (m0 - m_lo + kHalo) * kTilePitch + n0 - n_lo + kHalo;
         float wt[4], wr[4];
         b3_weights(__int_as_float(e.y), wt);
         b3_weights(__int_as_float(e.z), wr);
@@ -357,7 +415,7 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
             for (int q = 0; q < 4; ++q) acc[4 * a + q] = fmaf(va, wr[q], acc[4 * a + q]);
         }
     }
-    flush_tile(cur, m_lo, n_lo, tile, acc);
+    if (win != nullptr) flush_window(win, acc);
     __syncthreads();
     for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
         const int m = i / kTileCols, n = i - m * kTileCols;
