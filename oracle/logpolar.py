@@ -197,11 +197,14 @@ class Partition:
 
 
 def fft_size(n: int) -> int:
-    """Smallest size >= n of the form 2^a, 3*2^a or 5*2^a (a >= 0)."""
+    """Smallest size >= n of the form 2^a, 3*2^a, 5*2^a (a >= 0) or 9*2^a
+    (1 <= a <= 8). Reading: the paper fixes no FFT length beyond the padding
+    the kernel window needs; any length at or above it gives the same linear
+    convolution, and the frequency rectangle L is fixed in cycles per cell."""
     best = None
     p = 1
     while p < 2 * n + 2:
-        for c in (p, 3 * p, 5 * p):
+        for c in (p, 3 * p, 5 * p) + ((9 * p,) if 2 <= p <= 256 else ()):
             if c >= n and (best is None or c < best):
                 best = c
         p *= 2

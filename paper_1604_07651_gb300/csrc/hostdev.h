@@ -148,6 +148,39 @@ HD void dft_small<6>(cf v[6], int dir) { dft_3xF<2>(v, dir); }
 template <>
 HD void dft_small<12>(cf v[12], int dir) { dft_3xF<4>(v, dir); }
 
+// exp(dir * 2 pi i m / 9) for m = 1, 2, 4, the twiddles of the 3 x 3 split
+// (cos and sin of 40, 80 and 160 degrees).
+HD cf root9(int m, int dir) {
+    switch (m) {
+        case 1: return {0.76604444311897803520f, dir * 0.64278760968653932632f};
+        case 2: return {0.17364817766693034885f, dir * 0.98480775301220805936f};
+        default: return {-0.93969262078590838405f, dir * 0.34202014332566873304f};
+    }
+}
+
+// Size 9 as 3 x 3 (Cooley-Tukey with n = 3 n1 + n2, k = k1 + 3 k2):
+// Y[n2][k1] = DFT3 over n1 of x[3 n1 + n2], times W9^(n2 k1), then
+// X[k1 + 3 k2] = DFT3 over n2.
+template <>
+HD void dft_small<9>(cf v[9], int dir) {
+    cf y[3][3];
+HD_UNROLL
+    for (int n2 = 0; n2 < 3; ++n2) {
+HD_UNROLL
+        for (int n1 = 0; n1 < 3; ++n1) y[n2][n1] = v[3 * n1 + n2];
+        dft_small<3>(y[n2], dir);
+    }
+HD_UNROLL
+    for (int k1 = 0; k1 < 3; ++k1) {
+        cf z[3];
+HD_UNROLL
+        for (int n2 = 0; n2 < 3; ++n2) z[n2] = (n2 * k1 != 0) ? cmul(y[n2][k1], root9(n2 * k1, dir)) : y[n2][k1];
+        dft_small<3>(z, dir);
+HD_UNROLL
+        for (int k2 = 0; k2 < 3; ++k2) v[k1 + 3 * k2] = z[k2];
+    }
+}
+
 // Size 5 directly: with t1 = x1 + x4, t2 = x2 + x3, t3 = x1 - x4,
 // t4 = x2 - x3 and c_m = cos(2 pi m / 5), s_m = sin(2 pi m / 5):
 // X1,4 = x0 + c1 t1 + c2 t2 +- i dir (s1 t3 + s2 t4),
@@ -298,15 +331,18 @@ HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int lgNs, int j
     stockham_store<R>(out, Ns, lgNs, j, dir, v);
 }
 
-// Radix plan of n = 2^a, 3 * 2^a or 5 * 2^a: radix 16 while possible, then
-// the rest r = n / 16^k in one stage when r is 2, 3, 4, 5, 6, 8, 10 or 12,
-// else radix 4 then 6 (r = 24), radix 4 then 5 (r = 20) or radix 8 then 5
-// (r = 40); the factor 3 or 5 is always in the last stage, so every stage
-// sees a power-of-two Ns. Returns the number of stages, or -1 for any other
-// n.
+// Radix plan of n = 2^a, 3 * 2^a, 5 * 2^a or 9 * 2^a (n <= 2304): radix 16
+// while possible, then the rest r = n / 16^k in one stage when r is 2, 3, 4,
+// 5, 6, 8, 9, 10 or 12, else radix 4 then 6 (r = 24), radix 4 then 5
+// (r = 20), radix 8 then 5 (r = 40) or radix 2, 4, 8 then 9 (r = 18, 36,
+// 72); the factor 3, 5 or 9 is always in the last stage, so every stage sees
+// a power-of-two Ns. Returns the number of stages, or -1 for any other n.
 HD int fft_radices(int n, int rad[32]) {
     int m = n;
-    if (m % 3 == 0) m /= 3;
+    if (m % 9 == 0) {
+        if (n > 2304) return -1;   // 9 * 2^a up to 2304 (a larger one would need radix 18)
+        m /= 9;
+    } else if (m % 3 == 0) m /= 3;
     else if (m % 5 == 0) m /= 5;
     if (m < 1 || (m & (m - 1)) != 0) return -1;
     int k = 0;
@@ -323,8 +359,11 @@ HD int fft_radices(int n, int rad[32]) {
     } else if (n == 40) {
         rad[k++] = 8;
         rad[k++] = 5;
+    } else if (n == 18 || n == 36 || n == 72) {
+        rad[k++] = n / 9;
+        rad[k++] = 9;
     } else if (n != 1) {
-        rad[k++] = n;   // 2, 3, 4, 5, 6, 8, 10 or 12
+        rad[k++] = n;   // 2, 3, 4, 5, 6, 8, 9, 10 or 12
     }
     return k;
 }
@@ -348,7 +387,7 @@ inline int fft_stage_tables(int n, cf* T) {
 // round when n / R <= threads * fft_qmax(R).
 HD int fft_qmax(int R) {
     switch (R) {
-        case 16: case 12: case 10: case 8: return 1;
+        case 16: case 12: case 10: case 9: case 8: return 1;
         case 6: case 5: case 2: return 2;
         case 4: return 3;
         default: return 4;   // 3

@@ -78,12 +78,12 @@ __device__ __forceinline__ void fft_stage(cf* buf, int n, int nrows, int Ns, int
 
 // Block-cooperative in-place FFT of `nrows` sequences of length n
 // (unnormalised; DIR = -1 forward, +1 inverse). The radix plan is radix 16
-// stages and a rest of radix 2, 3, 4, 5, 6, 8, 10 or 12 (or 4 then 6, 4
-// then 5, 8 then 5) (fft_radices); written as straight-line code so that
+// stages and a rest of radix 2, 3, 4, 5, 6, 8, 9, 10 or 12 (or 4 then 6, 4
+// then 5, 8 then 5, 2/4/8 then 9) (fft_radices); written as straight-line code so that
 // each stage keeps its own small register footprint. Q, the butterflies a
 // thread holds at once, is chosen so that a stage covers every row in one
 // round where the registers allow. Supported: every n with fft_fits(n, 512)
-// (2^a <= 4096, 3 * 2^a <= 6144, 5 * 2^a <= 5120).
+// (2^a <= 4096, 3 * 2^a <= 6144, 5 * 2^a <= 5120, 9 * 2^a <= 2304).
 // One stage with Q butterflies per thread: enough for all rows of the block
 // in one round where the register budget QMAX = fft_qmax(R) allows, and at
 // least enough for one whole sequence (fft_fits guarantees that fits).
@@ -118,6 +118,7 @@ __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* _
         const int R = fp.rad[s];
         if (R == 12) fft_stage_q<12, 1, DIR>(buf, n, nrows, Ns, lg, T);
         else if (R == 10) fft_stage_q<10, 1, DIR>(buf, n, nrows, Ns, lg, T);
+        else if (R == 9) fft_stage_q<9, 1, DIR>(buf, n, nrows, Ns, lg, T);
         else if (R == 8) fft_stage_q<8, 1, DIR>(buf, n, nrows, Ns, lg, T);
         else if (R == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, T);
         else if (R == 5) fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, T);
@@ -129,8 +130,9 @@ __device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* _
         lg = 31 - __clz(Ns);
         ++s;
     }
-    if (s < fp.nst) {   // after radix 4 or 8 (n / 16^k = 24, 20, 40): radix 6 or 5
+    if (s < fp.nst) {   // after radix 2, 4 or 8 (n / 16^k = 24, 20, 40, 18, 36, 72): radix 6, 5 or 9
         if (fp.rad[s] == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, T);
+        else if (fp.rad[s] == 9) fft_stage_q<9, 1, DIR>(buf, n, nrows, Ns, lg, T);
         else fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, T);
     }
 }

@@ -36,10 +36,13 @@ const double kPi = 3.14159265358979323846;
 const double kTOverlap = 1.25;   // half-width ratio of the time-partition transition bands
 const double kBetaMin = 1e-3;    // smallest angular opening of a sub-problem
 
+// Smallest FFT length >= n of the form 2^a, 3 * 2^a, 5 * 2^a or 9 * 2^a
+// (18 <= 9 * 2^a <= 2304, the range the block FFT and the real-FFT half
+// length handle).
 int fft_size(int n) {
     long best = -1;
     for (long p = 1; p < 2L * n + 2; p *= 2) {
-        for (long c : {p, 3 * p, 5 * p})
+        for (long c : {p, 3 * p, 5 * p, (p >= 2 && p <= 256) ? 9 * p : 0})
             if (c >= n && (best < 0 || c < best)) best = c;
     }
     return (int)best;
@@ -663,7 +666,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.k1max = h.k1max;
     P.k2max = h.k2max;
     // FFT lengths the in-place block FFT handles (512 threads): 2^a <= 4096,
-    // 3 * 2^a <= 6144, 5 * 2^a <= 5120
+    // 3 * 2^a <= 6144, 5 * 2^a <= 5120, 9 * 2^a <= 2304
     auto fft_ok = [](int n) {
         return ((n % 3 == 0) ? n <= 6144 : (n % 5 == 0) ? n <= 5120 : n <= 4096) && fft_fits(n, 512);
     };

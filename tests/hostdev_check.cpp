@@ -48,6 +48,7 @@ static std::vector<cf> fft_emul_sw(std::vector<cf> a, int dir) {
             else if (R == 12) stockham_butterfly<12>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
             else if (R == 6) stockham_butterfly<6>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
             else if (R == 10) stockham_butterfly<10>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
+            else if (R == 9) stockham_butterfly<9>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
             else if (R == 5) stockham_butterfly<5>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
             else if (R == 8) stockham_butterfly<8>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
             else if (R == 4) stockham_butterfly<4>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
@@ -152,23 +153,26 @@ static double b3_error() {
 int main() {
     std::mt19937 rng(1604);
     double e = 0;
-    for (int n : {2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512,
-                  640, 768, 1024, 1280, 1536, 2048, 2560, 3072, 4096, 5120, 6144})
+    for (int n : {2, 3, 4, 5, 6, 8, 9, 10, 12, 16, 18, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96, 128, 144, 160, 192,
+                  256, 288, 320, 384, 512, 576, 640, 768, 1024, 1152, 1280, 1536, 2048, 2304, 2560, 3072, 4096, 5120,
+                  6144})
         e = std::max(e, std::max(fft_error(n, -1, rng), fft_error(n, +1, rng)));
     std::printf("fft_rel_l2 %.3e\n", e);
     e = 0;
-    for (int P : {8, 12, 20, 48, 64, 80, 96, 768, 1024, 2560, 3072}) e = std::max(e, rfft_error(P, rng));
+    for (int P : {8, 12, 18, 20, 48, 64, 80, 96, 144, 768, 1024, 2304, 2560, 3072}) e = std::max(e, rfft_error(P, rng));
     std::printf("rfft_rel_l2 %.3e\n", e);
     e = 0;
-    for (int P : {8, 12, 20, 48, 64, 80, 96, 768, 1024, 2560, 3072}) e = std::max(e, irfft_error(P, P / 2 - 1, rng));
+    for (int P : {8, 12, 18, 20, 48, 64, 80, 96, 144, 768, 1024, 2304, 2560, 3072})
+        e = std::max(e, irfft_error(P, P / 2 - 1, rng));
     for (int P : {64, 768}) e = std::max(e, irfft_error(P, P / 5, rng));
     std::printf("irfft_rel_l2 %.3e\n", e);
     std::printf("b3_weights %.3e\n", b3_error());
     // the layout swizzle is a permutation of [0, n) for every FFT length used
-    int bad = 0;
+    int bad = 0, nlen = 0;
     for (int n = 1; n <= 6144; ++n) {
         int rad[32];
         if (fft_radices(n, rad) < 0 || (n % 3 == 0 ? n > 6144 : n % 5 == 0 ? n > 5120 : n > 4096)) continue;
+        ++nlen;
         std::vector<int> seen(n, 0);
         for (int i = 0; i < n; ++i) {
             const int p = sw(i);
@@ -176,6 +180,7 @@ int main() {
         }
     }
     std::printf("swizzle_violations %d\n", bad);
+    std::printf("fft_lengths %d\n", nlen);
     // every length within the limits fits the 512-thread block FFT
     int nofit = 0;
     for (int n = 2; n <= 6144; ++n) {

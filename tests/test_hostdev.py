@@ -37,6 +37,8 @@ def test_b3_weights(results):
 
 def test_shared_memory_swizzle_is_a_permutation(results):
     assert results["swizzle_violations"] == 0
+    # 2^a <= 4096, 3 2^a <= 6144, 5 2^a <= 5120 and 9 2^a <= 2304: 13 + 12 + 11 + 9 lengths
+    assert results["fft_lengths"] == 45
 
 
 def test_every_supported_length_fits_the_block_fft(results):
