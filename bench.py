@@ -139,14 +139,14 @@ PROFILE_EVERY = 4   # one timed step in PROFILE_EVERY records per-stage kernel e
 
 MEASURED_TRAFFIC = {
     # kernel: (sha256 prefix of csrc/kernels.cu, bytes per launch averaged over a step's launches)
-    "k_grid_tiles": ("fa1a438a9571d4a8", 127.83e6),
-    "k_rows_r2c": ("fa1a438a9571d4a8", 28.30e6),
-    "k_colconv": ("fa1a438a9571d4a8", 51.31e6),
-    "k_rows_c2r": ("fa1a438a9571d4a8", 29.37e6),
-    "k_interp_columns": ("fa1a438a9571d4a8", 130.09e6),
-    "k_col_profiles": ("fa1a438a9571d4a8", 142.45e6),
-    "k_band_rows": ("fa1a438a9571d4a8", 45.62e6),
-    "k_gather_samples": ("fa1a438a9571d4a8", 105.18e6),
+    "k_grid_tiles": ("fa1d51f8c0c844cf", 127.10e6),
+    "k_rows_r2c": ("fa1d51f8c0c844cf", 28.30e6),
+    "k_colconv": ("fa1d51f8c0c844cf", 48.03e6),
+    "k_rows_c2r": ("fa1d51f8c0c844cf", 27.51e6),
+    "k_interp_columns": ("fa1d51f8c0c844cf", 100.93e6),
+    "k_col_profiles": ("fa1d51f8c0c844cf", 107.44e6),
+    "k_band_rows": ("fa1d51f8c0c844cf", 45.62e6),
+    "k_gather_samples": ("fa1d51f8c0c844cf", 105.13e6),
 }
 
 # FFT kernels run out of shared memory and are limited by instruction issue,
@@ -482,7 +482,8 @@ def main():
         "roofline": roofline(dom, d, per_kernel, hbm, peak_kind, plan, clk.summary(), dev, len(profiled)),
         "stages": stages,
         "kernel_timing": f"per-stage CUDA events on {len(profiled)} of the {args.steps} timed steps "
-                         f"(every {PROFILE_EVERY}th, launched eagerly)",
+                         + (f"(every {PROFILE_EVERY}th" if args.steps >= PROFILE_EVERY else "(the last")
+                         + ", launched eagerly)",
         "launch": "eager" if graph is None else
                   f"CUDA graph replay of the step on {args.steps - len(profiled)} of the {args.steps} timed steps",
         "gpu_launches": launches,
