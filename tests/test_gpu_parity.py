@@ -166,6 +166,40 @@ def test_full_size_2048_against_logpolar_oracle(hr):
     assert _rel(g, g_ref) < PARITY_TOL
 
 
+# Geometries whose lattices take each radix plan of the 9 * 2^a FFT lengths:
+# (dimension, length): Nt = Ntau, Nx = Nq, dt, dx, qmin, qmax, method
+RADIX9 = {
+    ("rho", 144): (128, 128, 0.004, 1.6 / 127, 0.2, 0.7, {}),                       # half length 72 = 8 x 9
+    ("rho", 288): (192, 128, 0.004, 1.6 / 127, 0.2, 0.7, {}),                       # 144 = 16 x 9
+    ("rho", 576): (320, 256, 0.004, 1.6 / 255, 0.2, 0.7, {}),                       # 288 = 16 x 2 x 9
+    ("rho", 1152): (768, 384, 0.002, 2.0 / 383, 0.2, 0.7, {}),                      # 576 = 16 x 4 x 9
+    ("theta", 144): (128, 32, 0.004, 1.6 / 31, 0.2, 0.7, dict(nq=2)),               # 16 x 9
+    ("theta", 288): (128, 128, 0.004, 1.6 / 127, 0.2, 0.7, dict(nq=2)),             # 16 x 2 x 9
+    ("theta", 576): (128, 160, 0.004, 1.6 / 159, 0.2, 0.7, dict(nq=2)),             # 16 x 4 x 9
+    ("theta", 1152): (768, 768, 0.002, 2.0 / 767, 0.1, 0.9, dict(sigma=2.0, omega_c=0.25)),   # 16 x 8 x 9
+    ("theta", 2304): (1024, 1024, 0.002, 2.0 / 1023, 0.1, 0.7, dict(sigma=2.0, omega_c=0.25)),  # 16 x 16 x 9
+}
+
+
+@pytest.mark.parametrize("key", list(RADIX9))
+def test_radix9_fft_lengths_match_oracle(hr, key):
+    """Every radix plan of the 9 * 2^a lengths (column FFT of that length, or
+    row FFT with that half length) against the FP64 oracle, forward and
+    adjoint; the row length 2304 (half 1152 = 16 x 8 x 9) is the 2048x2048
+    workload's."""
+    dim, length = key
+    Nt, Nx, dt, dx, qmin, qmax, kw = RADIX9[key]
+    geo = synth.Geometry(Nt, Nx, Nt, Nx, dt, dx, qmin, qmax)
+    plan, desc = _pair(hr, geo, **kw)
+    assert length in [p["Ptheta" if dim == "theta" else "Prho"] for p in plan.pieces()]
+    lp = LogPolar(desc)
+    f = synth.band_limited_gather(geo, 95, n_events=6, nu=10.0)
+    g = synth.random_radon_image(geo, 96)
+    assert _rel(plan.forward(_cuda(f)).cpu().numpy(), lp.forward(f)) < PARITY_TOL
+    assert _rel(plan.adjoint(_cuda(g)).cpu().numpy(), lp.adjoint(g)) < PARITY_TOL
+    plan.close()
+
+
 def test_direct_sum_kernel_matches_oracle(hr, oracle_direct):
     geo, f = synth.single_gather(1)
     g = hr.direct_forward(_cuda(f), geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax).cpu().numpy()
