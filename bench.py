@@ -138,15 +138,15 @@ STAGE_KERNEL = {"grid_fwd": "k_grid_tiles", "rows_r2c_fwd": "k_rows_r2c", "colco
 PROFILE_EVERY = 4   # one timed step in PROFILE_EVERY records per-stage kernel events
 
 MEASURED_TRAFFIC = {
-    # kernel: (sha256 prefix of csrc/kernels.cu, bytes per launch averaged over a step's launches)
-    "k_grid_tiles": ("fa1d51f8c0c844cf", 127.10e6),
-    "k_rows_r2c": ("fa1d51f8c0c844cf", 28.30e6),
-    "k_colconv": ("fa1d51f8c0c844cf", 48.03e6),
-    "k_rows_c2r": ("fa1d51f8c0c844cf", 27.51e6),
-    "k_interp_columns": ("fa1d51f8c0c844cf", 100.93e6),
-    "k_col_profiles": ("fa1d51f8c0c844cf", 107.44e6),
-    "k_band_rows": ("fa1d51f8c0c844cf", 45.62e6),
-    "k_gather_samples": ("fa1d51f8c0c844cf", 105.13e6),
+    # kernel: (kernel_source_digest() when measured, bytes per launch averaged over a step's launches)
+    "k_grid_tiles": ("f332f83052384e83", 127.13e6),
+    "k_rows_r2c": ("f332f83052384e83", 28.30e6),
+    "k_colconv": ("f332f83052384e83", 48.03e6),
+    "k_rows_c2r": ("f332f83052384e83", 27.51e6),
+    "k_interp_columns": ("f332f83052384e83", 100.96e6),
+    "k_col_profiles": ("f332f83052384e83", 107.21e6),
+    "k_band_rows": ("f332f83052384e83", 45.60e6),
+    "k_gather_samples": ("f332f83052384e83", 105.10e6),
 }
 
 # FFT kernels run out of shared memory and are limited by instruction issue,
@@ -281,14 +281,21 @@ def batched_uneven(dev, n: int) -> dict:
 
 
 def measured_traffic(kernel: str):
-    import hashlib
     ent = MEASURED_TRAFFIC.get(kernel)
     if ent is None:
         return None
-    src = os.path.join(ROOT, "paper_1604_07651_gb300", "csrc", "kernels.cu")
-    with open(src, "rb") as fh:
-        digest = hashlib.sha256(fh.read()).hexdigest()[:16]
-    return ent[1] if digest == ent[0] else None
+    return ent[1] if kernel_source_digest() == ent[0] else None
+
+
+def kernel_source_digest() -> str:
+    """sha256 prefix of the sources the kernels compile from (kernels.cu and
+    the two headers it includes), the key of MEASURED_TRAFFIC."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "internal.h", "hostdev.h"):
+        with open(os.path.join(ROOT, "paper_1604_07651_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def cpu_baseline(geo, f, target_s: float = 12.0):

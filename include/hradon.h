@@ -67,7 +67,7 @@ typedef struct radon_plan_s* radon_plan;
  *   n_qsplit: number of slowness pieces (Section 5), >= 1; each gets its
  *             own log-polar setup.
  *   device  : CUDA device ordinal, or -1 for the calling thread's current device.
- *   rows_per_band: lattice rows one CTA of the row-FFT kernels holds, 1..4,
+ *   rows_per_band: lattice rows one CTA of the row-FFT kernels holds, 1..6,
  *             or 0 to have radon_plan_create_ex (and radon_batch_create, when
  *             every descriptor asks for it) time each feasible value on the
  *             device and keep the fastest; radon_plan_desc reports the choice.

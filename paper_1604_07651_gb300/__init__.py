@@ -46,7 +46,7 @@ class Plan:
     (``dtau=0``: ``(Nt-1) dt/(Ntau-1)``) and ``q`` evenly on
     ``[qmin, qmax]``; method parameters ``sigma``, ``omega_c``, ``tsplit``
     (split points of Eq. (19) as fractions of T), ``n_qsplit``;
-    ``rows_per_band`` (1..4, or 0 to time them at plan creation; the plan's
+    ``rows_per_band`` (1..6, or 0 to time them at plan creation; the plan's
     ``desc.rows_per_band`` reports the value in use). Unequally spaced grids
     (``radon_plan_create_grid``): ``x`` gives the Nx offsets (km) in place of
     ``k*dx``, ``q`` the Nq slownesses (s/km) in place of the regular grid.

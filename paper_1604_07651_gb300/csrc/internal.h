@@ -109,7 +109,7 @@ constexpr int kTileRows = 16;
 constexpr int kTileCols = 128;
 constexpr int kUnitChunks = 256;
 // Most lattice rows one band of the row kernels holds.
-constexpr int kMaxBandRows = 4;
+constexpr int kMaxBandRows = 6;
 
 // Launchers (kernels.cu). The batched ones take n <= kMaxBatch pieces (host
 // copies of the descriptors) and launch one grid over all of them.

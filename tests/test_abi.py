@@ -50,7 +50,7 @@ def test_host_side_argument_checks(lib):
     assert (d.device, d.rows_per_band, d.n_qsplit, d.n_tsplit) == (-1, 3, 1, 2)
     h = ctypes.c_void_p()
     for field, value in [("Nt", 1), ("dt", 0.0), ("qmin", -1.0), ("omega_c", 0.6), ("sigma", 0.0),
-                         ("n_qsplit", 0), ("n_tsplit", 9), ("rows_per_band", 5), ("rows_per_band", -1)]:
+                         ("n_qsplit", 0), ("n_tsplit", 9), ("rows_per_band", 7), ("rows_per_band", -1)]:
         bad = _lib.RadonDesc.from_buffer_copy(d)
         setattr(bad, field, value)
         assert L.radon_plan_create_ex(ctypes.byref(h), ctypes.byref(bad)) == 1, field

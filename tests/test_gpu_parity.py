@@ -311,13 +311,13 @@ def test_rows_per_band_choices_and_tuner(hr):
     f = synth.band_limited_gather(geo, 71, n_events=5, nu=10.0)
     g_in = synth.random_radon_image(geo, 72)
     outs = {}
-    for R in (0, 1, 2, 3, 4):
+    for R in (0, 1, 2, 3, 4, 5, 6):
         plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, rows_per_band=R)
-        assert 1 <= plan.desc.rows_per_band <= 4
+        assert 1 <= plan.desc.rows_per_band <= 6
         if R:
             assert plan.desc.rows_per_band == R
         outs[R] = (plan.forward(_cuda(f)).cpu().numpy(), plan.adjoint(_cuda(g_in)).cpu().numpy())
         plan.close()
-    for R in (0, 1, 2, 4):
+    for R in (0, 1, 2, 4, 5, 6):
         assert _rel(outs[R][0], outs[3][0].astype(np.float64)) < 1e-6
         assert _rel(outs[R][1], outs[3][1].astype(np.float64)) < 1e-6
