@@ -287,6 +287,19 @@ def measured_traffic(kernel: str):
     return ent[1] if kernel_source_digest() == ent[0] else None
 
 
+def step_stats(step_ms, profiled) -> dict:
+    """Median and p10 / p90 of the timed steps' durations (ms), over all
+    steps and separately over the steps with and without per-kernel events
+    (the latter replay the CUDA graph unless --no-graph)."""
+    def q(v, p):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, int(round(p * (len(v) - 1)))))] if v else None
+    with_ev = [t for s, t in enumerate(step_ms) if s in profiled]
+    plain = [t for s, t in enumerate(step_ms) if s not in profiled]
+    return {"median": q(step_ms, 0.5), "p10": q(step_ms, 0.1), "p90": q(step_ms, 0.9),
+            "without_events_median": q(plain, 0.5), "with_kernel_events_median": q(with_ev, 0.5)}
+
+
 def kernel_source_digest() -> str:
     """sha256 prefix of the sources the kernels compile from (kernels.cu and
     the two headers it includes), the key of MEASURED_TRAFFIC."""
@@ -321,11 +334,43 @@ def cpu_baseline(geo, f, target_s: float = 12.0):
         n *= 4
     t_fwd_full = (t1 - t0) * (geo.Ntau * geo.Nq) / n
     t_adj_full = (t2 - t1) * (geo.Nt * geo.Nx) / n
-    return {"value": 1.0 / (t_fwd_full + t_adj_full), "unit": UNIT, "cores": direct.num_threads(),
-            "kind": "oracle",
-            "sample": f"FP64 direct sum (oracle/direct.c, OpenMP) on {n} random outputs (forward) and "
-                      f"{n} random gather points (adjoint) of the 2048x2048 workload, extrapolated to "
-                      f"full transforms ({t2 - t0:.1f} s measured)"}
+    cores = direct.num_threads()
+    out = {"value": 1.0 / (t_fwd_full + t_adj_full), "unit": UNIT, "cores": cores,
+           "kind": "oracle",
+           "sample": f"FP64 direct sum (oracle/direct.c, OpenMP) on {n} random outputs (forward) and "
+                     f"{n} random gather points (adjoint) of the 2048x2048 workload, extrapolated to "
+                     f"full transforms ({t2 - t0:.1f} s measured)"}
+    # the same on one core (the paper's direct-sum column is one core)
+    n1 = max(1024, n // max(1, cores))
+    direct.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        direct.fwd_points(f, geo.dt, geo.dx, geo.tau(), geo.q(), ii[:n1], li[:n1])
+        t1 = time.perf_counter()
+        direct.adj_points(g_img + 1.0, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q(), jj[:n1], kk[:n1])
+        t2 = time.perf_counter()
+    finally:
+        direct.set_threads(cores)
+    out["one_core"] = {"value": 1.0 / ((t1 - t0) * geo.Ntau * geo.Nq / n1 + (t2 - t1) * geo.Nt * geo.Nx / n1),
+                       "unit": UNIT, "cores": 1,
+                       "sample": f"{n1} outputs + {n1} gather points, extrapolated ({t2 - t0:.1f} s measured)"}
+    out["logpolar_fp64"] = cpu_logpolar()
+    return out
+
+
+def cpu_logpolar(N: int = 512) -> dict:
+    """The FP64 log-polar oracle (numpy) on the N x N sweep gather: plan and
+    kernel spectra built first (untimed), then one forward + adjoint pair."""
+    import synth
+    from oracle.logpolar import Desc, LogPolar
+    geo, f = synth.sweep_gather(N)
+    lp = LogPolar(Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+                       sigma=1.25, omega_c=0.35, tsplits=(0.25, 0.5)))
+    t0 = time.perf_counter()
+    lp.adjoint(lp.forward(f))
+    t = time.perf_counter() - t0
+    return {"value": 1.0 / t, "unit": f"transform pairs/s at N={N}", "N": N,
+            "sample": f"one fwd+adj pair of the {N}x{N} sweep gather, numpy FP64 ({t:.2f} s)"}
 
 
 def run_reference(args, rank, world):
@@ -495,6 +540,7 @@ def main():
                   f"CUDA graph replay of the step on {args.steps - len(profiled)} of the {args.steps} timed steps",
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "step_ms": step_stats(step_ms, profiled),
     }
 
     # end to end through the public API with host buffers (pinned), copies

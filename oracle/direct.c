@@ -268,6 +268,17 @@ void oracle_direct_adj_x_points(const double *g, int Nx, double dt, const double
         out[p] = adj_point_x(g, Nx, dt, x, tau0, dtau, Ntau, q, Nq, jj[p], kk[p]);
 }
 
+/* Threads the following calls use (OpenMP; no effect without it). */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
 int oracle_num_threads(void)
 {

@@ -47,6 +47,7 @@ def _load():
         lib.oracle_direct_adj_x.argtypes = [_dp, i, i, d, _dp, d, d, i, _dp, i, _dp]
         lib.oracle_direct_adj_x_points.argtypes = [_dp, i, d, _dp, d, d, i, _dp, i, _ip, _ip, i, _dp]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [i]
         _lib = lib
     return _lib
 
@@ -63,6 +64,11 @@ def _i(a):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the following calls (the host's cores by default)."""
+    _load().oracle_set_threads(int(n))
 
 
 def fwd(f, dt, dx, tau, q):
