@@ -231,6 +231,54 @@ def sparse_inversion(dev, stream) -> dict:
             "rel_l2_missing_traces": err, "opnorm_R2": lam}
 
 
+def size_sweep(dev, sizes=(512, 1024, 4096), steps: int = 20) -> dict:
+    """Forward + adjoint pairs/s on the N x N sweep gathers (same recipe and
+    default method as the main workload, plan tuned at creation), the pair
+    replayed as a CUDA graph, L2 flushed before every step, inputs resident;
+    the paper's Table 2 per-iteration times give its own pairs/s beside it."""
+    import torch
+    import synth
+    import paper_1604_07651_gb300 as hr
+    paper = {512: 1.0 / (1.9e-3 + 2.3e-3), 1024: 1.0 / (7.4e-3 + 8.7e-3), 2048: 1.0 / (2.9e-2 + 3.2e-2),
+             4096: 1.0 / (1.1e-1 + 1.3e-1)}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {}
+    for N in sizes:
+        geo, f_np = synth.sweep_gather(N)
+        plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+                       rows_per_band=0, device=dev.index)
+        f = torch.tensor(f_np, dtype=torch.float32, device=dev)
+        g = torch.empty((geo.Nq, geo.Ntau), dtype=torch.float32, device=dev)
+        fa = torch.empty_like(f)
+        for _ in range(3):
+            plan.forward(f, out=g)
+            plan.adjoint(g, out=fa)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.forward(f, out=g)
+            plan.adjoint(g, out=fa)
+        graph.replay()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record()
+            graph.replay()
+            b.record()
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        med = ms[len(ms) // 2]
+        out[str(N)] = {"pairs_per_s": 1e3 / med, "ms_per_pair_median": med, "ms_p10": ms[len(ms) // 10],
+                       "ms_p90": ms[(9 * len(ms)) // 10], "paper_gtx970_pairs_per_s": paper.get(N),
+                       "lattices": [(p["Ntheta"], p["Nrho"], p["Ptheta"], p["Prho"]) for p in plan.pieces()]}
+        plan.close()
+        del f, g, fa, graph
+    return {"workload": "sweep gathers N x N (T = 2 s, X = 2 km, 32 Ricker events 20-40 Hz + 5 % noise), "
+                        "default method, fwd + adj as one CUDA graph, L2 flushed per step",
+            "sizes": out}
+
+
 def batched_uneven(dev, n: int) -> dict:
     """Uneven batch: n gathers with Nt ~ U{500..3000} (dt 4 ms), Nx ~
     U{60..480} (dx 25 m), Nq = Nx, 10-40 Ricker events each, stored BF16,
@@ -425,6 +473,7 @@ def main():
     ap.add_argument("--no-solver", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch every timed step eagerly")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the N = 512, 1024, 4096 sweep")
     ap.add_argument("--rows-per-band", type=int, default=0,
                     help="rows per band of the row-FFT kernels; 0 times them at plan creation")
     ap.add_argument("--batch-gathers", type=int, default=256)
@@ -656,6 +705,8 @@ def main():
             result["sparse_inversion"] = sparse_inversion(dev, stream)
         if not args.no_batch:
             result["batched_uneven"] = batched_uneven(dev, args.batch_gathers)
+        if not args.no_sweep:
+            result["sweep"] = size_sweep(dev)
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(geo, f_np)
         print(json.dumps(result), flush=True)
