@@ -180,6 +180,10 @@ radon_status radon_plan_piece_info(radon_plan p, int piece, radon_piece_info* in
  */
 radon_status radon_geometry(const radon_desc* d, int* npieces, radon_piece_info* infos,
                             int max_infos);
+/* As radon_geometry on given offsets / slownesses (x, q as in
+ * radon_plan_create_grid; either may be NULL), host only. */
+radon_status radon_geometry_grid(const radon_desc* d, const double* x, const double* q, int* npieces,
+                                 radon_piece_info* infos, int max_infos);
 
 /* The descriptor the plan was built from (defaults resolved). */
 radon_status radon_plan_desc(radon_plan p, radon_desc* d);

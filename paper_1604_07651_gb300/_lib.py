@@ -49,6 +49,9 @@ SIGNATURES = {
     "radon_plan_desc": (_c_int, [_vp, ctypes.POINTER(RadonDesc)]),
     "radon_geometry": (_c_int, [ctypes.POINTER(RadonDesc), ctypes.POINTER(_c_int),
                                 ctypes.POINTER(RadonPieceInfo), _c_int]),
+    "radon_geometry_grid": (_c_int, [ctypes.POINTER(RadonDesc), ctypes.POINTER(_c_double),
+                                     ctypes.POINTER(_c_double), ctypes.POINTER(_c_int),
+                                     ctypes.POINTER(RadonPieceInfo), _c_int]),
     "radon_plan_device_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "radon_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(RadonDesc)]),
     "radon_batch_create_grid": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(RadonDesc),

@@ -1309,15 +1309,21 @@ extern "C" radon_status radon_plan_piece_info(radon_plan p, int piece, radon_pie
 
 extern "C" radon_status radon_geometry(const radon_desc* din, int* npieces, radon_piece_info* infos,
                                        int max_infos) {
+    return radon_geometry_grid(din, nullptr, nullptr, npieces, infos, max_infos);
+}
+
+extern "C" radon_status radon_geometry_grid(const radon_desc* din, const double* x, const double* q,
+                                            int* npieces, radon_piece_info* infos, int max_infos) {
     if (!npieces) return fail(RADON_ERR_INVALID_ARG, "npieces is NULL");
     if (radon_status s = check_desc(din)) return s;
+    Grid g;
+    if (radon_status s = check_grid(*din, x, q, g)) return s;
     radon_desc d = *din;
     if (d.dtau <= 0) d.dtau = (d.Nt - 1) * d.dt / (d.Ntau - 1);
     const std::vector<double> bs = accepted_splits(d);
     const std::vector<TPiece> tps = time_pieces(d, bs);
     std::vector<double> phi_all;
     int n = 0;
-    const Grid g;
     for (auto& lq : slowness_pieces(d, g))
         for (auto& tp : tps) {
             HostPiece h;
