@@ -198,13 +198,6 @@ __device__ __forceinline__ void rows_r2c_write(const PieceDev& P, int mb, int nr
     }
 }
 
-__device__ __forceinline__ void zero_rows(const PieceDev& P) {
-    float4* p = reinterpret_cast<float4*>(smem_f);
-    const int n4 = P.R * P.Prho / 4;
-    for (int i = threadIdx.x; i < n4; i += blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
-
 // Shared gridding tile: the kTileRows x kTileCols cells plus a halo of 3
 // cells on every side, so that every tap of a sample whose footprint meets
 // the tile lands in it without a bounds check (the halo is dropped at the
