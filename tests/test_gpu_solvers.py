@@ -136,3 +136,22 @@ def test_multiple_attenuation(hr):
     assert _rel(fo.cpu().numpy(), fo_ref) < 1e-3
     assert _rel(fo.cpu().numpy(), prim) < 0.3
     assert _rel(fo.cpu().numpy(), prim) < 0.5 * _rel(f, prim)
+
+
+def test_ista_replays_from_a_cuda_graph(hr, small):
+    """radon_ista makes no host round trip: the whole solve captures into a
+    CUDA graph, and a replay gives the eager result (to the rounding of the
+    gridding's global atomics)."""
+    geo, plan, lp, f, mask = small
+    fc, mc = _cuda(f), _cuda(mask)
+    mu, c2 = 0.05, 1e-3
+    g_eager = plan.ista(fc, mu, 10, mask=mc, step=c2, accelerate=True)
+    out = torch.zeros_like(g_eager)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        out.zero_()
+        plan.ista(fc, mu, 10, mask=mc, step=c2, accelerate=True, out=out)
+    out.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert _rel(out.cpu().numpy(), g_eager.cpu().numpy().astype(np.float64)) < 1e-5
