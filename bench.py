@@ -139,14 +139,14 @@ PROFILE_EVERY = 4   # one timed step in PROFILE_EVERY records per-stage kernel e
 
 MEASURED_TRAFFIC = {
     # kernel: (kernel_source_digest() when measured, bytes per launch averaged over a step's launches)
-    "k_grid_tiles": ("f332f83052384e83", 127.13e6),
-    "k_rows_r2c": ("f332f83052384e83", 28.30e6),
-    "k_colconv": ("f332f83052384e83", 48.03e6),
-    "k_rows_c2r": ("f332f83052384e83", 27.51e6),
-    "k_interp_columns": ("f332f83052384e83", 100.96e6),
-    "k_col_profiles": ("f332f83052384e83", 107.21e6),
-    "k_band_rows": ("f332f83052384e83", 45.60e6),
-    "k_gather_samples": ("f332f83052384e83", 105.10e6),
+    "k_grid_tiles": ("f643e63a17886cc7", 127.38e6),
+    "k_rows_r2c": ("f643e63a17886cc7", 28.30e6),
+    "k_colconv": ("f643e63a17886cc7", 48.06e6),
+    "k_rows_c2r": ("f643e63a17886cc7", 27.50e6),
+    "k_interp_columns": ("f643e63a17886cc7", 100.96e6),
+    "k_col_profiles": ("f643e63a17886cc7", 107.12e6),
+    "k_band_rows": ("f643e63a17886cc7", 45.60e6),
+    "k_gather_samples": ("f643e63a17886cc7", 105.21e6),
 }
 
 # FFT kernels run out of shared memory and are limited by instruction issue,
