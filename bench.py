@@ -351,6 +351,12 @@ def measured_traffic(kernel: str):
     return ent[1] if kernel_source_digest() == ent[0] else None
 
 
+def profiled_steps(K: int) -> list:
+    """The timed steps that carry per-kernel events: one in PROFILE_EVERY,
+    at least the last one."""
+    return [s for s in range(K) if s % PROFILE_EVERY == PROFILE_EVERY - 1] or [K - 1]
+
+
 def step_stats(step_ms, profiled) -> dict:
     """Median and p10 / p90 of the timed steps' durations (ms), over all
     steps and separately over the steps with and without per-kernel events
@@ -548,7 +554,7 @@ def main():
     # the stream about 2 us, 40 us over a step's 20
     plan.set_profiling(False)
     plan.profile_read()
-    profiled = [s for s in range(args.steps) if s % PROFILE_EVERY == PROFILE_EVERY - 1] or [args.steps - 1]
+    profiled = profiled_steps(args.steps)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
