@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import RadonError, RadonDesc, RadonPieceInfo
 
-__all__ = ["Plan", "Batch", "radon", "radon_adjoint", "direct_forward", "direct_adjoint", "RadonError",
+__all__ = ["Plan", "Batch", "radon", "radon_adjoint", "radon_adj", "direct_forward", "direct_adjoint", "RadonError",
            "HRadon"]
 
 
@@ -395,6 +395,9 @@ def radon(f: torch.Tensor, plan: Plan) -> torch.Tensor:
 def radon_adjoint(g: torch.Tensor, plan: Plan) -> torch.Tensor:
     """Differentiable adjoint transform."""
     return HRadonAdjoint.apply(g, plan)
+
+
+radon_adj = radon_adjoint   # the C ABI's name
 
 
 def direct_forward(f: torch.Tensor, Ntau: int, Nq: int, dt: float, dx: float, qmin: float,
