@@ -139,3 +139,20 @@ def test_descriptor_rejects_bad_grids():
         Desc(8, 4, 8, 3, 0.01, 0.1, 0.2, 0.6, x=(0.0, 0.1, 0.2))
     with pytest.raises(ValueError):
         Desc(8, 4, 8, 3, 0.01, 0.1, 0.2, 0.6, q_values=(0.2, 0.2, 0.6))
+
+
+def test_irregular_geometry_generator():
+    """The input recipe: inner offsets jittered within half a spacing (so
+    strictly increasing), the end offsets fixed; slownesses from qmin to qmax,
+    denser towards qmin for q_power > 1."""
+    import synth
+    geo = synth.irregular_geometry(100, 257, 90, 65, 0.004, 2.0, 0.2, 0.7, 5, jitter=0.45, near=0.1, q_power=1.6)
+    x, q = geo.x(), geo.q()
+    h = (2.0 - 0.1) / 256
+    assert x.shape == (257,) and np.all(np.diff(x) > 0)
+    assert x[0] == 0.1 and x[-1] == 2.0 and geo.X == 2.0
+    assert np.max(np.abs(x - (0.1 + np.arange(257) * h))) <= 0.45 * h + 1e-12
+    assert q.shape == (65,) and np.all(np.diff(q) > 0) and q[0] == 0.2 and abs(q[-1] - 0.7) < 1e-12
+    assert np.diff(q)[0] < np.diff(q)[-1]
+    again = synth.irregular_geometry(100, 257, 90, 65, 0.004, 2.0, 0.2, 0.7, 5, jitter=0.45, near=0.1, q_power=1.6)
+    assert again == geo                                  # seeded
