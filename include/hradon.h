@@ -126,7 +126,8 @@ radon_status radon_plan_create(radon_plan* out, int Nt, int Nx, int Ntau, int Nq
  * lookup tables; allocates the work buffers. On failure *out is NULL.
  * RADON_ERR_UNSUPPORTED if a lattice needs more shared memory per block
  * than the device offers (FFT lengths above 12288 along rho or 6144 along
- * theta on GB300).
+ * theta on GB300, or time pieces x lattice length along rho x 4 bytes above
+ * it for the output interpolation's profiles).
  */
 radon_status radon_plan_create_ex(radon_plan* out, const radon_desc* d);
 

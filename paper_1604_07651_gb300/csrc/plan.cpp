@@ -1137,6 +1137,12 @@ extern "C" radon_status radon_plan_create_grid(radon_plan* out, const radon_desc
     p->ncols = (int)cmap.size();
     for (const int4& c : cmap) p->col_pieces = std::max(p->col_pieces, c.y);
     p->nsblocks = (int)smap.size();
+    // the output interpolation holds one rho profile per time piece of a column
+    if ((size_t)p->col_pieces * p->nrho_max * sizeof(float) > (size_t)max_smem_optin()) {
+        destroy_plan(p);
+        return fail(RADON_ERR_UNSUPPORTED, "too many time pieces for the lattice length along rho "
+                                           "(the output interpolation's profiles exceed shared memory)");
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) {
         destroy_plan(p);
         return fail(RADON_ERR_CUDA, "plan creation failed on the device");
@@ -1574,6 +1580,11 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
     b->ncols = (int)cmap.size();
     for (const int4& c : cmap) b->col_pieces = std::max(b->col_pieces, c.y);
     b->nsblocks = (int)smap.size();
+    if ((size_t)b->col_pieces * b->nrho_max * sizeof(float) > (size_t)max_smem_optin()) {
+        destroy_batch(b);
+        return fail(RADON_ERR_UNSUPPORTED, "too many time pieces for the lattice length along rho "
+                                           "(the output interpolation's profiles exceed shared memory)");
+    }
     // rows per band tuned over the whole batch when every descriptor asks
     bool tune = true;
     int rmax = kMaxBandRows;
