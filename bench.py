@@ -73,6 +73,9 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def count(self) -> int:
+        return len(self.lines)
+
     def __exit__(self, *a):
         if self.proc is not None:
             self.proc.terminate()
@@ -568,6 +571,15 @@ def main():
             step() if eager else graph.replay()
             ends[s].record(stream)
         torch.cuda.synchronize()
+        plan.set_profiling(False)
+        # nvidia-smi samples every 200 ms and a short timed region falls
+        # between two samples: the same load continues, untimed, until it has
+        # been sampled three times (at most 2 s)
+        t_stop = time.time() + 2.0
+        while clk.count() < 3 and time.time() < t_stop:
+            for _ in range(50):
+                step() if graph is None else graph.replay()
+            torch.cuda.synchronize()
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     prof = plan.profile_read()
@@ -611,6 +623,8 @@ def main():
                   f"CUDA graph replay of the step on {args.steps - len(profiled)} of the {args.steps} timed steps",
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "clock_sampling": "nvidia-smi every 200 ms over the timed steps and the same load continued "
+                          "untimed right after them until three samples",
         "step_ms": step_stats(step_ms, profiled),
     }
 
