@@ -5,9 +5,10 @@ T = 2 s, X = 2 km, q in [0.2, 0.7] s/km, 32 Ricker events 20-40 Hz plus 5 %
 noise), default method parameters. One step = radon_fwd then radon_adj on
 device-resident data (the pair one iteration of Eq. (18) needs). L2 is
 flushed (a 256 MiB write) before every timed step; only the step itself is
-timed, with CUDA events on the launching stream. Kernel durations come from
-per-stage events on every fourth timed step (launched eagerly); the other
-timed steps replay the step as a CUDA graph (--no-graph: all eager).
+timed, with CUDA events on the launching stream. The timed steps replay the
+step as a CUDA graph (--no-graph: eager launches). Kernel durations come from
+per-stage events on separate eager steps run right after the timed ones
+(same flush), so that no event sits between the timed steps' kernels.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -135,10 +136,10 @@ STAGE_KERNEL = {"grid_fwd": "k_grid_tiles", "rows_r2c_fwd": "k_rows_r2c", "colco
                 "rows_c2r_adj": "k_rows_c2r", "gather_adj": "k_gather_samples",
                 "profiles_adj": "k_col_profiles"}
 
-# DRAM bytes (read + write) per launch from one ncu capture of the benchmark
-# workload (profiles/*.md), valid only for the kernel source they were taken
-# on: the entry is dropped (traffic null) when csrc/kernels.cu changes.
-PROFILE_EVERY = 4   # one timed step in PROFILE_EVERY records per-stage kernel events
+# DRAM bytes (read + write) per launch recorded from one ncu capture of the
+# benchmark workload, valid only for the kernel source they were taken on:
+# the entry is dropped (traffic null) when the kernel sources change.
+PROFILE_EVERY = 4   # eager steps with per-stage kernel events: one per PROFILE_EVERY timed steps
 
 MEASURED_TRAFFIC = {
     # kernel: (kernel_source_digest() when measured, bytes per launch averaged over a step's launches)
@@ -177,7 +178,11 @@ def roofline(dom, d, per_kernel, hbm, peak_kind, plan, clocks, dev, steps):
     bandwidth for the gathers and the gridding (algorithmic bytes)."""
     sec = d["ms"] / 1e3 / max(1, d["launches"])            # average launch
     bytes_launch = d["bytes"] / max(1, d["launches"])
-    out = {"kernel": dom, "traffic": measured_traffic(dom),
+    tr = measured_traffic(dom)
+    out = {"kernel": dom, "traffic": tr,
+           "traffic_source": ("recorded: dram__bytes_read.sum + dram__bytes_write.sum of one earlier ncu capture "
+                              f"of this workload on the same kernel sources ({kernel_source_digest()})")
+           if tr is not None else "null: the kernel sources changed since the last ncu capture",
            "algorithmic_bytes_per_launch": bytes_launch,
            "hbm_achieved_GBps": bytes_launch / sec / 1e9 if sec > 0 else 0.0,
            "hbm_frac": (bytes_launch / sec / 1e9) / hbm if sec > 0 else 0.0,
@@ -298,21 +303,28 @@ def size_sweep(dev, sizes=(512, 1024, 4096), steps: int = 20) -> dict:
             "sizes": out}
 
 
-def batched_uneven(dev, n: int) -> dict:
+def batched_uneven(dev, n: int, rank: int = 0, world: int = 1) -> dict:
     """Uneven batch: n gathers with Nt ~ U{500..3000} (dt 4 ms), Nx ~
     U{60..480} (dx 25 m), Nq = Nx, 10-40 Ricker events each, stored BF16,
-    computed FP32; forward + adjoint of the whole batch as one CUDA graph
-    (5 + 5 launches), timed over replays."""
+    computed FP32; forward + adjoint of the whole batch as one CUDA graph,
+    timed over replays. Under torchrun every rank takes one contiguous shard
+    of the gathers (balanced by samples) and the job time is the slowest
+    rank's. Accuracy: every gather's forward on 256 sampled outputs and
+    adjoint on 256 sampled gather points against the FP64 direct sum (of the
+    BF16-rounded input)."""
     import numpy as np
     import torch
     import synth
     import paper_1604_07651_gb300 as hr
-    geos = synth.batch_geometries(n)
+    from paper_1604_07651_gb300.shard import gather_in_order, shard_bounds
+    geos_all = synth.batch_geometries(n)
+    lo, hi = shard_bounds([g_.Nt * g_.Nx for g_ in geos_all], world)[rank]
+    geos = geos_all[lo:hi]
     t0 = time.time()
     batch = hr.Batch([dict(Nt=g.Nt, Nx=g.Nx, Ntau=g.Ntau, Nq=g.Nq, dt=g.dt, dx=g.dx, qmin=g.qmin,
                            qmax=g.qmax, rows_per_band=0) for g in geos])   # tuned over the batch
     t_plan = time.time() - t0
-    f = batch.pack([torch.tensor(synth.batch_gather(g, i), dtype=torch.float32) for i, g in enumerate(geos)],
+    f = batch.pack([torch.tensor(synth.batch_gather(g, lo + i), dtype=torch.float32) for i, g in enumerate(geos)],
                    dtype=torch.bfloat16)
     g = torch.empty(batch.g_offsets[-1], dtype=torch.float32, device=dev)
     fa = torch.empty(batch.f_offsets[-1], dtype=torch.float32, device=dev)
@@ -338,13 +350,40 @@ def batched_uneven(dev, n: int) -> dict:
         graph.replay()
     a1.record()
     torch.cuda.synchronize()
-    ms = a0.elapsed_time(a1) / reps
-    samples = int(sum(g_.Nt * g_.Nx for g_ in geos))
+    ms = job_time_ms(a0.elapsed_time(a1) / reps, world, dev)
+    # per-gather accuracy of this shard against the FP64 direct sum
+    from oracle import direct
+    direct.build()
+    rng = np.random.default_rng(4 + rank)
+    f_np = f.float().cpu().numpy().astype(np.float64)
+    g_np = g.cpu().numpy().astype(np.float64)
+    fa_np = fa.cpu().numpy()
+    errs = []
+    for i, geo in enumerate(geos):
+        fi = f_np[batch.f_offsets[i]:batch.f_offsets[i + 1]].reshape(geo.Nx, geo.Nt)
+        gi = g_np[batch.g_offsets[i]:batch.g_offsets[i + 1]].reshape(geo.Nq, geo.Ntau)
+        ai = fa_np[batch.f_offsets[i]:batch.f_offsets[i + 1]].reshape(geo.Nx, geo.Nt)
+        ii, li = rng.integers(0, geo.Ntau, 256), rng.integers(0, geo.Nq, 256)
+        jj, kk = rng.integers(0, geo.Nt, 256), rng.integers(0, geo.Nx, 256)
+        ref = direct.fwd_points(fi, geo.dt, geo.dx, geo.tau(), geo.q(), ii, li)
+        refa = direct.adj_points(gi, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q(), jj, kk)
+        errs.append((float(np.linalg.norm(gi[li, ii] - ref) / np.linalg.norm(ref)),
+                     float(np.linalg.norm(ai[kk, jj] - refa) / np.linalg.norm(refa))))
+    errs = gather_in_order(errs, world)
+    samples = int(sum(g_.Nt * g_.Nx for g_ in geos_all))
+    ef, ea = [e[0] for e in errs], [e[1] for e in errs]
     batch.close()
     return {"workload": f"{n} uneven gathers, Nt 500-3000 (4 ms), Nx 60-480 (25 m), Nq = Nx, 10-40 events, "
                         f"BF16 input, {samples / 1e6:.1f} M samples",
             "gathers_per_s": n / (ms / 1e3), "ms_per_batch_fwd_adj": ms, "launches_per_batch": 10,
-            "plan_s": t_plan, "graph": True, "rows_per_band": "tuned over the batch at creation"}
+            "ranks": world, "shard_of_rank0": [0, shard_bounds([g_.Nt * g_.Nx for g_ in geos_all], world)[0][1]],
+            "plan_s": t_plan, "graph": True, "rows_per_band": "tuned over the batch at creation",
+            "per_gather_rel_l2_vs_direct_sum": {
+                "sample": "256 random outputs (forward) and 256 random gather points (adjoint of the computed "
+                          "image) per gather, FP64 direct sum of the BF16-rounded input",
+                "fwd_max": max(ef), "fwd_median": statistics.median(ef),
+                "adj_max": max(ea), "adj_median": statistics.median(ea),
+                "gathers_above_1e-2": sum(1 for a, b in errs if max(a, b) > 1e-2)}}
 
 
 def measured_traffic(kernel: str):
@@ -354,23 +393,22 @@ def measured_traffic(kernel: str):
     return ent[1] if kernel_source_digest() == ent[0] else None
 
 
-def profiled_steps(K: int) -> list:
-    """The timed steps that carry per-kernel events: one in PROFILE_EVERY,
-    at least the last one."""
-    return [s for s in range(K) if s % PROFILE_EVERY == PROFILE_EVERY - 1] or [K - 1]
+def profiled_steps(K: int) -> int:
+    """Eager steps with per-kernel events run after the K timed steps: one per
+    PROFILE_EVERY timed steps, at least one."""
+    return max(1, K // PROFILE_EVERY)
 
 
-def step_stats(step_ms, profiled) -> dict:
-    """Median and p10 / p90 of the timed steps' durations (ms), over all
-    steps and separately over the steps with and without per-kernel events
-    (the latter replay the CUDA graph unless --no-graph)."""
-    def q(v, p):
-        v = sorted(v)
-        return v[min(len(v) - 1, max(0, int(round(p * (len(v) - 1)))))] if v else None
-    with_ev = [t for s, t in enumerate(step_ms) if s in profiled]
-    plain = [t for s, t in enumerate(step_ms) if s not in profiled]
-    return {"median": q(step_ms, 0.5), "p10": q(step_ms, 0.1), "p90": q(step_ms, 0.9),
-            "without_events_median": q(plain, 0.5), "with_kernel_events_median": q(with_ev, 0.5)}
+def _quantile(v, p):
+    v = sorted(v)
+    return v[min(len(v) - 1, max(0, int(round(p * (len(v) - 1)))))] if v else None
+
+
+def step_stats(step_ms, event_ms) -> dict:
+    """Median and p10 / p90 of the timed steps' durations (ms), and the
+    median of the separate eager steps that carry per-kernel events."""
+    return {"median": _quantile(step_ms, 0.5), "p10": _quantile(step_ms, 0.1), "p90": _quantile(step_ms, 0.9),
+            "with_kernel_events_median": _quantile(event_ms, 0.5)}
 
 
 def kernel_source_digest() -> str:
@@ -471,7 +509,9 @@ def run_reference(args, rank, world):
 
     for _ in range(args.warmup):
         step()
+    t_run = time.perf_counter()
     tot = sum(step() for _ in range(args.steps))
+    measured = time.perf_counter() - t_run
     value = args.steps / tot
     cores = direct.num_threads()
     sample = (f"FP64 direct-sum oracle, {n} random outputs + {n} random gather points per step, "
@@ -479,6 +519,10 @@ def run_reference(args, rank, world):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "extrapolated": True,
+        "ms_per_step_note": (f"time of one full 2048^2 forward + adjoint pair, extrapolated from {n} sampled "
+                             f"outputs and {n} sampled gather points per step (measured "
+                             f"{1e3 * measured / args.steps:.1f} ms of host time per step)"),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -551,13 +595,11 @@ def main():
             graph.replay()
         torch.cuda.synchronize()
 
-    # timed region: per-step CUDA events, L2 flushed before each step. The
-    # per-stage events (kernel durations for the roofline) are recorded on
-    # every PROFILE_EVERY-th step only: an event between two launches costs
-    # the stream about 2 us, 40 us over a step's 20
+    # timed region: K steps, each a replay of the step's CUDA graph (eager
+    # without a graph), a CUDA event on each side of every step, L2 flushed
+    # before each step
     plan.set_profiling(False)
     plan.profile_read()
-    profiled = profiled_steps(args.steps)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -565,13 +607,28 @@ def main():
     with ClockSampler(local) as clk:
         for s in range(args.steps):
             flush.fill_(float(s))
-            eager = graph is None or s in profiled
-            plan.set_profiling(s in profiled)
             starts[s].record(stream)
-            step() if eager else graph.replay()
+            step() if graph is None else graph.replay()
             ends[s].record(stream)
         torch.cuda.synchronize()
-        plan.set_profiling(False)
+        barrier()
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        # kernel durations: separate eager steps with a CUDA event pair around
+        # every kernel (an event between two launches costs the stream about
+        # 2 us), same flush, right after the timed steps and under the same
+        # clock sampling
+        n_prof = profiled_steps(args.steps)
+        ev_ms = []
+        for s in range(n_prof):
+            flush.fill_(float(s))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            plan.set_profiling(True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            plan.set_profiling(False)
+            torch.cuda.synchronize()
+            ev_ms.append(e0.elapsed_time(e1))
         # nvidia-smi samples every 200 ms and a short timed region falls
         # between two samples: the same load continues, untimed, until it has
         # been sampled three times (at most 2 s)
@@ -580,8 +637,6 @@ def main():
             for _ in range(50):
                 step() if graph is None else graph.replay()
             torch.cuda.synchronize()
-    barrier()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     prof = plan.profile_read()
     plan.set_profiling(False)
     total_ms = job_time_ms(sum(step_ms), world, dev)
@@ -598,13 +653,12 @@ def main():
         acc["launches"] += v["launches"]
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     d = per_kernel[dom]
-    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
     stages = {k: {"ms_per_launch": (v["ms"] / v["launches"]) if v["launches"] else 0.0,
-                  "launches_per_step": v["launches"] / len(profiled),
+                  "launches_per_step": v["launches"] / n_prof,
                   "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0,
                   "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
               for k, v in prof.items()}
-    launches = int(round(sum(v["launches"] for v in prof.values()) / len(profiled))) * args.steps
+    launches = int(round(sum(v["launches"] for v in prof.values()) / n_prof)) * args.steps
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -614,18 +668,17 @@ def main():
                               "tsplit": [plan.desc.tsplit[i] for i in range(plan.desc.n_tsplit)],
                               "n_qsplit": plan.desc.n_qsplit, "rows_per_band": plan.desc.rows_per_band},
                    "lattices": [(p["Ntheta"], p["Nrho"], p["Ptheta"], p["Prho"]) for p in plan.pieces()]},
-        "roofline": roofline(dom, d, per_kernel, hbm, peak_kind, plan, clk.summary(), dev, len(profiled)),
+        "roofline": roofline(dom, d, per_kernel, hbm, peak_kind, plan, clk.summary(), dev, n_prof),
         "stages": stages,
-        "kernel_timing": f"per-stage CUDA events on {len(profiled)} of the {args.steps} timed steps "
-                         + (f"(every {PROFILE_EVERY}th" if args.steps >= PROFILE_EVERY else "(the last")
-                         + ", launched eagerly)",
-        "launch": "eager" if graph is None else
-                  f"CUDA graph replay of the step on {args.steps - len(profiled)} of the {args.steps} timed steps",
+        "kernel_timing": f"per-stage CUDA events on {n_prof} eager steps run right after the {args.steps} "
+                         "timed steps (same L2 flush, same clock sampling); the timed steps carry no "
+                         "event between kernels",
+        "launch": "eager" if graph is None else f"CUDA graph replay of the step on all {args.steps} timed steps",
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "clock_sampling": "nvidia-smi every 200 ms over the timed steps and the same load continued "
                           "untimed right after them until three samples",
-        "step_ms": step_stats(step_ms, profiled),
+        "step_ms": step_stats(step_ms, ev_ms),
     }
 
     # end to end through the public API with host buffers (pinned), copies
@@ -694,6 +747,8 @@ def main():
                      "copies": "pinned host buffers, one copy stream per direction overlapped with the transforms",
                      "launch": "eager" if graph is None else "CUDA graph replay of the transforms"}
 
+    if not args.no_batch:   # every rank takes its shard of the batch
+        result["batched_uneven"] = batched_uneven(dev, args.batch_gathers, rank, world)
     if rank == 0:
         # accuracy of this run's results against the FP64 oracle (sampled points)
         from oracle import direct
@@ -739,8 +794,6 @@ def main():
                                         "speedup_of_log_polar": value / world / (1e3 / dms)}
         if not args.no_solver:
             result["sparse_inversion"] = sparse_inversion(dev, stream)
-        if not args.no_batch:
-            result["batched_uneven"] = batched_uneven(dev, args.batch_gathers)
         if not args.no_sweep:
             result["sweep"] = size_sweep(dev)
         if not args.no_cpu_baseline and world == 1:

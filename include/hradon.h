@@ -27,11 +27,19 @@
  * (allocated by radon_plan_create*, freed by radon_plan_destroy). Outputs
  * are overwritten, never accumulated. Calls are asynchronous on the given
  * stream (a cudaStream_t passed as void*, NULL = the legacy default
- * stream); no call in this header synchronises the host except plan
- * creation. A plan may be used by one stream at a time.
+ * stream). The transform calls (radon_fwd, radon_adj, the batch, solver and
+ * no-alloc calls) never make the host wait; plan and batch creation and
+ * destruction, and radon_plan_profile_read, synchronise. A plan may be used
+ * by one stream at a time.
  *
  * Errors: every function returns a radon_status and never aborts;
  * radon_last_error() gives a message for the calling thread's last failure.
+ * Everything a failed creation had allocated is released.
+ *
+ * Testing the out-of-memory path: when the environment variable
+ * RADON_FAIL_ALLOC_AT holds n > 0 at the start of radon_plan_create* or
+ * radon_batch_create*, the n-th device allocation of that creation fails
+ * as if the device were out of memory, and the call returns RADON_ERR_OOM.
  */
 #ifndef HRADON_H
 #define HRADON_H

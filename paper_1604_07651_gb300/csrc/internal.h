@@ -163,7 +163,15 @@ int plan_device(const radon_plan_s* p);
 int plan_forward_work_bytes(const radon_plan_s* p, size_t* bytes);
 int plan_forward_in_work(radon_plan_s* p, const float* f, float* g, void* work, size_t bytes,
                          void* stream);
+// Most pieces a plan may have for plan_forward_in_work; launch_write_pieces
+// writes n <= kWorkMaxPieces descriptors to device memory `dst` with one
+// kernel launch on `stream` (the descriptors travel as its parameter).
+constexpr int kWorkMaxPieces = 32;
+int launch_write_pieces(const PieceDev* pieces, int n, PieceDev* dst, void* stream);
 size_t colconv_smem_bytes(const PieceDev& P);
 int max_smem_optin();
+// Dynamic shared memory available to the output interpolation's profiles
+// (the opt-in limit less the kernel's static shared memory); 0 on error.
+size_t interp_smem_limit();
 
 }  // namespace hr

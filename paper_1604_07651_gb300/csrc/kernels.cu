@@ -1199,6 +1199,18 @@ int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
     return set_and_launch(k_rows_c2r<DevBatch>, nblocks, smem, S, stream);
 }
 
+// Dynamic shared memory the output interpolation may take on the current
+// device: the opt-in limit less the kernel's own static shared arrays.
+size_t interp_smem_limit() {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, (const void*)k_interp_columns) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const size_t lim = (size_t)max_smem_optin();
+    return lim > fa.sharedSizeBytes ? lim - fa.sharedSizeBytes : 0;
+}
+
 int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,
                           int ntau_all, int np_all, float* g, void* stream) {
     if (np_max > kMaxColPieces) return (int)cudaErrorInvalidValue;

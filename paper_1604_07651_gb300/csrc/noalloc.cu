@@ -24,6 +24,38 @@
 
 static __device__ __align__(256) unsigned char g_noalloc_work[RADON_NOALLOC_MAX_BYTES];
 
+namespace hr {
+
+// The piece descriptors of one call travel as a kernel parameter (about 13 KB
+// for 32 pieces, under the 32 KB parameter limit) and one small kernel writes
+// them into the work area: no host-to-device copy from pageable memory, which
+// would make the host wait for the stream.
+struct PieceTable {
+    int n;
+    PieceDev p[kWorkMaxPieces];
+};
+static_assert(sizeof(PieceTable) <= 32000, "kernel parameters are limited to 32764 bytes");
+static_assert(sizeof(PieceDev) % sizeof(int) == 0, "descriptors are copied as ints");
+
+__global__ void k_write_pieces(const __grid_constant__ PieceTable T, PieceDev* dst) {
+    const int words = (int)(sizeof(PieceDev) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(T.p);
+    int* out = reinterpret_cast<int*>(dst);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.n * words; i += gridDim.x * blockDim.x)
+        out[i] = src[i];
+}
+
+int launch_write_pieces(const PieceDev* pieces, int n, PieceDev* dst, void* stream) {
+    if (n < 0 || n > kWorkMaxPieces) return (int)cudaErrorInvalidValue;
+    PieceTable T;
+    T.n = n;
+    for (int i = 0; i < n; ++i) T.p[i] = pieces[i];
+    k_write_pieces<<<1, 256, 0, (cudaStream_t)stream>>>(T, dst);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace hr
+
 namespace {
 
 const int kMaxDevices = 256;

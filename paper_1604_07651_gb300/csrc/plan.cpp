@@ -32,6 +32,39 @@ radon_status fail(radon_status s, const std::string& msg) {
     return s;
 }
 
+// Allocation-failure hook for tests of the out-of-memory path: when the
+// environment variable RADON_FAIL_ALLOC_AT holds n > 0 at the start of a
+// plan or batch creation, the n-th device allocation of that creation fails
+// as if cudaMalloc had run out of memory (counted over every thread of the
+// creation; nothing is asked of the device). Unset, 0 or not a number: off.
+std::atomic<long> g_alloc_countdown{0};
+
+void arm_alloc_hook() {
+    const char* v = std::getenv("RADON_FAIL_ALLOC_AT");
+    long n = 0;
+    if (v) {
+        char* end = nullptr;
+        n = std::strtol(v, &end, 10);
+        if (end == v || n < 0) n = 0;
+    }
+    g_alloc_countdown.store(n);
+}
+
+// True when the hook makes this allocation fail.
+bool alloc_hook_fails() {
+    if (g_alloc_countdown.load(std::memory_order_relaxed) <= 0) return false;
+    return g_alloc_countdown.fetch_sub(1) == 1;
+}
+
+// cudaMalloc behind the hook.
+cudaError_t hooked_malloc(void** ptr, size_t bytes) {
+    if (alloc_hook_fails()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
 const double kPi = 3.14159265358979323846;
 const double kTOverlap = 1.25;   // half-width ratio of the time-partition transition bands
 const double kBetaMin = 1e-3;    // smallest angular opening of a sub-problem
@@ -299,7 +332,7 @@ template <class T>
 radon_status dev_upload(radon_plan_s* p, const std::vector<T>& v, const T** out) {
     void* ptr = nullptr;
     size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
-    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    if (hooked_malloc(&ptr, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(RADON_ERR_OOM, "cudaMalloc of a plan table failed");
     }
@@ -313,7 +346,7 @@ radon_status dev_upload(radon_plan_s* p, const std::vector<T>& v, const T** out)
 
 radon_status dev_alloc(radon_plan_s* p, size_t bytes, void** out) {
     void* ptr = nullptr;
-    if (cudaMalloc(&ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    if (hooked_malloc(&ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) {
         cudaGetLastError();
         return fail(RADON_ERR_OOM, "cudaMalloc of a plan buffer failed");
     }
@@ -532,9 +565,9 @@ radon_status kernel_spectrum(radon_plan_s* p, const HostPiece& h, int CB, int nk
     }
     double *dA = nullptr, *dR = nullptr, *dI = nullptr, *dZr = nullptr, *dZi = nullptr;
     const size_t bA = A.size() * 8, bB = Bre.size() * 8, bZ = (size_t)n1 * n2 * 8;
-    if (cudaMalloc(&dA, bA) != cudaSuccess || cudaMalloc(&dR, bB) != cudaSuccess ||
-        cudaMalloc(&dI, bB) != cudaSuccess || cudaMalloc(&dZr, bZ) != cudaSuccess ||
-        cudaMalloc(&dZi, bZ) != cudaSuccess) {
+    if (hooked_malloc((void**)&dA, bA) != cudaSuccess || hooked_malloc((void**)&dR, bB) != cudaSuccess ||
+        hooked_malloc((void**)&dI, bB) != cudaSuccess || hooked_malloc((void**)&dZr, bZ) != cudaSuccess ||
+        hooked_malloc((void**)&dZi, bZ) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(dA); cudaFree(dR); cudaFree(dI); cudaFree(dZr); cudaFree(dZi);
         return fail(RADON_ERR_OOM, "cudaMalloc of the kernel-spectrum work arrays failed");
@@ -1063,6 +1096,7 @@ extern "C" radon_status radon_plan_create_grid(radon_plan* out, const radon_desc
                                                const double* q) {
     if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    arm_alloc_hook();
     radon_plan_s* p = nullptr;
     if (radon_status s = plan_core(din, x, q, &p)) return s;
     DeviceGuard guard(p->device);
@@ -1138,7 +1172,7 @@ extern "C" radon_status radon_plan_create_grid(radon_plan* out, const radon_desc
     for (const int4& c : cmap) p->col_pieces = std::max(p->col_pieces, c.y);
     p->nsblocks = (int)smap.size();
     // the output interpolation holds one rho profile per time piece of a column
-    if ((size_t)p->col_pieces * p->nrho_max * sizeof(float) > (size_t)max_smem_optin()) {
+    if ((size_t)p->col_pieces * p->nrho_max * sizeof(float) > interp_smem_limit()) {
         destroy_plan(p);
         return fail(RADON_ERR_UNSUPPORTED, "too many time pieces for the lattice length along rho "
                                            "(the output interpolation's profiles exceed shared memory)");
@@ -1457,6 +1491,7 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
     if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || !descs) return fail(RADON_ERR_INVALID_ARG, "a batch needs n >= 1 descriptors");
+    arm_alloc_hook();
     radon_batch_s* b = new (std::nothrow) radon_batch_s();
     if (!b) return fail(RADON_ERR_OOM, "host allocation failed");
     b->store = new (std::nothrow) radon_plan_s();
@@ -1580,7 +1615,7 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
     b->ncols = (int)cmap.size();
     for (const int4& c : cmap) b->col_pieces = std::max(b->col_pieces, c.y);
     b->nsblocks = (int)smap.size();
-    if ((size_t)b->col_pieces * b->nrho_max * sizeof(float) > (size_t)max_smem_optin()) {
+    if ((size_t)b->col_pieces * b->nrho_max * sizeof(float) > interp_smem_limit()) {
         destroy_batch(b);
         return fail(RADON_ERR_UNSUPPORTED, "too many time pieces for the lattice length along rho "
                                            "(the output interpolation's profiles exceed shared memory)");
@@ -1713,10 +1748,6 @@ extern "C" radon_status radon_batch_adj(radon_batch b, const float* g, float* f,
 // ---------------------------------------------------------------------------
 namespace hr {
 
-namespace {
-const int kWorkMaxPieces = 32;
-}  // namespace
-
 int set_error(int status, const char* msg) { return fail((radon_status)status, msg); }
 
 int plan_device(const radon_plan_s* p) { return p->device; }
@@ -1760,10 +1791,8 @@ int plan_forward_in_work(radon_plan_s* p, const float* f, float* g, void* work, 
         off += piece_spectrum_bytes(local[i]);
     }
     DeviceGuard guard(p->device);
-    // pageable source: the copy is staged before the call returns
-    if (cudaMemcpyAsync(dpieces, local, np * sizeof(PieceDev), cudaMemcpyHostToDevice,
-                        (cudaStream_t)stream) != cudaSuccess)
-        return fail(RADON_ERR_CUDA, "copy of the piece descriptors failed");
+    if (radon_status s = cuda_status(launch_write_pieces(local, np, dpieces, stream), "piece descriptors"))
+        return s;
     return run_forward(p, local, dpieces, lat, lat_bytes, f, g, stream);
 }
 

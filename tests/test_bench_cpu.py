@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: step statistics, the FFT flop
 model behind the FP32 roofline, the traffic table's source key, and the
-per-stage kernel events of one timed step in PROFILE_EVERY."""
+number of eager steps with per-stage kernel events (one per PROFILE_EVERY
+timed steps)."""
 import math
 
 import bench
@@ -8,13 +9,12 @@ import bench
 
 def test_step_stats_split_and_quantiles():
     steps = [0.70, 0.71, 0.69, 0.80, 0.70, 0.70, 0.72, 0.79]
-    st = bench.step_stats(steps, profiled=[3, 7])
-    assert st["with_kernel_events_median"] in (0.79, 0.80)
-    assert st["without_events_median"] in (0.70, 0.71)
+    st = bench.step_stats(steps, [0.76, 0.78])
+    assert st["with_kernel_events_median"] in (0.76, 0.78)
     assert st["p10"] <= st["median"] <= st["p90"]
     assert min(steps) <= st["p10"] and st["p90"] <= max(steps)
-    empty = bench.step_stats([0.5], profiled=[0])
-    assert empty["without_events_median"] is None and empty["with_kernel_events_median"] == 0.5
+    empty = bench.step_stats([0.5], [])
+    assert empty["median"] == 0.5 and empty["with_kernel_events_median"] is None
 
 
 def test_fft_flop_model_by_hand():
@@ -42,10 +42,9 @@ def test_traffic_table_lookup_follows_the_source_digest(monkeypatch):
 
 
 def test_profiled_steps_are_a_bounded_share():
-    """The steps carrying per-kernel events: one in PROFILE_EVERY (at least
-    one), the rest run without events."""
+    """Eager steps with per-kernel events after the timed ones: one per
+    PROFILE_EVERY timed steps, at least one."""
     for K in (1, 2, 3, 4, 10, 20):
-        prof = bench.profiled_steps(K)
-        assert 1 <= len(prof) <= max(1, K // bench.PROFILE_EVERY)
-        assert all(0 <= s < K for s in prof) and len(set(prof)) == len(prof)
-    assert bench.profiled_steps(20) == [3, 7, 11, 15, 19]
+        n = bench.profiled_steps(K)
+        assert 1 <= n <= max(1, K // bench.PROFILE_EVERY)
+    assert bench.profiled_steps(20) == 5

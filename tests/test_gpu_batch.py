@@ -8,10 +8,10 @@ import torch
 
 import synth
 from oracle.logpolar import Desc, LogPolar
+from parity import assert_parity
 
 pytestmark = pytest.mark.gpu
 
-PARITY_TOL = 1e-5
 
 
 def _rel(a, b):
@@ -78,12 +78,12 @@ def test_batch_against_oracle_fp32_and_bf16(hr):
                                                        for x in gimg]).cuda()))
     for geo, x, a, b, gi, fi in zip(geos, gathers, g32, gb, gimg, fa):
         lp = _oracle(geo)
-        assert _rel(a.cpu().numpy(), lp.forward(x)) < PARITY_TOL
+        assert_parity(a.cpu().numpy(), lp.forward(x), what="batch FP32 forward")
         xb = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
         ref_b = lp.forward(xb)
-        assert _rel(b.cpu().numpy(), ref_b) < PARITY_TOL        # same input as the kernel sees
+        assert_parity(b.cpu().numpy(), ref_b, what="batch BF16 forward")   # same input as the kernel sees
         assert _rel(b.cpu().numpy(), lp.forward(x)) < 1e-2      # BF16 storage error of the input
-        assert _rel(fi.cpu().numpy(), lp.adjoint(gi)) < PARITY_TOL
+        assert_parity(fi.cpu().numpy(), lp.adjoint(gi), what="batch adjoint")
     batch.close()
 
 

@@ -19,13 +19,13 @@ import pytest
 import torch
 
 import synth
+from parity import assert_parity
 from oracle import direct as odirect
 from oracle import solvers
 from oracle.logpolar import Desc, LogPolar
 
 pytestmark = pytest.mark.gpu
 
-PARITY_TOL = 1e-5
 
 
 def _rel(a, b):
@@ -88,8 +88,8 @@ def test_forward_and_adjoint_match_oracle_on_given_grids(hr, name):
     lp = LogPolar(desc)
     f = synth.band_limited_gather(geo, 71, n_events=6, nu=10.0)
     g = synth.random_radon_image(geo, 72)
-    assert _rel(plan.forward(_cuda(f)).cpu().numpy(), lp.forward(f)) < PARITY_TOL
-    assert _rel(plan.adjoint(_cuda(g)).cpu().numpy(), lp.adjoint(g)) < PARITY_TOL
+    assert_parity(plan.forward(_cuda(f)).cpu().numpy(), lp.forward(f), what=name + " forward")
+    assert_parity(plan.adjoint(_cuda(g)).cpu().numpy(), lp.adjoint(g), what=name + " adjoint")
 
 
 def test_regular_grids_given_as_lists(hr):

@@ -225,3 +225,45 @@ def test_mutant_angle_sign_caught(monkeypatch):
 
     monkeypatch.setattr(LP, "radon_points", mutant)
     assert _blob_error() > 1e-2
+
+
+def test_lattice_spacing_rule_by_brute_force():
+    """Eq. (18) by brute force, independent of the oracle's vectorised rule:
+    every pair of neighbouring samples (t_j, x_k)-(t_j + dt, x_k) and
+    (t_j, x_k)-(t_j, x_k + dx) of the time piece on an 8 x 16 gather, mapped
+    one by one through (s, y) = (t^2, x^2) (rescaled), the rotation and
+    scaling of the square in the sector, u = a R(alpha) (s - 1/2, y - 1/2) + O,
+    and the log-polar angle and log-radius of u. The largest differences are
+    the rule's spacings; on this geometry the t-neighbours decide the angle
+    spacing and the x-neighbours the log-radius spacing (so dropping either
+    direction, or swapping the axes, changes the rule and fails)."""
+    for tsplits in ((), (0.5,)):
+        d = Desc(8, 16, 8, 16, 0.05, 0.2, 0.2, 0.7, sigma=1.0, tsplits=tsplits)
+        n_t, n_x = d.Nt - 1, d.Nx - 1
+        for part in LP.plan(d):
+            ca, sa = math.cos(part.alpha), math.sin(part.alpha)
+
+            def lp(j, k):
+                s = (j / n_t) ** 2 - 0.5
+                y = (k / n_x) ** 2 - 0.5
+                u1 = part.a * (ca * s - sa * y) + part.O1
+                u2 = part.a * (sa * s + ca * y) + part.O2
+                return math.atan2(u2, u1), 0.5 * math.log(u1 * u1 + u2 * u2)
+
+            by_t = [0.0, 0.0]
+            by_x = [0.0, 0.0]
+            for j in range(part.jt_lo, part.jt_hi + 1):
+                for k in range(d.Nx):
+                    p0 = lp(j, k)
+                    if j + 1 <= part.jt_hi:
+                        p1 = lp(j + 1, k)
+                        by_t = [max(by_t[0], abs(p1[0] - p0[0])), max(by_t[1], abs(p1[1] - p0[1]))]
+                    if k + 1 < d.Nx:
+                        p1 = lp(j, k + 1)
+                        by_x = [max(by_x[0], abs(p1[0] - p0[0])), max(by_x[1], abs(p1[1] - p0[1]))]
+            dphi, deta = max(by_t[0], by_x[0]), max(by_t[1], by_x[1])
+            assert abs(part.dphi_rule - dphi) <= 1e-12 * dphi, (part.dphi_rule, dphi)
+            assert abs(part.deta_rule - deta) <= 1e-12 * deta, (part.deta_rule, deta)
+            if not tsplits:
+                # both neighbour directions matter here: each decides one spacing
+                assert by_t[0] > by_x[0] * 1.01 and by_x[1] > by_t[1] * 1.01, (by_t, by_x)

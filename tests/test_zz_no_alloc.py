@@ -11,15 +11,13 @@ in the shared array). This file is collected last on purpose.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
 import synth
+from parity import assert_parity   # the bounds of the other GPU parity tests
 
 pytestmark = pytest.mark.gpu
-
-TOL = 1e-5  # the tolerance of the other GPU parity tests
 
 
 @pytest.fixture(scope="module")
@@ -61,9 +59,7 @@ def test_noalloc_forward_matches_regular_forward_twice(lib):
             lib.check(L.radon_fwd(plan, _ptr(f), _ptr(g_ref), stream))
             lib.check(L.radon_fwd_noalloc(plan, _ptr(f), _ptr(g), stream))
             torch.cuda.synchronize()
-            a, b = g.double().cpu().numpy(), g_ref.double().cpu().numpy()
-            assert np.all(np.isfinite(a))
-            assert np.linalg.norm(a - b) / np.linalg.norm(b) < TOL
+            assert_parity(g.double().cpu().numpy(), g_ref.double().cpu().numpy(), what=f"no-alloc call {tag}")
     finally:
         L.radon_plan_destroy(plan)
 
