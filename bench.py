@@ -358,6 +358,7 @@ def batched_uneven(dev, n: int, rank: int = 0, world: int = 1) -> dict:
     f_np = f.float().cpu().numpy().astype(np.float64)
     g_np = g.cpu().numpy().astype(np.float64)
     fa_np = fa.cpu().numpy()
+    from oracle.logpolar import Desc, LogPolar
     errs = []
     for i, geo in enumerate(geos):
         fi = f_np[batch.f_offsets[i]:batch.f_offsets[i + 1]].reshape(geo.Nx, geo.Nt)
@@ -367,11 +368,21 @@ def batched_uneven(dev, n: int, rank: int = 0, world: int = 1) -> dict:
         jj, kk = rng.integers(0, geo.Nt, 256), rng.integers(0, geo.Nx, 256)
         ref = direct.fwd_points(fi, geo.dt, geo.dx, geo.tau(), geo.q(), ii, li)
         refa = direct.adj_points(gi, geo.Nt, geo.Nx, geo.dt, geo.dx, 0.0, geo.dtau, geo.q(), jj, kk)
-        errs.append((float(np.linalg.norm(gi[li, ii] - ref) / np.linalg.norm(ref)),
-                     float(np.linalg.norm(ai[kk, jj] - refa) / np.linalg.norm(refa))))
+        late = ii >= (geo.Ntau - 1) // 4            # intercept times from T/4 on
+        e = [float(np.linalg.norm(gi[li, ii] - ref) / np.linalg.norm(ref)),
+             float(np.linalg.norm(ai[kk, jj] - refa) / np.linalg.norm(refa)),
+             float(np.linalg.norm(gi[li[late], ii[late]] - ref[late]) / np.linalg.norm(ref[late])), None, None]
+        if lo + i < 8:    # the first gathers also against the FP64 log-polar oracle, every output
+            lp = LogPolar(Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+                               sigma=1.25, omega_c=0.35, tsplits=(0.25, 0.5)))
+            r1, r2 = lp.forward(fi), lp.adjoint(gi)
+            e[3] = float(np.linalg.norm(gi - r1) / np.linalg.norm(r1))
+            e[4] = float(np.linalg.norm(ai - r2) / np.linalg.norm(r2))
+        errs.append(e)
     errs = gather_in_order(errs, world)
     samples = int(sum(g_.Nt * g_.Nx for g_ in geos_all))
-    ef, ea = [e[0] for e in errs], [e[1] for e in errs]
+    ef, ea, el = [e[0] for e in errs], [e[1] for e in errs], [e[2] for e in errs]
+    par = [max(e[3], e[4]) for e in errs if e[3] is not None]
     batch.close()
     return {"workload": f"{n} uneven gathers, Nt 500-3000 (4 ms), Nx 60-480 (25 m), Nq = Nx, 10-40 events, "
                         f"BF16 input, {samples / 1e6:.1f} M samples",
@@ -383,7 +394,14 @@ def batched_uneven(dev, n: int, rank: int = 0, world: int = 1) -> dict:
                           "image) per gather, FP64 direct sum of the BF16-rounded input",
                 "fwd_max": max(ef), "fwd_median": statistics.median(ef),
                 "adj_max": max(ea), "adj_median": statistics.median(ea),
-                "gathers_above_1e-2": sum(1 for a, b in errs if max(a, b) > 1e-2)}}
+                "fwd_tau_from_T/4_max": max(el), "fwd_tau_from_T/4_median": statistics.median(el),
+                "gathers_above_1e-2": sum(1 for e in errs if max(e[0], e[1]) > 1e-2),
+                "note": "traces 25 m apart against 4 ms samples: the Eq. (18) lattice follows the trace "
+                        "spacing and cannot resolve small-t wavelets, so outputs at small intercept time "
+                        "miss the direct sum; the kernels match the FP64 log-polar oracle on the same lattices"},
+            "per_gather_rel_l2_vs_fp64_logpolar": {
+                "sample": f"every output and gather point of the first {len(par)} gathers",
+                "max_fwd_or_adj": max(par) if par else None}}
 
 
 def measured_traffic(kernel: str):

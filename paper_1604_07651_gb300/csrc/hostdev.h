@@ -382,6 +382,84 @@ inline int fft_stage_tables(int n, cf* T) {
     return len;
 }
 
+// ---------------------------------------------------------------------------
+// In-place mixed-radix FFT by decimation in frequency (forward) and in time
+// (inverse). The forward transform leaves its output in digit-reversed order
+// and the inverse takes digit-reversed input back to natural order, so a
+// pointwise product between them needs no reordering, and every pass reads
+// and writes the same positions (one barrier between passes in shared
+// memory).
+//
+// Passes p = 0 .. s-1 take the radices of fft_radices in order, with strides
+// S_p = n / (R_0 ... R_p) and blocks of L_p = R_p S_p consecutive elements.
+// Forward pass p, butterfly b in [0, n / R_p): block q = b div S_p,
+// m = b mod S_p; inputs x_r at q L_p + m + r S_p (r < R_p); outputs
+//     y_k = W_{L_p}^(m k) sum_r x_r W_{R_p}^(r k),   W_N = exp(-2 pi i / N),
+// at the same positions (k in place of r). After the last pass position
+// sum_p k_p S_p holds frequency sum_p k_p R_0 ... R_(p-1). Inverse pass p
+// (p = s-1 down to 0) undoes forward pass p up to the factor R_p:
+//     x_r = sum_k conj(W_{L_p}^(m k)) y_k W_{R_p}^(-r k).
+// The twiddles W_{L_p}^(m k) of pass p are stage_twiddles(S_p, R_p); the last
+// pass has S = 1 and none.
+// ---------------------------------------------------------------------------
+constexpr int kMaxDifPasses = 8;
+
+// Radices and strides of the passes of length n: the radices of fft_radices
+// in reverse order (the factor 3, 5 or 9 first, radix 16 last, so that the
+// last pass, stride 1, is a radix-16 pass whenever 16 divides n); returns s
+// (-1 if n is not a supported length).
+HD int dif_plan(int n, int R[kMaxDifPasses], int S[kMaxDifPasses]) {
+    int rad[32];
+    const int s = fft_radices(n, rad);
+    if (s < 0 || s > kMaxDifPasses) return -1;
+    int L = n;
+    for (int p = 0; p < s; ++p) {
+        R[p] = rad[s - 1 - p];
+        S[p] = L / R[p];
+        L = S[p];
+    }
+    return s;
+}
+
+// Shared-memory layout of the 16-byte elements (two spectrum columns) of the
+// column kernel: the low three bits of the index are XOR-ed with bits 4..6,
+// so that the 8 elements of a quarter warp land in 8 different 16-byte bank
+// groups both for consecutive indices and for the stride-16 accesses of a
+// radix-16 pass. Changes only the low three bits: a permutation of every
+// aligned group of 8 (and the identity below 16).
+HD int swc(int i) { return i ^ ((i >> 4) & 7); }
+
+// First position of butterfly b's elements in pass (R, S): q L + m.
+HD int dif_base(int R, int S, int b) {
+    const int q = b / S;
+    return q * S * R + (b - q * S);
+}
+
+// Frequency held at position pos after the forward passes.
+HD int dif_freq(int s, const int R[kMaxDifPasses], const int S[kMaxDifPasses], int pos) {
+    int f = 0, w = 1;
+    for (int p = 0; p < s; ++p) {
+        const int k = pos / S[p];
+        pos -= k * S[p];
+        f += k * w;
+        w *= R[p];
+    }
+    return f;
+}
+
+// Every pass's twiddle table back to back in pass order (the last pass has
+// none); returns the number of entries (T may be null to query it).
+inline int fft_dif_tables(int n, cf* T) {
+    int R[kMaxDifPasses], S[kMaxDifPasses];
+    const int s = dif_plan(n, R, S);
+    int len = 0;
+    for (int p = 0; p < s; ++p) {
+        if (T) stage_twiddles(S[p], R[p], T + len);
+        len += stage_table_len(S[p], R[p]);
+    }
+    return len;
+}
+
 // Butterflies of one radix a thread of the block FFT holds at once (the
 // register budget of 64 per thread): one sequence of length n fits one stage
 // round when n / R <= threads * fft_qmax(R).

@@ -17,7 +17,9 @@ namespace hr {
 struct FftPlan {            // radix schedule of one FFT length
     int n;
     int nst;
-    int rad[24];
+    int rad[8];             // radix of each stage / pass
+    int st[8];              // column plans (decimation in frequency): stride of each pass
+    int tw[8];              // column plans: offset of each pass's twiddles in the table
 };
 
 // Lattice position of one gather sample, computed once per plan in FP64:
@@ -70,7 +72,8 @@ struct PieceDev {
     const cf* K;            // [nkb][k1max+1][CB] kernel spectrum (normalised)
     const cf* twM;          // stage twiddle tables of the row FFT (length Prho/2)
     const cf* twP;          // [Prho/2+1] exp(-2 pi i k / Prho)
-    const cf* twT;          // stage twiddle tables of the column FFT (length Ptheta)
+    const cf* twT;          // pass twiddle tables of the column FFT pair (length Ptheta), twT_len entries
+    int twT_len;            // entries of twT, a multiple of 2 (16-byte copies)
     FftPlan fftM;           // row FFT (length Prho/2)
     FftPlan fftT;           // column FFT (length Ptheta)
     float* lat;             // [Ntheta][Nrho] real lattice (Q forward, G' adjoint)

@@ -82,11 +82,28 @@ int fft_size(int n) {
 }
 
 FftPlan make_fft_plan(int n) {
-    FftPlan fp;
+    FftPlan fp{};
     fp.n = n;
     int rad[32];
     fp.nst = fft_radices(n, rad);
-    for (int i = 0; i < fp.nst && i < 24; ++i) fp.rad[i] = rad[i];
+    for (int i = 0; i < fp.nst && i < 8; ++i) fp.rad[i] = rad[i];
+    return fp;
+}
+
+// Pass schedule of the column transform pair (decimation in frequency /
+// time, dif_plan): radices, strides and twiddle-table offsets.
+FftPlan make_dif_fft_plan(int n) {
+    FftPlan fp{};
+    fp.n = n;
+    int R[kMaxDifPasses], S[kMaxDifPasses];
+    fp.nst = dif_plan(n, R, S);
+    int ofs = 0;
+    for (int p = 0; p < fp.nst && p < 8; ++p) {
+        fp.rad[p] = R[p];
+        fp.st[p] = S[p];
+        fp.tw[p] = ofs;
+        ofs += stage_table_len(S[p], R[p]);
+    }
     return fp;
 }
 
@@ -713,9 +730,11 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     if (Rmax < 1) return fail(RADON_ERR_UNSUPPORTED, "row FFT length too large for shared memory");
     h.Rmax = Rmax;
     const int R = std::min(Rmax, d.rows_per_band > 0 ? d.rows_per_band : 3);
-    int CB = 2;
-    while (CB > 1 && (size_t)CB * h.Ptheta * sizeof(cf) > (size_t)smem_max) --CB;
-    if ((size_t)CB * h.Ptheta * sizeof(cf) > (size_t)smem_max)
+    const int CB = 2;   // spectrum columns per column block (the column kernel holds both)
+    // the column kernel holds the column block, its slice of K and the twiddle tables
+    const size_t col_smem = ((size_t)h.Ptheta + h.k1max + 1) * 2 * sizeof(cf) +
+                            (size_t)((fft_dif_tables(h.Ptheta, nullptr) + 2) & ~1) * sizeof(cf);
+    if (col_smem > (size_t)smem_max)
         return fail(RADON_ERR_UNSUPPORTED, "column FFT length too large for shared memory");
     P.R = R;
     P.CB = CB;
@@ -730,7 +749,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.l_lo = h.l_lo;
     P.l_hi = h.l_hi;
     P.fftM = make_fft_plan(h.Prho / 2);
-    P.fftT = make_fft_plan(h.Ptheta);
+    P.fftT = make_dif_fft_plan(h.Ptheta);
 
     // per-time weight (window, 2 a^2 tb, quadrature and B-spline normalisation)
     // and trapezoid weights in x, both FP64 for the position-table kernel
@@ -788,9 +807,10 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     set_rows(h, R);
     // twiddles
     const int M = h.Prho / 2;
-    std::vector<cf> twM(fft_stage_tables(M, nullptr) + 1), twP(M + 1), twT(fft_stage_tables(h.Ptheta, nullptr) + 1);
+    std::vector<cf> twM(fft_stage_tables(M, nullptr) + 1), twP(M + 1), twT((fft_dif_tables(h.Ptheta, nullptr) + 2) & ~1);
     fft_stage_tables(M, twM.data());
-    fft_stage_tables(h.Ptheta, twT.data());
+    fft_dif_tables(h.Ptheta, twT.data());
+    P.twT_len = (int)twT.size();
     for (int k = 0; k <= M; ++k)
         twP[k] = {(float)std::cos(-2 * kPi * k / h.Prho), (float)std::sin(-2 * kPi * k / h.Prho)};
     std::vector<cf> K;

@@ -134,6 +134,90 @@ static double irfft_error(int P, int kmax, std::mt19937& rng) {
     return std::sqrt(num / den);
 }
 
+// The column kernel's transform pair, run sequentially in place: forward
+// passes by decimation in frequency, product with a spectrum K at each
+// position's digit-reversed frequency, inverse passes by decimation in time.
+// Returns the relative L2 error against n * IDFT(K .* DFT(x)) in FP64, and
+// counts positions whose frequency map is not a permutation.
+template <int R>
+static void dif_pass(std::vector<cf>& a, int S, const cf* T, int b, bool inverse) {
+    const int base = dif_base(R, S, b);
+    const int m = b % S;
+    cf x[R];
+    for (int r = 0; r < R; ++r) x[r] = a[base + r * S];
+    if (!inverse) {
+        dft_small<R>(x, -1);
+        if (S > 1)
+            for (int k = 1; k < R; ++k) x[k] = cmul(x[k], T[(k - 1) * S + m]);
+    } else {
+        if (S > 1)
+            for (int k = 1; k < R; ++k) x[k] = cmulc(x[k], T[(k - 1) * S + m]);
+        dft_small<R>(x, +1);
+    }
+    for (int r = 0; r < R; ++r) a[base + r * S] = x[r];
+}
+
+static void dif_pass_any(int R, std::vector<cf>& a, int S, const cf* T, int b, bool inv) {
+    switch (R) {
+        case 16: dif_pass<16>(a, S, T, b, inv); break;
+        case 12: dif_pass<12>(a, S, T, b, inv); break;
+        case 10: dif_pass<10>(a, S, T, b, inv); break;
+        case 9: dif_pass<9>(a, S, T, b, inv); break;
+        case 8: dif_pass<8>(a, S, T, b, inv); break;
+        case 6: dif_pass<6>(a, S, T, b, inv); break;
+        case 5: dif_pass<5>(a, S, T, b, inv); break;
+        case 4: dif_pass<4>(a, S, T, b, inv); break;
+        case 3: dif_pass<3>(a, S, T, b, inv); break;
+        default: dif_pass<2>(a, S, T, b, inv); break;
+    }
+}
+
+static double dif_conv_error(int n, std::mt19937& rng, int& bad_freq) {
+    std::normal_distribution<double> N(0, 1);
+    int R[kMaxDifPasses], S[kMaxDifPasses];
+    const int s = dif_plan(n, R, S);
+    std::vector<cf> T(fft_dif_tables(n, nullptr) + 1);
+    fft_dif_tables(n, T.data());
+    std::vector<cf> a(n), K(n);
+    std::vector<cd> xd(n), Kd(n);
+    for (int i = 0; i < n; ++i) {
+        a[i] = {(float)N(rng), (float)N(rng)};
+        xd[i] = cd(a[i].x, a[i].y);
+        K[i] = {(float)N(rng), (float)N(rng)};
+        Kd[i] = cd(K[i].x, K[i].y);
+    }
+    int ofs = 0;
+    std::vector<int> off(s);
+    for (int p = 0; p < s; ++p) {
+        off[p] = ofs;
+        ofs += stage_table_len(S[p], R[p]);
+    }
+    for (int p = 0; p < s; ++p)
+        for (int b = 0; b < n / R[p]; ++b) dif_pass_any(R[p], a, S[p], T.data() + off[p], b, false);
+    std::vector<int> seen(n, 0);
+    for (int pos = 0; pos < n; ++pos) {
+        const int f = dif_freq(s, R, S, pos);
+        if (f < 0 || f >= n || seen[f]++) ++bad_freq;
+        else a[pos] = cmul(a[pos], K[f]);
+    }
+    for (int p = s - 1; p >= 0; --p)
+        for (int b = 0; b < n / R[p]; ++b) dif_pass_any(R[p], a, S[p], T.data() + off[p], b, true);
+    std::vector<cd> X(n);
+    for (int k = 0; k < n; ++k) {
+        cd acc = 0;
+        for (int i = 0; i < n; ++i) acc += xd[i] * std::polar(1.0, -2 * M_PI * (double)((long)k * i % n) / n);
+        X[k] = acc * Kd[k];
+    }
+    double num = 0, den = 0;
+    for (int i = 0; i < n; ++i) {
+        cd acc = 0;
+        for (int k = 0; k < n; ++k) acc += X[k] * std::polar(1.0, 2 * M_PI * (double)((long)k * i % n) / n);
+        num += std::norm(acc - cd(a[i].x, a[i].y));
+        den += std::norm(acc);
+    }
+    return std::sqrt(num / den);
+}
+
 static double b3_error() {
     double e = 0;
     for (int i = 0; i <= 1000; ++i) {
@@ -167,16 +251,25 @@ int main() {
     for (int P : {64, 768}) e = std::max(e, irfft_error(P, P / 5, rng));
     std::printf("irfft_rel_l2 %.3e\n", e);
     std::printf("b3_weights %.3e\n", b3_error());
+    e = 0;
+    int bad_freq = 0;
+    for (int n : {2, 3, 4, 5, 6, 8, 9, 10, 12, 16, 18, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96, 128, 144, 160, 192,
+                  256, 288, 320, 384, 512, 576, 640, 768, 1024, 1152, 1280, 1536, 2048, 2304, 2560, 3072, 4096, 5120,
+                  6144})
+        e = std::max(e, dif_conv_error(n, rng, bad_freq));
+    std::printf("dif_conv_rel_l2 %.3e\n", e);
+    std::printf("dif_freq_violations %d\n", bad_freq);
     // the layout swizzle is a permutation of [0, n) for every FFT length used
     int bad = 0, nlen = 0;
     for (int n = 1; n <= 6144; ++n) {
         int rad[32];
         if (fft_radices(n, rad) < 0 || (n % 3 == 0 ? n > 6144 : n % 5 == 0 ? n > 5120 : n > 4096)) continue;
         ++nlen;
-        std::vector<int> seen(n, 0);
+        std::vector<int> seen(n, 0), seen2(n, 0);
         for (int i = 0; i < n; ++i) {
-            const int p = sw(i);
+            const int p = sw(i), q = swc(i);
             if (p < 0 || p >= n || seen[p]++) ++bad;
+            if (q < 0 || q >= n || seen2[q]++) ++bad;
         }
     }
     std::printf("swizzle_violations %d\n", bad);

@@ -31,6 +31,15 @@ def test_real_fft_packing(results):
     assert results["irfft_rel_l2"] < 5e-7
 
 
+def test_dif_dit_transform_pair(results):
+    """The column kernel's in-place pair: forward passes by decimation in
+    frequency, product at each position's digit-reversed frequency, inverse
+    passes by decimation in time, for every supported length, against
+    n * IDFT(K .* DFT(x)) in FP64."""
+    assert results["dif_freq_violations"] == 0
+    assert results["dif_conv_rel_l2"] < 1e-6
+
+
 def test_b3_weights(results):
     assert results["b3_weights"] < 1e-6
 
