@@ -1,7 +1,8 @@
 // Pure arithmetic shared by the device kernels and by the host unit tests of
 // those kernels (compiled with g++ for the tests, nvcc for the library):
 // * cubic B-spline tap weights (the B3 of Eq. (14)-(17));
-// * one radix-r Stockham butterfly (the FFT of Eq. (7), (16)-(17));
+// * the in-register DFTs and the in-place FFT passes, with their position
+//   maps (the FFTs of Eq. (7), (16)-(17));
 // * the packing of a real FFT into a complex FFT of half the length.
 #pragma once
 
@@ -280,18 +281,11 @@ HD_UNROLL
     }
 }
 
-// One Stockham autosort butterfly (Govindaraju et al., SC'08 formulation),
-// split in its two halves so that a caller can keep all loads of a stage
-// before all stores (in-place stages): stage of radix R with
-// Ns = product of the radices already applied (a power of two), butterfly
-// index j in [0, n/R). The twiddles of a stage depend only on Ns, R and
-// jm = j mod Ns: v[r] is multiplied by exp(-2 pi i r jm / (Ns R)) (its
-// conjugate for dir = +1), read from the stage's table T[(r - 1) Ns + jm]
-// (stage_twiddles); the first stage (Ns = 1) has none. The tables of
-// consecutive stages lie back to back, Ns (R - 1) entries each.
+// Twiddle table of one FFT pass with Ns butterflies per block and radix R:
+// entry (r - 1) Ns + jm is exp(-2 pi i r jm / (Ns R)), r = 1 .. R-1,
+// jm < Ns; computed in FP64 and rounded once. A pass with Ns = 1 has none.
 HD int stage_table_len(int Ns, int R) { return Ns > 1 ? Ns * (R - 1) : 0; }
 
-// One stage's table, computed in FP64 and rounded once.
 inline void stage_twiddles(int Ns, int R, cf* T) {
     if (Ns <= 1) return;
     for (int r = 1; r < R; ++r)
@@ -299,36 +293,6 @@ inline void stage_twiddles(int Ns, int R, cf* T) {
             const double a = -2.0 * 3.14159265358979323846 * (double)((r * jm) % (Ns * R)) / (double)(Ns * R);
             T[(r - 1) * Ns + jm] = {(float)cos(a), (float)sin(a)};
         }
-}
-
-template <int R>
-HD void stockham_load(const cf* in, int n, int Ns, int j, const cf* T, int dir, cf v[R]) {
-    HD_UNROLL
-    for (int r = 0; r < R; ++r) v[r] = in[sw(j + r * (n / R))];
-    if (Ns > 1) {
-        const int jm = j & (Ns - 1);
-        HD_UNROLL
-        for (int r = 1; r < R; ++r) {
-            const cf w = T[(r - 1) * Ns + jm];
-            v[r] = dir < 0 ? cmul(v[r], w) : cmulc(v[r], w);
-        }
-    }
-}
-
-template <int R>
-HD void stockham_store(cf* out, int Ns, int lgNs, int j, int dir, cf v[R]) {
-    dft_small<R>(v, dir);
-    const int jm = j & (Ns - 1);
-    const int dst = ((j >> lgNs) * R << lgNs) + jm;
-HD_UNROLL
-    for (int r = 0; r < R; ++r) out[sw(dst + r * Ns)] = v[r];
-}
-
-template <int R>
-HD void stockham_butterfly(const cf* in, cf* out, int n, int Ns, int lgNs, int j, const cf* T, int dir) {
-    cf v[R];
-    stockham_load<R>(in, n, Ns, j, T, dir, v);
-    stockham_store<R>(out, Ns, lgNs, j, dir, v);
 }
 
 // Radix plan of n = 2^a, 3 * 2^a, 5 * 2^a or 9 * 2^a (n <= 2304): radix 16
@@ -366,20 +330,6 @@ HD int fft_radices(int n, int rad[32]) {
         rad[k++] = n;   // 2, 3, 4, 5, 6, 8, 9, 10 or 12
     }
     return k;
-}
-
-// Every stage's twiddle table of an FFT of length n, back to back in stage
-// order; returns the number of entries (T may be null to query it).
-inline int fft_stage_tables(int n, cf* T) {
-    int rad[32];
-    const int nst = fft_radices(n, rad);
-    int len = 0, Ns = 1;
-    for (int s = 0; s < nst; ++s) {
-        if (T) stage_twiddles(Ns, rad[s], T + len);
-        len += stage_table_len(Ns, rad[s]);
-        Ns *= rad[s];
-    }
-    return len;
 }
 
 // ---------------------------------------------------------------------------
@@ -447,6 +397,19 @@ HD int dif_freq(int s, const int R[kMaxDifPasses], const int S[kMaxDifPasses], i
     return f;
 }
 
+// Position holding frequency f after the forward passes (inverse of
+// dif_freq): the digits of f in the mixed radix R_0, R_1, ... (least
+// significant first) weighted by the strides.
+HD int dif_pos(int s, const int R[kMaxDifPasses], const int S[kMaxDifPasses], int f) {
+    int pos = 0;
+    for (int p = 0; p < s; ++p) {
+        const int q = f / R[p];
+        pos += (f - q * R[p]) * S[p];
+        f = q;
+    }
+    return pos;
+}
+
 // Every pass's twiddle table back to back in pass order (the last pass has
 // none); returns the number of entries (T may be null to query it).
 inline int fft_dif_tables(int n, cf* T) {
@@ -460,58 +423,36 @@ inline int fft_dif_tables(int n, cf* T) {
     return len;
 }
 
-// Butterflies of one radix a thread of the block FFT holds at once (the
-// register budget of 64 per thread): one sequence of length n fits one stage
-// round when n / R <= threads * fft_qmax(R).
-HD int fft_qmax(int R) {
-    switch (R) {
-        case 16: case 12: case 10: case 9: case 8: return 1;
-        case 6: case 5: case 2: return 2;
-        case 4: return 3;
-        default: return 4;   // 3
-    }
-}
-
-// Whether the block FFT of `threads` threads handles length n.
-HD bool fft_fits(int n, int threads) {
-    int rad[32];
-    const int nst = fft_radices(n, rad);
-    if (nst < 0) return false;
-    for (int s = 0; s < nst; ++s)
-        if (n / rad[s] > threads * fft_qmax(rad[s])) return false;
-    return true;
-}
-
 // Real FFT of length P = 2M through a complex FFT of length M of the packed
-// pairs z[n] = x[2n] + i x[2n+1] with transform Z (both in the sw layout). Unnormalised, without the
+// pairs z[n] = x[2n] + i x[2n+1] with transform Z. Unnormalised, without the
 // factors 1/2 (they are folded into the kernel spectrum):
 //   X[k] = (Z[k] + conj Z[M-k]) - i W^k (Z[k] - conj Z[M-k]),  W = exp(-2 pi i / P),
-// Z[M] = Z[0]. twP[k] = W^k.
-HD cf r2c_post(const cf* Z, int M, int k, const cf* twP) {
-    cf a = Z[sw(k)];
-    cf b = cconj(Z[sw(k == 0 ? 0 : M - k)]);
-    cf e = cadd(a, b);
-    cf o = cmul(twP[k], csub(a, b));
-    return {e.x + o.y, e.y - o.x};          // e - i o
-}
-
-// Inverse of r2c_post for the pair (k, M-k), 0 < k < M, in place: from the
-// half spectrum X (X[M] = 0) build Z[k] = E + i O with
-//   E = X[k] + conj X[M-k],  O = W^-k (X[k] - conj X[M-k]).
-// W^-(M-k) = -W^k gives Z[M-k] from the same two values.
-HD void c2r_pre_pair(cf* X, int M, int k, const cf* twP) {
-    cf a = X[sw(k)], b = X[sw(M - k)];
-    cf w = twP[k];
-    cf e1 = cadd(a, cconj(b));
-    cf o1 = cmulc(csub(a, cconj(b)), w);     // (a - conj b) * conj(W^k)
-    cf e2 = cadd(b, cconj(a));
-    cf o2 = cmul(csub(b, cconj(a)), w);      // (b - conj a) * W^k, times -1 below
-    X[sw(k)] = {e1.x - o1.y, e1.y + o1.x};       // e1 + i o1
-    X[sw(M - k)] = {e2.x + o2.y, e2.y - o2.x};   // e2 + i (-o2)
-}
-
+// Z[M] = Z[0], twP[k] = W^k. The inverse builds, for the pair (k, M-k),
+// 0 < k < M, from the half spectrum X (X[M] = 0), Z[k] = E + i O with
+//   E = X[k] + conj X[M-k],  O = W^-k (X[k] - conj X[M-k]),
+// and W^-(M-k) = -W^k gives Z[M-k] from the same two values.
 // k = 0 of the inverse: X[0] real part only (its imaginary part and X[M]
 // are zero for a real signal), Z[0] = X0 + i X0.
 HD cf c2r_pre_dc(cf X0) { return {X0.x, X0.x}; }
+
+// The row kernels hold Z in digit-reversed order: the forward step reads
+// Z[k] and Z[M-k] from buffer positions pk and pmk;
+HD cf r2c_post_at(const cf* Z, int pk, int pmk, int k, const cf* twP) {
+    cf a = Z[pk];
+    cf b = cconj(Z[pmk]);
+    cf e = cadd(a, b);
+    cf o = cmul(twP[k], csub(a, b));
+    return {e.x + o.y, e.y - o.x};
+}
+// the inverse step takes a = X[k], b = X[M-k] and w = W^k and gives the
+// packed inputs Z[k] (zk) and Z[M-k] (zmk), 0 < k < M.
+HD void c2r_pre_vals(cf a, cf b, cf w, cf& zk, cf& zmk) {
+    cf e1 = cadd(a, cconj(b));
+    cf o1 = cmulc(csub(a, cconj(b)), w);
+    cf e2 = cadd(b, cconj(a));
+    cf o2 = cmul(csub(b, cconj(a)), w);
+    zk = {e1.x - o1.y, e1.y + o1.x};
+    zmk = {e2.x + o2.y, e2.y - o2.x};
+}
 
 }  // namespace hr

@@ -70,7 +70,8 @@ struct PieceDev {
     const int* colm0;       // [ncol] first theta tap of each column
     const float* colscale;  // [ncol] output scale 2 X cos(psi) / a
     const cf* K;            // [nkb][k1max+1][CB] kernel spectrum (normalised)
-    const cf* twM;          // stage twiddle tables of the row FFT (length Prho/2)
+    const cf* twM;          // pass twiddle tables of the row FFT pair (length Prho/2)
+    const int* rpos;        // [Prho/2] position of each frequency after the forward row passes
     const cf* twP;          // [Prho/2+1] exp(-2 pi i k / Prho)
     const cf* twT;          // pass twiddle tables of the column FFT pair (length Ptheta), twT_len entries
     int twT_len;            // entries of twT, a multiple of 2 (16-byte copies)

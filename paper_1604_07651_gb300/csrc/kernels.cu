@@ -37,106 +37,6 @@ __device__ __forceinline__ cf ldcf(const cf* p) {
     float2 v = __ldg(reinterpret_cast<const float2*>(p));
     return {v.x, v.y};
 }
-// One in-place Stockham stage of radix R over `nrows` sequences of length n
-// stored back to back in shared memory. Every thread first loads the inputs
-// of up to Q butterflies into registers, the block synchronises, then every
-// thread transforms and stores; so the stage can overwrite its own input.
-// Rows are processed in rounds of as many whole rows as blockDim.x * Q
-// butterflies cover (the plan guarantees n / R <= blockDim.x * Q).
-template <int R, int Q, int DIR>
-__device__ __forceinline__ void fft_stage(cf* buf, int n, int nrows, int Ns, int lgNs,
-                                          const cf* __restrict__ tw) {
-    const int nb = n / R;
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const int per_round = max(1, (nthr * Q) / nb);
-    const float inv_nb = 1.0f / (float)nb;
-    for (int r0 = 0; r0 < nrows; r0 += per_round) {
-        const int items = min(per_round, nrows - r0) * nb;
-        cf v[Q][R];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int idx = tid + q * nthr;
-            if (idx < items) {
-                const int row = (int)(((float)idx + 0.5f) * inv_nb);
-                const int j = idx - row * nb;
-                stockham_load<R>(buf + (size_t)(r0 + row) * n, n, Ns, j, tw, DIR, v[q]);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int idx = tid + q * nthr;
-            if (idx < items) {
-                const int row = (int)(((float)idx + 0.5f) * inv_nb);
-                const int j = idx - row * nb;
-                stockham_store<R>(buf + (size_t)(r0 + row) * n, Ns, lgNs, j, DIR, v[q]);
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Block-cooperative in-place FFT of `nrows` sequences of length n
-// (unnormalised; DIR = -1 forward, +1 inverse). The radix plan is radix 16
-// stages and a rest of radix 2, 3, 4, 5, 6, 8, 9, 10 or 12 (or 4 then 6, 4
-// then 5, 8 then 5, 2/4/8 then 9) (fft_radices); written as straight-line code so that
-// each stage keeps its own small register footprint. Q, the butterflies a
-// thread holds at once, is chosen so that a stage covers every row in one
-// round where the registers allow. Supported: every n with fft_fits(n, 512)
-// (2^a <= 4096, 3 * 2^a <= 6144, 5 * 2^a <= 5120, 9 * 2^a <= 2304).
-// One stage with Q butterflies per thread: enough for all rows of the block
-// in one round where the register budget QMAX = fft_qmax(R) allows, and at
-// least enough for one whole sequence (fft_fits guarantees that fits).
-template <int R, int QMAX, int DIR>
-__device__ __forceinline__ void fft_stage_q(cf* buf, int n, int nrows, int Ns, int lgNs, const cf* __restrict__ tw) {
-    const int nb = n / R;
-    const int nthr = (int)blockDim.x;
-    int q = (nb * nrows + nthr - 1) / nthr;
-    q = q > QMAX ? QMAX : q;
-    const int qmin = (nb + nthr - 1) / nthr;
-    q = q < qmin ? qmin : q;
-    if (QMAX >= 4 && q >= 4) fft_stage<R, (QMAX >= 4 ? 4 : 1), DIR>(buf, n, nrows, Ns, lgNs, tw);
-    else if (QMAX >= 3 && q == 3) fft_stage<R, (QMAX >= 3 ? 3 : 1), DIR>(buf, n, nrows, Ns, lgNs, tw);
-    else if (QMAX >= 2 && q == 2) fft_stage<R, (QMAX >= 2 ? 2 : 1), DIR>(buf, n, nrows, Ns, lgNs, tw);
-    else fft_stage<R, 1, DIR>(buf, n, nrows, Ns, lgNs, tw);
-}
-
-template <int DIR>
-__device__ __forceinline__ void block_fft(cf* buf, int n, int nrows, const cf* __restrict__ tw,
-                                          const FftPlan& fp) {
-    // tw: the stage twiddle tables of length n back to back (fft_stage_tables)
-    int Ns = 1, lg = 0;
-    int s = 0;
-    const cf* T = tw;
-    for (; s < fp.nst && fp.rad[s] == 16; ++s) {
-        fft_stage<16, 1, DIR>(buf, n, nrows, Ns, lg, T);
-        T += stage_table_len(Ns, 16);
-        Ns <<= 4;
-        lg += 4;
-    }
-    if (s < fp.nst) {
-        const int R = fp.rad[s];
-        if (R == 12) fft_stage_q<12, 1, DIR>(buf, n, nrows, Ns, lg, T);
-        else if (R == 10) fft_stage_q<10, 1, DIR>(buf, n, nrows, Ns, lg, T);
-        else if (R == 9) fft_stage_q<9, 1, DIR>(buf, n, nrows, Ns, lg, T);
-        else if (R == 8) fft_stage_q<8, 1, DIR>(buf, n, nrows, Ns, lg, T);
-        else if (R == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, T);
-        else if (R == 5) fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, T);
-        else if (R == 4) fft_stage_q<4, 3, DIR>(buf, n, nrows, Ns, lg, T);
-        else if (R == 3) fft_stage_q<3, 4, DIR>(buf, n, nrows, Ns, lg, T);
-        else fft_stage_q<2, 2, DIR>(buf, n, nrows, Ns, lg, T);
-        T += stage_table_len(Ns, R);
-        Ns *= R;
-        lg = 31 - __clz(Ns);
-        ++s;
-    }
-    if (s < fp.nst) {   // after radix 2, 4 or 8 (n / 16^k = 24, 20, 40, 18, 36, 72): radix 6, 5 or 9
-        if (fp.rad[s] == 6) fft_stage_q<6, 2, DIR>(buf, n, nrows, Ns, lg, T);
-        else if (fp.rad[s] == 9) fft_stage_q<9, 1, DIR>(buf, n, nrows, Ns, lg, T);
-        else fft_stage_q<5, 2, DIR>(buf, n, nrows, Ns, lg, T);
-    }
-}
-
 // --------------------------------------------------------------------------
 // Row kernels: scatter into a band of lattice rows, then real FFT of the rows.
 // Shared memory: [R][Prho] floats (rows, viewed as [R][M] complex); the FFT
@@ -178,11 +78,131 @@ __device__ __forceinline__ float load_in(const __nv_bfloat16* p) { return __bflo
 // Real sample n of a row buffer (stored as complex pairs in the sw layout).
 __device__ __forceinline__ int swr(int n) { return 2 * sw(n >> 1) + (n & 1); }
 
-__device__ __forceinline__ void rows_r2c_write(const PieceDev& P, int mb, int nrows) {
+// Row transforms: the real FFT of a lattice row of length Prho (first half
+// of Eq. (7)/(16)) as a complex FFT of the M = Prho / 2 packed pairs
+// z[n] = x[2n] + i x[2n+1], and its inverse, by the in-place decimation in
+// frequency / time of the column pass (dif_plan of M: P.fftM, twiddles
+// P.twM). The forward leaves Z in digit-reversed order; the real-FFT
+// post-processing reads Z[k] and Z[M - k] at their positions (P.rpos), and
+// the inverse's pre-processing writes the packed pairs straight to theirs.
+// One row butterfly per thread, the band's rows back to back in shared
+// memory ([R][M] complex, element i of a row at sw(i)), one barrier per pass.
+template <int R>
+__device__ __forceinline__ void row_fwd(cf x[R], const cf* __restrict__ T, int S, int m) {
+    dft_small<R>(x, -1);
+    if (S > 1) {
+#pragma unroll
+        for (int k = 1; k < R; ++k) x[k] = cmul(x[k], ldcf(T + (k - 1) * S + m));
+    }
+}
+template <int R>
+__device__ __forceinline__ void row_inv(cf x[R], const cf* __restrict__ T, int S, int m) {
+    if (S > 1) {
+#pragma unroll
+        for (int k = 1; k < R; ++k) x[k] = cmulc(x[k], ldcf(T + (k - 1) * S + m));
+    }
+    dft_small<R>(x, +1);
+}
+
+// One pass over every row of the band, in place in shared memory.
+template <int R, bool INV>
+__device__ __forceinline__ void rows_pass(cf* X, int M, int nrows, int S, const cf* __restrict__ T) {
+    const int nb = M / R, tot = nb * nrows;
+    const float inv_nb = 1.0f / (float)nb, invS = 1.0f / (float)S;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int row = (int)(((float)idx + 0.5f) * inv_nb);   // exact for idx < 2^22
+        const int b = idx - row * nb;
+        const int q = (int)(((float)b + 0.5f) * invS);
+        const int m = b - q * S;
+        const int base = q * S * R + m;
+        cf* Z = X + row * M;
+        cf x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = Z[sw(base + r * S)];
+        if (INV) row_inv<R>(x, T, S, m);
+        else row_fwd<R>(x, T, S, m);
+#pragma unroll
+        for (int r = 0; r < R; ++r) Z[sw(base + r * S)] = x[r];
+    }
+}
+
+// Forward pass 0 reading the band's lattice rows (Nr reals each, zero padded)
+// from global memory.
+template <int R>
+__device__ __forceinline__ void rows_first_lat(cf* X, const float* __restrict__ lat, int Nr, int M, int nrows, int S,
+                                               const cf* __restrict__ T) {
+    const int tot = S * nrows;
+    const float invS = 1.0f / (float)S;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int row = (int)(((float)idx + 0.5f) * invS);
+        const int m = idx - row * S;
+        const float* src = lat + (size_t)row * Nr;
+        cf x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int n2 = 2 * (m + r * S);
+            x[r].x = n2 < Nr ? __ldg(src + n2) : 0.f;
+            x[r].y = n2 + 1 < Nr ? __ldg(src + n2 + 1) : 0.f;
+        }
+        row_fwd<R>(x, T, S, m);
+        cf* Z = X + row * M;
+#pragma unroll
+        for (int r = 0; r < R; ++r) Z[sw(m + r * S)] = x[r];
+    }
+}
+
+// Inverse pass 0 writing the band's lattice rows (first Nr reals) to global
+// memory.
+template <int R>
+__device__ __forceinline__ void rows_last_lat(const cf* X, float* lat, int Nr, int M, int nrows, int S,
+                                              const cf* __restrict__ T) {
+    const int tot = S * nrows;
+    const float invS = 1.0f / (float)S;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int row = (int)(((float)idx + 0.5f) * invS);
+        const int m = idx - row * S;
+        const cf* Z = X + row * M;
+        cf x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = Z[sw(m + r * S)];
+        row_inv<R>(x, T, S, m);
+        float* dst = lat + (size_t)row * Nr;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int n2 = 2 * (m + r * S);
+            if (n2 < Nr) dst[n2] = x[r].x;
+            if (n2 + 1 < Nr) dst[n2 + 1] = x[r].y;
+        }
+    }
+}
+
+#define HR_RADIX_CASES(CALL) \
+    case 16: CALL(16); break; \
+    case 12: CALL(12); break; \
+    case 10: CALL(10); break; \
+    case 9: CALL(9); break;   \
+    case 8: CALL(8); break;   \
+    case 6: CALL(6); break;   \
+    case 5: CALL(5); break;   \
+    case 4: CALL(4); break;   \
+    case 3: CALL(3); break;   \
+    default: CALL(2); break;
+
+// Forward passes p0 .. s-1 in shared memory (p0 = 1 after rows_first_lat).
+__device__ __forceinline__ void rows_fwd_passes(cf* X, int M, int nrows, const FftPlan& fp, const cf* T, int p0) {
+    for (int p = p0; p < fp.nst; ++p) {
+#define HR_RF(RR) rows_pass<RR, false>(X, M, nrows, fp.st[p], T + fp.tw[p])
+        switch (fp.rad[p]) { HR_RADIX_CASES(HR_RF) }
+#undef HR_RF
+        __syncthreads();
+    }
+}
+
+// Real-FFT post-processing of the band's transformed rows (digit-reversed in
+// shared memory) into the half spectrum, bins k <= k2max, blocked layout.
+__device__ __forceinline__ void rows_post(const PieceDev& P, const cf* Z0, int mb, int nrows) {
     cf* __restrict__ spec = P.spec;
     const int M = P.Prho / 2;
-    cf* Z = reinterpret_cast<cf*>(smem_f);
-    block_fft<-1>(Z, M, nrows, P.twM, P.fftM);
     const int nk = P.k2max + 1;
     const int per_kb = nrows * P.CB;
     const int total = P.nkb * per_kb;
@@ -193,8 +213,40 @@ __device__ __forceinline__ void rows_r2c_write(const PieceDev& P, int mb, int nr
         const int c = rem - m * P.CB;
         const int k = kb * P.CB + c;
         cf X = {0.f, 0.f};
-        if (k < nk) X = r2c_post(Z + m * M, M, k, P.twP);
+        if (k < nk)
+            X = r2c_post_at(Z0 + m * M, sw(__ldg(P.rpos + k)), sw(__ldg(P.rpos + (k == 0 ? 0 : M - k))), k, P.twP);
         spec[((size_t)kb * P.Ntheta + (mb + m)) * P.CB + c] = X;
+    }
+}
+
+// Inverse: the real-FFT pre-processing of the band's half-spectrum rows
+// (bins above k2max are zero), pairs (k, M - k) for 0 <= k <= M/2, written to
+// their digit-reversed positions in shared memory.
+__device__ __forceinline__ void rows_pre(const PieceDev& P, cf* X, int mb, int nrows) {
+    const cf* __restrict__ spec = P.spec;
+    const int M = P.Prho / 2, half = M / 2;
+    const int nk = P.k2max + 1;
+    const int per_kb = nrows * 2;                 // (row, c) of a column block, c fastest
+    const int total = (half / 2 + 1) * per_kb;    // k = 2 kb + c <= half
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int kb = idx / per_kb;
+        const int rem = idx - kb * per_kb;
+        const int m = rem >> 1;
+        const int k = 2 * kb + (rem & 1);
+        if (k > half) continue;
+        const size_t rowoff = (size_t)(mb + m) * 2;
+        const cf a = k < nk ? ldcf(spec + (size_t)(k >> 1) * P.Ntheta * 2 + rowoff + (k & 1)) : cf{0.f, 0.f};
+        cf* Z = X + m * M;
+        if (k == 0) {
+            Z[sw(__ldg(P.rpos))] = c2r_pre_dc(a);
+            continue;
+        }
+        const int k2 = M - k;
+        const cf b = k2 < nk ? ldcf(spec + (size_t)(k2 >> 1) * P.Ntheta * 2 + rowoff + (k2 & 1)) : cf{0.f, 0.f};
+        cf zk, zmk;
+        c2r_pre_vals(a, b, ldcf(P.twP + k), zk, zmk);
+        Z[sw(__ldg(P.rpos + k))] = zk;
+        Z[sw(__ldg(P.rpos + k2))] = zmk;
     }
 }
 
@@ -420,43 +472,24 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
 }
 
 // Real FFT of a band of lattice rows (P.lat, zero-padded to Prho) into the
-// half spectrum (first half of Eq. (7)/(16)).
+// half spectrum (first half of Eq. (7)/(16)): pass 0 reads the rows from
+// global memory.
 template <class Src>
 __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src B) {
     int bx;
     const PieceDev& P = piece_of(B, bx);
-    if ((size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
+    if (P.CB != 2 || (size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
-    const int Pr = P.Prho, Nr = P.Nrho;
-    // zero padding of every row, then the band's rows (contiguous in P.lat)
-    // with every load of a chunk issued before the first is stored
-    const int pad = Pr - Nr;
-    for (int idx = threadIdx.x; idx < nrows * pad; idx += blockDim.x) {
-        const int m = idx / pad;
-        smem_f[m * Pr + swr(Nr + idx - m * pad)] = 0.f;
-    }
-    const float* __restrict__ src = P.lat + (size_t)mb * Nr;
-    const int tot = nrows * Nr;
-    constexpr int L = 8;
-    for (int i0 = 0; i0 < tot; i0 += L * (int)blockDim.x) {
-        float v[L];
-#pragma unroll
-        for (int q = 0; q < L; ++q) {
-            const int idx = i0 + q * (int)blockDim.x + threadIdx.x;
-            v[q] = idx < tot ? __ldg(src + idx) : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < L; ++q) {
-            const int idx = i0 + q * (int)blockDim.x + threadIdx.x;
-            if (idx < tot) {
-                const int m = idx / Nr;
-                smem_f[m * Pr + swr(idx - m * Nr)] = v[q];
-            }
-        }
-    }
+    const int M = P.Prho / 2;
+    cf* X = reinterpret_cast<cf*>(smem_f);
+    const FftPlan& fp = P.fftM;
+#define HR_RL(RR) rows_first_lat<RR>(X, P.lat + (size_t)mb * P.Nrho, P.Nrho, M, nrows, fp.st[0], P.twM)
+    switch (fp.rad[0]) { HR_RADIX_CASES(HR_RL) }
+#undef HR_RL
     __syncthreads();
-    rows_r2c_write(P, mb, nrows);
+    rows_fwd_passes(X, M, nrows, fp, P.twM, 1);
+    rows_post(P, X, mb, nrows);
 }
 
 // Adjoint of the output interpolation (transpose of Eq. (17)), separated
@@ -582,7 +615,7 @@ template <class Src>
 __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Src B) {
     int band;
     const PieceDev& P = piece_of(B, band);
-    if ((size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
+    if (P.CB != 2 || (size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
     const float* __restrict__ h = P.prof;
     const int hp = P.hpitch;
     const int mb = band * P.R;
@@ -626,7 +659,8 @@ __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Sr
         }
     }
     __syncthreads();
-    rows_r2c_write(P, mb, nrows);
+    rows_fwd_passes(reinterpret_cast<cf*>(smem_f), P.Prho / 2, nrows, P.fftM, P.twM, 0);
+    rows_post(P, reinterpret_cast<const cf*>(smem_f), mb, nrows);
 }
 
 // --------------------------------------------------------------------------
@@ -762,18 +796,6 @@ __device__ __forceinline__ void c1_kernel(cf* A, const FftPlan& fp, const cf* K,
     }
 }
 
-#define HR_RADIX_CASES(CALL) \
-    case 16: CALL(16); break; \
-    case 12: CALL(12); break; \
-    case 10: CALL(10); break; \
-    case 9: CALL(9); break;   \
-    case 8: CALL(8); break;   \
-    case 6: CALL(6); break;   \
-    case 5: CALL(5); break;   \
-    case 4: CALL(4); break;   \
-    case 3: CALL(3); break;   \
-    default: CALL(2); break;
-
 // Shared memory of the column kernel: the column block [Ptheta] (16-byte
 // elements), its slice of K [k1max + 1] (16 bytes each), the twiddle tables
 // (twlen complex, a multiple of 2).
@@ -843,52 +865,31 @@ __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src 
 
 // --------------------------------------------------------------------------
 // Inverse real FFT of a band of rows from the half spectrum (bins <= k2max,
-// the rest zero) into the real lattice P.lat[Ntheta][Nrho].
+// the rest zero) into the real lattice P.lat[Ntheta][Nrho]: the
+// pre-processing reads the spectrum from global memory, the last pass writes
+// the lattice rows.
 // --------------------------------------------------------------------------
 template <class Src>
 __global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ Src B) {
     int bx;
     const PieceDev& P = piece_of(B, bx);
-    if ((size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
-    const cf* __restrict__ spec = P.spec;
+    if (P.CB != 2 || (size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int M = P.Prho / 2;
     cf* X = reinterpret_cast<cf*>(smem_f);
-    const int nk = P.k2max + 1;
-    // zero the bins above k2max, then copy the stored ones in the blocked
-    // layout's order (contiguous rows of the band for each column block)
-    for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
-        const int m = idx / M, k = idx - m * M;
-        if (k >= nk) X[m * M + sw(k)] = cf{0.f, 0.f};
-    }
-    const int per_kb = nrows * P.CB;
-    for (int idx = threadIdx.x; idx < P.nkb * per_kb; idx += blockDim.x) {
-        const int kb = idx / per_kb;
-        const int rem = idx - kb * per_kb;
-        const int m = rem / P.CB, c = rem - m * P.CB;
-        const int k = kb * P.CB + c;
-        if (k < nk) X[m * M + sw(k)] = ldcf(spec + ((size_t)kb * P.Ntheta + mb) * P.CB + rem);
-    }
+    const FftPlan& fp = P.fftM;
+    rows_pre(P, X, mb, nrows);
     __syncthreads();
-    const int half = M / 2;
-    for (int idx = threadIdx.x; idx < nrows * (half + 1); idx += blockDim.x) {
-        const int m = idx / (half + 1), k = idx - m * (half + 1);
-        cf* row = X + m * M;
-        if (k == 0)
-            row[0] = c2r_pre_dc(row[0]);
-        else
-            c2r_pre_pair(row, M, k, P.twP);
+    for (int p = fp.nst - 1; p >= 1; --p) {
+#define HR_RI(RR) rows_pass<RR, true>(X, M, nrows, fp.st[p], P.twM + fp.tw[p])
+        switch (fp.rad[p]) { HR_RADIX_CASES(HR_RI) }
+#undef HR_RI
+        __syncthreads();
     }
-    __syncthreads();
-    block_fft<+1>(X, M, nrows, P.twM, P.fftM);
-    const cf* z = X;
-    const int Nr = P.Nrho;
-    for (int idx = threadIdx.x; idx < nrows * Nr; idx += blockDim.x) {
-        const int m = idx / Nr, n = idx - m * Nr;
-        const cf v = z[m * M + sw(n >> 1)];
-        P.lat[(size_t)(mb + m) * Nr + n] = (n & 1) ? v.y : v.x;
-    }
+#define HR_RW(RR) rows_last_lat<RR>(X, P.lat + (size_t)mb * P.Nrho, P.Nrho, M, nrows, fp.st[0], P.twM)
+    switch (fp.rad[0]) { HR_RADIX_CASES(HR_RW) }
+#undef HR_RW
 }
 
 // --------------------------------------------------------------------------

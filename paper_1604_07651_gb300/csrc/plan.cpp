@@ -70,7 +70,7 @@ const double kTOverlap = 1.25;   // half-width ratio of the time-partition trans
 const double kBetaMin = 1e-3;    // smallest angular opening of a sub-problem
 
 // Smallest FFT length >= n of the form 2^a, 3 * 2^a, 5 * 2^a or 9 * 2^a
-// (18 <= 9 * 2^a <= 2304, the range the block FFT and the real-FFT half
+// (18 <= 9 * 2^a <= 2304, the range the FFT passes and the real-FFT half
 // length handle).
 int fft_size(int n) {
     long best = -1;
@@ -81,17 +81,8 @@ int fft_size(int n) {
     return (int)best;
 }
 
-FftPlan make_fft_plan(int n) {
-    FftPlan fp{};
-    fp.n = n;
-    int rad[32];
-    fp.nst = fft_radices(n, rad);
-    for (int i = 0; i < fp.nst && i < 8; ++i) fp.rad[i] = rad[i];
-    return fp;
-}
-
-// Pass schedule of the column transform pair (decimation in frequency /
-// time, dif_plan): radices, strides and twiddle-table offsets.
+// Pass schedule of an FFT pair by decimation in frequency / time
+// (dif_plan): radices, strides and twiddle-table offsets.
 FftPlan make_dif_fft_plan(int n) {
     FftPlan fp{};
     fp.n = n;
@@ -715,15 +706,16 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.Prho = h.Prho;
     P.k1max = h.k1max;
     P.k2max = h.k2max;
-    // FFT lengths the in-place block FFT handles (512 threads): 2^a <= 4096,
+    // FFT lengths the in-place passes handle: 2^a <= 4096,
     // 3 * 2^a <= 6144, 5 * 2^a <= 5120, 9 * 2^a <= 2304
     auto fft_ok = [](int n) {
-        return ((n % 3 == 0) ? n <= 6144 : (n % 5 == 0) ? n <= 5120 : n <= 4096) && fft_fits(n, 512);
+        int R[kMaxDifPasses], S[kMaxDifPasses];
+        return ((n % 3 == 0) ? n <= 6144 : (n % 5 == 0) ? n <= 5120 : n <= 4096) && dif_plan(n, R, S) > 0;
     };
     if (!fft_ok(h.Prho / 2) || !fft_ok(h.Ptheta))
         return fail(RADON_ERR_UNSUPPORTED,
                     "FFT length " + std::to_string(std::max(h.Prho / 2, h.Ptheta)) +
-                        " above the block FFT's limit (4096, 6144 = 3*2048 or 5120 = 5*1024)");
+                        " above the FFT passes' limit (4096, 6144 = 3*2048 or 5120 = 5*1024)");
     // rows per band: any value up to what shared memory allows gives the same
     // results; the descriptor's choice, else 3 until the plan times them
     const int Rmax = (int)std::min<size_t>(kMaxBandRows, (size_t)smem_max / (h.Prho * sizeof(float)));
@@ -748,7 +740,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     P.Ntau = d.Ntau;
     P.l_lo = h.l_lo;
     P.l_hi = h.l_hi;
-    P.fftM = make_fft_plan(h.Prho / 2);
+    P.fftM = make_dif_fft_plan(h.Prho / 2);
     P.fftT = make_dif_fft_plan(h.Ptheta);
 
     // per-time weight (window, 2 a^2 tb, quadrature and B-spline normalisation)
@@ -807,9 +799,15 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     set_rows(h, R);
     // twiddles
     const int M = h.Prho / 2;
-    std::vector<cf> twM(fft_stage_tables(M, nullptr) + 1), twP(M + 1), twT((fft_dif_tables(h.Ptheta, nullptr) + 2) & ~1);
-    fft_stage_tables(M, twM.data());
+    std::vector<cf> twM(fft_dif_tables(M, nullptr) + 1), twP(M + 1), twT((fft_dif_tables(h.Ptheta, nullptr) + 2) & ~1);
+    fft_dif_tables(M, twM.data());
     fft_dif_tables(h.Ptheta, twT.data());
+    std::vector<int> rpos(M);
+    {
+        int R[kMaxDifPasses], S[kMaxDifPasses];
+        const int s = dif_plan(M, R, S);
+        for (int k = 0; k < M; ++k) rpos[k] = dif_pos(s, R, S, k);
+    }
     P.twT_len = (int)twT.size();
     for (int k = 0; k <= M; ++k)
         twP[k] = {(float)std::cos(-2 * kPi * k / h.Prho), (float)std::sin(-2 * kPi * k / h.Prho)};
@@ -819,7 +817,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     radon_status s = RADON_OK;
     if ((s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
         (s = dev_upload(p, colscale, &P.colscale)) || (s = dev_upload(p, K, &P.K)) ||
-        (s = dev_upload(p, twM, &P.twM)) || (s = dev_upload(p, twP, &P.twP)) ||
+        (s = dev_upload(p, twM, &P.twM)) || (s = dev_upload(p, twP, &P.twP)) || (s = dev_upload(p, rpos, &P.rpos)) ||
         (s = dev_upload(p, twT, &P.twT)))
         return s;
     // position tables, FP64 on the device

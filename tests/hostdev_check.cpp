@@ -1,5 +1,8 @@
-// Host check of the arithmetic the CUDA kernels use (csrc/hostdev.h):
-// Stockham FFT stages, the real-FFT packing pair and the B-spline weights.
+// Host check of the arithmetic the CUDA kernels use (csrc/hostdev.h): the
+// in-place FFT passes (decimation in frequency / time) with their position
+// maps, the real-FFT packing pair on digit-reversed data, the column
+// kernel's transform pair around a pointwise product, the shared-memory
+// swizzles and the B-spline weights.
 // Compiled with g++ by tests/test_hostdev.py; prints "name value"
 // lines (errors) that the test compares with thresholds.
 #include <cmath>
@@ -13,132 +16,9 @@
 using namespace hr;
 typedef std::complex<double> cd;
 
-static std::vector<cf> twiddles(int n) {
-    std::vector<cf> t(n);
-    for (int k = 0; k < n; ++k) t[k] = {(float)std::cos(-2 * M_PI * k / n), (float)std::sin(-2 * M_PI * k / n)};
-    return t;
-}
-
-// The device driver's stage loop, run sequentially, on natural-order data
-// (converted to and from the swizzled shared-memory layout).
-static std::vector<cf> to_sw(const std::vector<cf>& x) {
-    std::vector<cf> y(x.size());
-    for (size_t i = 0; i < x.size(); ++i) y[sw((int)i)] = x[i];
-    return y;
-}
-static std::vector<cf> from_sw(const std::vector<cf>& y) {
-    std::vector<cf> x(y.size());
-    for (size_t i = 0; i < y.size(); ++i) x[i] = y[sw((int)i)];
-    return x;
-}
-
-static std::vector<cf> fft_emul_sw(std::vector<cf> a, int dir) {
-    const int n = (int)a.size();
-    int rad[32];
-    const int nst = fft_radices(n, rad);
-    std::vector<cf> b(n), T(fft_stage_tables(n, nullptr) + 1);
-    fft_stage_tables(n, T.data());
-    int Ns = 1, lg = 0, ofs = 0;
-    for (int s = 0; s < nst; ++s) {
-        const int R = rad[s];
-        const cf* tw = T.data() + ofs;
-        ofs += stage_table_len(Ns, R);
-        for (int j = 0; j < n / R; ++j) {
-            if (R == 16) stockham_butterfly<16>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else if (R == 12) stockham_butterfly<12>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else if (R == 6) stockham_butterfly<6>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else if (R == 10) stockham_butterfly<10>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else if (R == 9) stockham_butterfly<9>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else if (R == 5) stockham_butterfly<5>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else if (R == 8) stockham_butterfly<8>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else if (R == 4) stockham_butterfly<4>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else if (R == 2) stockham_butterfly<2>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-            else stockham_butterfly<3>(a.data(), b.data(), n, Ns, lg, j, tw, dir);
-        }
-        std::swap(a, b);
-        Ns *= R;
-        while ((1 << lg) < Ns) ++lg;
-    }
-    return a;
-}
-
-static std::vector<cf> fft_emul(const std::vector<cf>& a, int dir) {
-    return from_sw(fft_emul_sw(to_sw(a), dir));
-}
-
-static double fft_error(int n, int dir, std::mt19937& rng) {
-    std::normal_distribution<double> N(0, 1);
-    std::vector<cf> x(n);
-    std::vector<cd> xd(n);
-    for (int i = 0; i < n; ++i) {
-        x[i] = {(float)N(rng), (float)N(rng)};
-        xd[i] = cd(x[i].x, x[i].y);
-    }
-    std::vector<cf> y = fft_emul(x, dir);
-    double num = 0, den = 0;
-    for (int k = 0; k < n; ++k) {
-        cd acc = 0;
-        for (int i = 0; i < n; ++i) acc += xd[i] * std::polar(1.0, dir * 2 * M_PI * (double)((long)k * i % n) / n);
-        num += std::norm(acc - cd(y[k].x, y[k].y));
-        den += std::norm(acc);
-    }
-    return std::sqrt(num / den);
-}
-
-// Real FFT through the packed complex FFT: returns max relative error of
-// X_mine / X_true - 2 (the kernels omit the factors 1/2).
-static double rfft_error(int P, std::mt19937& rng) {
-    std::normal_distribution<double> N(0, 1);
-    const int M = P / 2;
-    std::vector<double> x(P);
-    for (auto& v : x) v = N(rng);
-    std::vector<cf> z(M);
-    for (int n = 0; n < M; ++n) z[n] = {(float)x[2 * n], (float)x[2 * n + 1]};
-    std::vector<cf> Z = fft_emul_sw(to_sw(z), -1);
-    std::vector<cf> twP(M + 1);
-    for (int k = 0; k <= M; ++k) twP[k] = {(float)std::cos(-2 * M_PI * k / P), (float)std::sin(-2 * M_PI * k / P)};
-    double num = 0, den = 0;
-    for (int k = 0; k <= M / 2; ++k) {
-        cd acc = 0;
-        for (int n = 0; n < P; ++n) acc += x[n] * std::polar(1.0, -2 * M_PI * (double)((long)k * n % P) / P);
-        cf X = r2c_post(Z.data(), M, k, twP.data());
-        num += std::norm(cd(X.x, X.y) - 2.0 * acc);
-        den += std::norm(2.0 * acc);
-    }
-    return std::sqrt(num / den);
-}
-
-// Inverse: half spectrum with bins 0..kmax (X0 real) -> x; returns the error
-// of x_mine against P * irfft(X) (normalised inverse times P).
-static double irfft_error(int P, int kmax, std::mt19937& rng) {
-    std::normal_distribution<double> N(0, 1);
-    const int M = P / 2;
-    std::vector<cd> Xd(M + 1, 0.0);
-    for (int k = 0; k <= kmax; ++k) Xd[k] = cd(N(rng), k ? N(rng) : 0.0);
-    std::vector<cf> X(M);
-    for (int k = 0; k < M; ++k) X[k] = {(float)Xd[k].real(), (float)Xd[k].imag()};
-    std::vector<cf> twP(M + 1);
-    for (int k = 0; k <= M; ++k) twP[k] = {(float)std::cos(-2 * M_PI * k / P), (float)std::sin(-2 * M_PI * k / P)};
-    X = to_sw(X);
-    X[0] = c2r_pre_dc(X[0]);
-    for (int k = 1; k <= M / 2; ++k) c2r_pre_pair(X.data(), M, k, twP.data());
-    std::vector<cf> z = from_sw(fft_emul_sw(X, +1));
-    double num = 0, den = 0;
-    for (int n = 0; n < P; ++n) {
-        double acc = Xd[0].real();
-        for (int k = 1; k < M; ++k) acc += 2.0 * (Xd[k] * std::polar(1.0, 2 * M_PI * (double)((long)k * n % P) / P)).real();
-        const double mine = (n & 1) ? z[n >> 1].y : z[n >> 1].x;
-        num += (mine - acc) * (mine - acc);
-        den += acc * acc;
-    }
-    return std::sqrt(num / den);
-}
-
-// The column kernel's transform pair, run sequentially in place: forward
-// passes by decimation in frequency, product with a spectrum K at each
-// position's digit-reversed frequency, inverse passes by decimation in time.
-// Returns the relative L2 error against n * IDFT(K .* DFT(x)) in FP64, and
-// counts positions whose frequency map is not a permutation.
+// The kernels' in-place passes (dif_plan order), run sequentially on a
+// sequence in natural order: forward passes leave digit-reversed order,
+// inverse passes take it.
 template <int R>
 static void dif_pass(std::vector<cf>& a, int S, const cf* T, int b, bool inverse) {
     const int base = dif_base(R, S, b);
@@ -172,12 +52,131 @@ static void dif_pass_any(int R, std::vector<cf>& a, int S, const cf* T, int b, b
     }
 }
 
+struct DifRun {
+    int s, R[kMaxDifPasses], S[kMaxDifPasses];
+    std::vector<cf> T;
+    std::vector<int> off;
+    explicit DifRun(int n) {
+        s = dif_plan(n, R, S);
+        T.resize(fft_dif_tables(n, nullptr) + 1);
+        fft_dif_tables(n, T.data());
+        int ofs = 0;
+        for (int p = 0; p < s; ++p) {
+            off.push_back(ofs);
+            ofs += stage_table_len(S[p], R[p]);
+        }
+    }
+    void forward(std::vector<cf>& a) const {
+        for (int p = 0; p < s; ++p)
+            for (int b = 0; b < (int)a.size() / R[p]; ++b) dif_pass_any(R[p], a, S[p], T.data() + off[p], b, false);
+    }
+    void inverse(std::vector<cf>& a) const {
+        for (int p = s - 1; p >= 0; --p)
+            for (int b = 0; b < (int)a.size() / R[p]; ++b) dif_pass_any(R[p], a, S[p], T.data() + off[p], b, true);
+    }
+};
+
+// Forward passes read back in natural order through dif_pos, and inverse
+// passes on a digit-reversed input, against a direct DFT.
+static double fft_error(int n, int dir, std::mt19937& rng) {
+    std::normal_distribution<double> N(0, 1);
+    DifRun D(n);
+    std::vector<cf> x(n);
+    std::vector<cd> xd(n);
+    for (int i = 0; i < n; ++i) {
+        x[i] = {(float)N(rng), (float)N(rng)};
+        xd[i] = cd(x[i].x, x[i].y);
+    }
+    std::vector<cf> y(n);
+    if (dir < 0) {
+        std::vector<cf> a = x;
+        D.forward(a);
+        for (int k = 0; k < n; ++k) y[k] = a[dif_pos(D.s, D.R, D.S, k)];
+    } else {
+        std::vector<cf> a(n);
+        for (int k = 0; k < n; ++k) a[dif_pos(D.s, D.R, D.S, k)] = x[k];
+        D.inverse(a);
+        y = a;
+    }
+    double num = 0, den = 0;
+    for (int k = 0; k < n; ++k) {
+        cd acc = 0;
+        for (int i = 0; i < n; ++i) acc += xd[i] * std::polar(1.0, dir * 2 * M_PI * (double)((long)k * i % n) / n);
+        num += std::norm(acc - cd(y[k].x, y[k].y));
+        den += std::norm(acc);
+    }
+    return std::sqrt(num / den);
+}
+
+// The row kernels' real FFT: the packed pairs through the forward passes,
+// then r2c_post_at at the positions of k and M - k; returns the error of
+// X_mine against 2 X_true (the kernels omit the factors 1/2).
+static double rfft_error(int P, std::mt19937& rng) {
+    std::normal_distribution<double> N(0, 1);
+    const int M = P / 2;
+    DifRun D(M);
+    std::vector<double> x(P);
+    for (auto& v : x) v = N(rng);
+    std::vector<cf> z(M);
+    for (int n = 0; n < M; ++n) z[n] = {(float)x[2 * n], (float)x[2 * n + 1]};
+    D.forward(z);
+    std::vector<cf> twP(M + 1);
+    for (int k = 0; k <= M; ++k) twP[k] = {(float)std::cos(-2 * M_PI * k / P), (float)std::sin(-2 * M_PI * k / P)};
+    double num = 0, den = 0;
+    for (int k = 0; k < M; ++k) {
+        cd acc = 0;
+        for (int n = 0; n < P; ++n) acc += x[n] * std::polar(1.0, -2 * M_PI * (double)((long)k * n % P) / P);
+        const int pk = dif_pos(D.s, D.R, D.S, k), pmk = dif_pos(D.s, D.R, D.S, k == 0 ? 0 : M - k);
+        cf X = r2c_post_at(z.data(), pk, pmk, k, twP.data());
+        num += std::norm(cd(X.x, X.y) - 2.0 * acc);
+        den += std::norm(2.0 * acc);
+    }
+    return std::sqrt(num / den);
+}
+
+// Inverse: half spectrum with bins 0..kmax (X0 real), c2r_pre_vals on the
+// pairs (k, M - k), k <= M/2, written at their positions, inverse passes;
+// returns the error of x_mine against P * irfft(X).
+static double irfft_error(int P, int kmax, std::mt19937& rng) {
+    std::normal_distribution<double> N(0, 1);
+    const int M = P / 2;
+    DifRun D(M);
+    std::vector<cd> Xd(M + 1, 0.0);
+    for (int k = 0; k <= kmax; ++k) Xd[k] = cd(N(rng), k ? N(rng) : 0.0);
+    auto X = [&](int k) { return cf{(float)Xd[k].real(), (float)Xd[k].imag()}; };
+    std::vector<cf> twP(M + 1);
+    for (int k = 0; k <= M; ++k) twP[k] = {(float)std::cos(-2 * M_PI * k / P), (float)std::sin(-2 * M_PI * k / P)};
+    std::vector<cf> z(M, cf{0.f, 0.f});
+    for (int k = 0; k <= M / 2; ++k) {
+        if (k == 0) {
+            z[dif_pos(D.s, D.R, D.S, 0)] = c2r_pre_dc(X(0));
+            continue;
+        }
+        cf zk, zmk;
+        c2r_pre_vals(X(k), X(M - k), twP[k], zk, zmk);
+        z[dif_pos(D.s, D.R, D.S, k)] = zk;
+        z[dif_pos(D.s, D.R, D.S, M - k)] = zmk;
+    }
+    D.inverse(z);
+    double num = 0, den = 0;
+    for (int n = 0; n < P; ++n) {
+        double acc = Xd[0].real();
+        for (int k = 1; k < M; ++k) acc += 2.0 * (Xd[k] * std::polar(1.0, 2 * M_PI * (double)((long)k * n % P) / P)).real();
+        const double mine = (n & 1) ? z[n >> 1].y : z[n >> 1].x;
+        num += (mine - acc) * (mine - acc);
+        den += acc * acc;
+    }
+    return std::sqrt(num / den);
+}
+
+// The column kernel's transform pair: forward passes, product with a
+// spectrum K at each position's frequency, inverse passes; returns the
+// relative L2 error against n * IDFT(K .* DFT(x)) in FP64, and counts
+// positions whose frequency map is not a permutation or not inverted by
+// dif_pos.
 static double dif_conv_error(int n, std::mt19937& rng, int& bad_freq) {
     std::normal_distribution<double> N(0, 1);
-    int R[kMaxDifPasses], S[kMaxDifPasses];
-    const int s = dif_plan(n, R, S);
-    std::vector<cf> T(fft_dif_tables(n, nullptr) + 1);
-    fft_dif_tables(n, T.data());
+    DifRun D(n);
     std::vector<cf> a(n), K(n);
     std::vector<cd> xd(n), Kd(n);
     for (int i = 0; i < n; ++i) {
@@ -186,22 +185,14 @@ static double dif_conv_error(int n, std::mt19937& rng, int& bad_freq) {
         K[i] = {(float)N(rng), (float)N(rng)};
         Kd[i] = cd(K[i].x, K[i].y);
     }
-    int ofs = 0;
-    std::vector<int> off(s);
-    for (int p = 0; p < s; ++p) {
-        off[p] = ofs;
-        ofs += stage_table_len(S[p], R[p]);
-    }
-    for (int p = 0; p < s; ++p)
-        for (int b = 0; b < n / R[p]; ++b) dif_pass_any(R[p], a, S[p], T.data() + off[p], b, false);
+    D.forward(a);
     std::vector<int> seen(n, 0);
     for (int pos = 0; pos < n; ++pos) {
-        const int f = dif_freq(s, R, S, pos);
-        if (f < 0 || f >= n || seen[f]++) ++bad_freq;
+        const int f = dif_freq(D.s, D.R, D.S, pos);
+        if (f < 0 || f >= n || seen[f]++ || dif_pos(D.s, D.R, D.S, f) != pos) ++bad_freq;
         else a[pos] = cmul(a[pos], K[f]);
     }
-    for (int p = s - 1; p >= 0; --p)
-        for (int b = 0; b < n / R[p]; ++b) dif_pass_any(R[p], a, S[p], T.data() + off[p], b, true);
+    D.inverse(a);
     std::vector<cd> X(n);
     for (int k = 0; k < n; ++k) {
         cd acc = 0;
@@ -274,13 +265,5 @@ int main() {
     }
     std::printf("swizzle_violations %d\n", bad);
     std::printf("fft_lengths %d\n", nlen);
-    // every length within the limits fits the 512-thread block FFT
-    int nofit = 0;
-    for (int n = 2; n <= 6144; ++n) {
-        int rad[32];
-        if (fft_radices(n, rad) < 0 || (n % 3 == 0 ? n > 6144 : n % 5 == 0 ? n > 5120 : n > 4096)) continue;
-        if (!fft_fits(n, 512)) ++nofit;
-    }
-    std::printf("fft_sizes_not_fitting %d\n", nofit);
     return 0;
 }
