@@ -107,6 +107,10 @@ typedef struct {
     int Ptheta, Prho;        /* zero-padded FFT sizes */
     int k1max, k2max;        /* frequency rectangle L in bins */
     double theta_m;          /* kernel window |theta| <= theta_m */
+    /* forward gridding work split (0 from radon_geometry, which builds no tables):
+       lattice tiles, work units, tiles cut into several units, and the most
+       chunks (runs of <= 8 samples of one trace) one tile holds */
+    int grid_tiles, grid_units, grid_split_tiles, grid_max_tile_chunks;
 } radon_piece_info;
 
 /*

@@ -29,7 +29,9 @@ class RadonPieceInfo(ctypes.Structure):
                 ("dphi_rule", _c_double), ("deta_rule", _c_double), ("dtheta", _c_double),
                 ("drho", _c_double), ("theta0", _c_double), ("rho0", _c_double),
                 ("Ntheta", _c_int), ("Nrho", _c_int), ("Ptheta", _c_int), ("Prho", _c_int),
-                ("k1max", _c_int), ("k2max", _c_int), ("theta_m", _c_double)]
+                ("k1max", _c_int), ("k2max", _c_int), ("theta_m", _c_double),
+                ("grid_tiles", _c_int), ("grid_units", _c_int), ("grid_split_tiles", _c_int),
+                ("grid_max_tile_chunks", _c_int)]
 
 
 # every symbol include/hradon.h declares, with its ctypes signature

@@ -63,6 +63,11 @@ struct PieceDev {
     int ntr, ntc;           // lattice tiles of the forward gridding: rows, columns
     int nunits;             // work units of the forward gridding
     const int4* units;      // (tile, first chunk, end chunk, 28 - ilogb(cell weight bound)), heaviest first
+    const int4* uslot;      // per unit: (first slot of its tile, units of the tile, its index among them,
+                            // counter of the tile); tiles of one unit: (0, 1, 0, -1)
+    float* slots;           // [nslots][kTileRows * kTileCols] partial tiles of the split tiles
+    int nslots;             // units of split tiles (tiles cut into several units)
+    int ncount;             // split tiles: their counters follow the lattice, [ncount] ints
     const int4* chunks;     // (trace k, first sample j, count <= 8, 0), grouped by tile
     const int2* lband;      // [nbands] candidate output-column range of each band
     const int* colsh;       // [ncol] 28 - ilogb(cell weight bound) of the adjoint column profiles

@@ -19,9 +19,10 @@
 // FP64 (k_sample_table, k_radon_table) and stores first tap and fractional
 // part, so the transforms themselves are FP32 loads, B-spline weights and
 // sums. Shared-memory accumulation is fixed point (integer atomics, order
-// independent); the gridding's work units meet on the lattice through FP32
-// global atomics, so the last bits of the forward lattice depend on the order
-// in which units finish. The adjoint has no floating-point atomics.
+// independent); a lattice tile cut into several gridding work units is
+// summed from their partial tiles in a fixed order by the last unit to
+// finish. No kernel uses floating-point atomics: the forward and the adjoint
+// are bitwise reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -373,6 +374,51 @@ __device__ __forceinline__ void slide_cols_left(int* t, float acc[16]) {
     }
 }
 
+// Split tiles: the unit's partial tile (value(i) of cell i, row-major over
+// the kTileRows x kTileCols cells) goes to its slot; the unit that finds it
+// is the tile's last to arrive (the others' slots are then complete and
+// visible: each writer fences before it counts) sums every slot of the tile
+// in slot order into the lattice and clears the counter. The result does
+// not depend on which unit runs first.
+template <class F>
+__device__ __forceinline__ void grid_merge_split(const PieceDev& P, int4 us, int m_lo, int n_lo, int nr, int nc,
+                                                 F&& value) {
+    __shared__ int s_last;
+    constexpr int kCells = kTileRows * kTileCols;
+    float* slot0 = P.slots + (size_t)us.x * kCells;
+    for (int i = threadIdx.x; i < kCells; i += blockDim.x) slot0[(size_t)us.z * kCells + i] = value(i);
+    __threadfence();
+    __syncthreads();
+    int* counter = reinterpret_cast<int*>(P.lat + (size_t)P.Ntheta * P.Nrho) + us.w;
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1) == us.y - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // each thread sums its kCells / kUnitChunks cells over the slots in slot
+    // order, all its cells' loads of two slots in flight together
+    constexpr int kPer = kCells / kUnitChunks;
+    static_assert(kCells % kUnitChunks == 0, "cells per thread");
+    float acc[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) acc[j] = 0.f;
+    const float* src = slot0 + threadIdx.x;
+#pragma unroll 2
+    for (int u = 0; u < us.y; ++u) {
+        float v[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) v[j] = __ldcg(src + (size_t)u * kCells + j * kUnitChunks);
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) acc[j] += v[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int i = threadIdx.x + j * kUnitChunks;
+        const int m = i / kTileCols, n = i - m * kTileCols;
+        if (m < nr && n < nc) P.lat[(size_t)(m_lo + m) * P.Nrho + n_lo + n] = acc[j];
+    }
+    if (threadIdx.x == 0) *counter = 0;
+}
+
 template <class Src, class T>
 __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_constant__ Src B,
                                                                const T* __restrict__ f) {
@@ -413,12 +459,17 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
         }
     }
     vmax = block_max_abs(vmax, red);   // also orders the tile's zeroing before the adds
-    if (vmax == 0.f) return;
+    const int4 us = __ldg(P.uslot + bx);  // (first slot, units of the tile, index, counter)
     const int nr = min(kTileRows, P.Ntheta - m_lo), nc = min(kTileCols, P.Nrho - n_lo);
-    if (!(vmax <= 3.402823466e38f)) {
-        for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
-            const int m = i / kTileCols, n = i - m * kTileCols;
-            if (m < nr && n < nc) P.lat[(size_t)(m_lo + m) * P.Nrho + n_lo + n] = __int_as_float(0x7fc00000);
+    if (!(vmax > 0.f && vmax <= 3.402823466e38f)) {   // all zero (nothing to add) or not finite (NaN tile)
+        const float fill = vmax == 0.f ? 0.f : __int_as_float(0x7fc00000);
+        if (us.y > 1) {
+            grid_merge_split(P, us, m_lo, n_lo, nr, nc, [&](int) { return fill; });
+        } else if (fill != 0.f) {
+            for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
+                const int m = i / kTileCols, n = i - m * kTileCols;
+                if (m < nr && n < nc) P.lat[(size_t)(m_lo + m) * P.Nrho + n_lo + n] = fill;
+            }
         }
         return;
     }
@@ -464,10 +515,15 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
     }
     if (win != nullptr) flush_window(win, acc);
     __syncthreads();
-    for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {
+    if (us.y > 1) {
+        grid_merge_split(P, us, m_lo, n_lo, nr, nc,
+                         [&](int i) { return sc.down(tile[(i / kTileCols + kHalo) * kTilePitch + i % kTileCols + kHalo]); });
+        return;
+    }
+    for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {   // the tile's only unit
         const int m = i / kTileCols, n = i - m * kTileCols;
         const int t = tile[(m + kHalo) * kTilePitch + n + kHalo];
-        if (t != 0 && m < nr && n < nc) atomicAdd(P.lat + (size_t)(m_lo + m) * P.Nrho + n_lo + n, sc.down(t));
+        if (t != 0 && m < nr && n < nc) P.lat[(size_t)(m_lo + m) * P.Nrho + n_lo + n] = sc.down(t);
     }
 }
 

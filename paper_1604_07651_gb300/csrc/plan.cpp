@@ -282,6 +282,7 @@ struct HostPiece {
     double dtheta = 0, drho = 0, theta0 = 0, rho0 = 0, theta_m = 0;
     std::vector<int> jfirst;
     int Rmax = 1;                                  // most rows per band shared memory allows
+    int max_tile_chunks = 0;                       // most gridding chunks of one tile
     const int2* lband_R[kMaxBandRows + 1] = {};    // band column ranges for each rows-per-band
     PieceDev dev{};
 };
@@ -618,7 +619,7 @@ radon_status kernel_spectrum(radon_plan_s* p, const HostPiece& h, int CB, int nk
 // for every tile, the chunks of at most 8 consecutive samples of one trace
 // whose 4x4 footprint meets it (along a trace the footprint moves
 // monotonically, so each trace meets a tile in one run of samples).
-radon_status build_tile_lists(radon_plan_s* p, const HostPiece& h, PieceDev& P) {
+radon_status build_tile_lists(radon_plan_s* p, HostPiece& h, PieceDev& P) {
     const int TR = kTileRows, TC = kTileCols;
     P.ntr = (h.Ntheta + TR - 1) / TR;
     P.ntc = (h.Nrho + TC - 1) / TC;
@@ -683,14 +684,43 @@ radon_status build_tile_lists(radon_plan_s* p, const HostPiece& h, PieceDev& P) 
             uwork.push_back(w);
         }
     }
+    // tiles cut into several units: one partial-tile slot per unit (in chunk
+    // order) and one arrival counter per tile; the last unit to finish sums
+    // the slots in slot order, so the lattice does not depend on the order in
+    // which units run
+    for (int t = 0; t < ntiles; ++t) h.max_tile_chunks = std::max(h.max_tile_chunks, (int)runs[t].size());
+    std::vector<int> nper(ntiles, 0), slot0(ntiles, 0), cidx(ntiles, -1), seen(ntiles, 0);
+    for (const int4& u : units) nper[u.x]++;
+    int nslots = 0, ncount = 0;
+    for (int t = 0; t < ntiles; ++t)
+        if (nper[t] > 1) {
+            slot0[t] = nslots;
+            nslots += nper[t];
+            cidx[t] = ncount++;
+        }
+    std::vector<int4> uslot(units.size());
+    for (size_t i = 0; i < units.size(); ++i) {
+        const int t = units[i].x;
+        uslot[i] = nper[t] > 1 ? int4{slot0[t], nper[t], seen[t]++, cidx[t]} : int4{0, 1, 0, -1};
+    }
     std::vector<int> order(units.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return uwork[x] > uwork[y]; });
-    std::vector<int4> sorted(units.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
+    std::vector<int4> sorted(units.size()), sorted_slot(units.size());
+    for (size_t i = 0; i < order.size(); ++i) {
+        sorted[i] = units[order[i]];
+        sorted_slot[i] = uslot[order[i]];
+    }
     P.nunits = (int)sorted.size();
+    P.nslots = nslots;
+    P.ncount = ncount;
     radon_status s = RADON_OK;
-    if ((s = dev_upload(p, flat, &P.chunks)) || (s = dev_upload(p, sorted, &P.units))) return s;
+    if ((s = dev_upload(p, flat, &P.chunks)) || (s = dev_upload(p, sorted, &P.units)) ||
+        (s = dev_upload(p, sorted_slot, &P.uslot)))
+        return s;
+    void* slots = nullptr;
+    if ((s = dev_alloc(p, (size_t)std::max(nslots, 1) * TR * TC * sizeof(float), &slots))) return s;
+    P.slots = (float*)slots;
     return RADON_OK;
 }
 
@@ -894,7 +924,12 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
 }
 
 size_t round256b(size_t v) { return (v + 255) & ~(size_t)255; }
-size_t piece_lattice_bytes(const PieceDev& P) { return round256b((size_t)P.Ntheta * P.Nrho * sizeof(float)); }
+// The lattice of a piece followed by the arrival counters of its split
+// gridding tiles (cleared together before every forward gridding).
+size_t piece_lattice_bytes(const PieceDev& P) {
+    return round256b((size_t)P.Ntheta * P.Nrho * sizeof(float) + (size_t)P.ncount * sizeof(int));
+}
+size_t piece_slot_bytes(const PieceDev& P) { return round256b((size_t)P.nslots * kTileRows * kTileCols * sizeof(float)); }
 size_t piece_spectrum_bytes(const PieceDev& P) { return round256b((size_t)P.nkb * P.CB * P.Ntheta * sizeof(cf)); }
 size_t piece_profile_bytes(const PieceDev& P) {
     return round256b((size_t)(P.l_hi - P.l_lo + 1) * P.hpitch * sizeof(float));
@@ -1356,6 +1391,10 @@ static void fill_info(const HostPiece& h, radon_piece_info* info) {
     info->k1max = h.k1max;
     info->k2max = h.k2max;
     info->theta_m = h.theta_m;
+    info->grid_tiles = h.dev.ntr * h.dev.ntc;
+    info->grid_units = h.dev.nunits;
+    info->grid_split_tiles = h.dev.ncount;
+    info->grid_max_tile_chunks = h.max_tile_chunks;
 }
 
 extern "C" radon_status radon_plan_piece_info(radon_plan p, int piece, radon_piece_info* info) {
@@ -1760,8 +1799,9 @@ extern "C" radon_status radon_batch_adj(radon_batch b, const float* g, float* f,
 // ---------------------------------------------------------------------------
 // Forward transform on caller-given work memory (used by radon_fwd_noalloc in
 // noalloc.cu). Layout of the area: the device copies of the piece
-// descriptors, every piece's lattice back to back, then every piece's
-// spectrum, each 256-byte aligned. Every byte the kernels read there is
+// descriptors, every piece's lattice (with its gridding counters) back to
+// back, then every piece's spectrum, then every piece's gridding slots, each
+// 256-byte aligned. Every byte the kernels read there is
 // written earlier in the same call, so nothing has to be cleared beforehand.
 // ---------------------------------------------------------------------------
 namespace hr {
@@ -1773,7 +1813,7 @@ int plan_device(const radon_plan_s* p) { return p->device; }
 int plan_forward_work_bytes(const radon_plan_s* p, size_t* bytes) {
     if (!p || !bytes) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
     size_t b = round256b(p->pieces.size() * sizeof(PieceDev));
-    for (auto& h : p->pieces) b += piece_lattice_bytes(h.dev) + piece_spectrum_bytes(h.dev);
+    for (auto& h : p->pieces) b += piece_lattice_bytes(h.dev) + piece_spectrum_bytes(h.dev) + piece_slot_bytes(h.dev);
     *bytes = b;
     return RADON_OK;
 }
@@ -1807,6 +1847,10 @@ int plan_forward_in_work(radon_plan_s* p, const float* f, float* g, void* work, 
     for (int i = 0; i < np; ++i) {
         local[i].spec = (cf*)(base + off);
         off += piece_spectrum_bytes(local[i]);
+    }
+    for (int i = 0; i < np; ++i) {
+        local[i].slots = (float*)(base + off);
+        off += piece_slot_bytes(local[i]);
     }
     DeviceGuard guard(p->device);
     if (radon_status s = cuda_status(launch_write_pieces(local, np, dpieces, stream), "piece descriptors"))

@@ -332,3 +332,31 @@ def test_rows_per_band_choices_and_tuner(hr):
     for R in (0, 1, 2, 4, 5, 6):
         assert _rel(outs[R][0], outs[3][0].astype(np.float64)) < 1e-6
         assert _rel(outs[R][1], outs[3][1].astype(np.float64)) < 1e-6
+
+
+def test_forward_and_adjoint_are_bitwise_reproducible(hr):
+    """No floating-point atomics anywhere: repeated transforms of the same
+    input give the same bits. The 2048^2 benchmark plan has gridding tiles
+    cut into several work units (the dense small-t samples), whose partial
+    tiles are summed in a fixed order; other launches run in between so that
+    the units are scheduled differently."""
+    geo, f = synth.sweep_gather(2048, noise=0.05)
+    plan, _ = _pair(hr, geo, rows_per_band=0)
+    ft = _cuda(f)
+    gg = _cuda(synth.smooth_radon_image(geo, 77))
+    g0, a0 = plan.forward(ft), plan.adjoint(gg)
+    noise = torch.empty(1 << 24, device="cuda")
+    for i in range(3):
+        noise.normal_()                       # unrelated work between the calls
+        assert torch.equal(plan.forward(ft), g0), i
+        assert torch.equal(plan.adjoint(gg), a0), i
+    plan.close()
+    geos = synth.batch_geometries(8)
+    b = hr.Batch([dict(Nt=g.Nt, Nx=g.Nx, Ntau=g.Ntau, Nq=g.Nq, dt=g.dt, dx=g.dx, qmin=g.qmin, qmax=g.qmax)
+                  for g in geos])
+    fb = b.pack([torch.tensor(synth.batch_gather(g, i), dtype=torch.float32) for i, g in enumerate(geos)])
+    r0 = b.forward(fb).clone()
+    for _ in range(3):
+        noise.normal_()
+        assert torch.equal(b.forward(fb), r0)
+    b.close()
