@@ -143,14 +143,14 @@ PROFILE_EVERY = 4   # eager steps with per-stage kernel events: one per PROFILE_
 
 MEASURED_TRAFFIC = {
     # kernel: (kernel_source_digest() when measured, bytes per launch averaged over a step's launches)
-    "k_grid_tiles": ("f643e63a17886cc7", 127.38e6),
-    "k_rows_r2c": ("f643e63a17886cc7", 28.30e6),
-    "k_colconv": ("f643e63a17886cc7", 48.06e6),
-    "k_rows_c2r": ("f643e63a17886cc7", 27.50e6),
-    "k_interp_columns": ("f643e63a17886cc7", 100.96e6),
-    "k_col_profiles": ("f643e63a17886cc7", 107.12e6),
-    "k_band_rows": ("f643e63a17886cc7", 45.60e6),
-    "k_gather_samples": ("f643e63a17886cc7", 105.21e6),
+    "k_grid_tiles": ("3386401af41f00ec", 127.48e6),
+    "k_rows_r2c": ("3386401af41f00ec", 28.50e6),
+    "k_colconv": ("3386401af41f00ec", 48.37e6),
+    "k_rows_c2r": ("3386401af41f00ec", 28.91e6),
+    "k_interp_columns": ("3386401af41f00ec", 102.15e6),
+    "k_col_profiles": ("3386401af41f00ec", 108.89e6),
+    "k_band_rows": ("3386401af41f00ec", 46.22e6),
+    "k_gather_samples": ("3386401af41f00ec", 106.87e6),
 }
 
 # FFT kernels run out of shared memory and are limited by instruction issue,
