@@ -1018,19 +1018,38 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
     __syncthreads();
     // rho taps: every output sums its pieces in piece order
     float* gl = g + (np_all > 0 ? 0 : pieces[c.x].g_off) + (size_t)l * Ntau;
-    for (int i = threadIdx.x; i < Ntau; i += blockDim.x) {
-        float acc = 0.f;
+    // each thread takes U outputs at once and loads their table entries of a
+    // piece together before using any (the entries come from DRAM and each
+    // output's taps wait on its entry: U chains in flight instead of one)
+    constexpr int U = 4;
+    for (int i0 = threadIdx.x; i0 < Ntau; i0 += U * blockDim.x) {
+        float acc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = 0.f;
         for (int p = 0; p < np; ++p) {
             const int2 rg = s_rg[p];
-            if (i < rg.x || i > rg.y) continue;
-            const int2 e = __ldg(s_rt[p] + i);
-            if (e.x < 0) continue;
-            float wr[4];
-            b3_weights(__int_as_float(e.y), wr);
-            const float* r = smem_f + p * nrho_max + e.x;
-            acc += s_sc[p] * (wr[0] * r[0] + wr[1] * r[1] + wr[2] * r[2] + wr[3] * r[3]);
+            int2 e[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * (int)blockDim.x;
+                e[u] = (i >= rg.x && i <= rg.y) ? __ldg(s_rt[p] + i) : make_int2(-1, 0);
+            }
+            const float scp = s_sc[p];
+            const float* rp = smem_f + p * nrho_max;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (e[u].x < 0) continue;
+                float wr[4];
+                b3_weights(__int_as_float(e[u].y), wr);
+                const float* r = rp + e[u].x;
+                acc[u] += scp * (wr[0] * r[0] + wr[1] * r[1] + wr[2] * r[2] + wr[3] * r[3]);
+            }
         }
-        gl[i] = acc;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i < Ntau) gl[i] = acc[u];
+        }
     }
 }
 
