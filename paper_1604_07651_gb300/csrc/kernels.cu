@@ -88,6 +88,15 @@ __device__ __forceinline__ int swr(int n) { return 2 * sw(n >> 1) + (n & 1); }
 // the inverse's pre-processing writes the packed pairs straight to theirs.
 // One row butterfly per thread, the band's rows back to back in shared
 // memory ([R][M] complex, element i of a row at sw(i)), one barrier per pass.
+// Stride between the band's rows in shared memory, in complex elements: one
+// element of padding, so that the same position of the band's rows falls in
+// different banks (M is a multiple of 16).
+__host__ __device__ __forceinline__ int row_stride(int M) { return M + 1; }
+// Shared memory of the row kernels: R rows of row_stride(Prho / 2) complex.
+__host__ __device__ __forceinline__ size_t rows_smem(const PieceDev& P) {
+    return (size_t)P.R * row_stride(P.Prho / 2) * sizeof(cf);
+}
+
 template <int R>
 __device__ __forceinline__ void row_fwd(cf x[R], const cf* __restrict__ T, int S, int m) {
     dft_small<R>(x, -1);
@@ -116,7 +125,7 @@ __device__ __forceinline__ void rows_pass(cf* X, int M, int nrows, int S, const 
         const int q = (int)(((float)b + 0.5f) * invS);
         const int m = b - q * S;
         const int base = q * S * R + m;
-        cf* Z = X + row * M;
+        cf* Z = X + row * row_stride(M);
         cf x[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = Z[sw(base + r * S)];
@@ -146,7 +155,7 @@ __device__ __forceinline__ void rows_first_lat(cf* X, const float* __restrict__ 
             x[r].y = n2 + 1 < Nr ? __ldg(src + n2 + 1) : 0.f;
         }
         row_fwd<R>(x, T, S, m);
-        cf* Z = X + row * M;
+        cf* Z = X + row * row_stride(M);
 #pragma unroll
         for (int r = 0; r < R; ++r) Z[sw(m + r * S)] = x[r];
     }
@@ -162,7 +171,7 @@ __device__ __forceinline__ void rows_last_lat(const cf* X, float* lat, int Nr, i
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
         const int row = (int)(((float)idx + 0.5f) * invS);
         const int m = idx - row * S;
-        const cf* Z = X + row * M;
+        const cf* Z = X + row * row_stride(M);
         cf x[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = Z[sw(m + r * S)];
@@ -215,7 +224,8 @@ __device__ __forceinline__ void rows_post(const PieceDev& P, const cf* Z0, int m
         const int k = kb * P.CB + c;
         cf X = {0.f, 0.f};
         if (k < nk)
-            X = r2c_post_at(Z0 + m * M, sw(__ldg(P.rpos + k)), sw(__ldg(P.rpos + (k == 0 ? 0 : M - k))), k, P.twP);
+            X = r2c_post_at(Z0 + m * row_stride(M), sw(__ldg(P.rpos + k)), sw(__ldg(P.rpos + (k == 0 ? 0 : M - k))), k,
+                            P.twP);
         spec[((size_t)kb * P.Ntheta + (mb + m)) * P.CB + c] = X;
     }
 }
@@ -229,25 +239,40 @@ __device__ __forceinline__ void rows_pre(const PieceDev& P, cf* X, int mb, int n
     const int nk = P.k2max + 1;
     const int per_kb = nrows * 2;                 // (row, c) of a column block, c fastest
     const int total = (half / 2 + 1) * per_kb;    // k = 2 kb + c <= half
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int kb = idx / per_kb;
-        const int rem = idx - kb * per_kb;
-        const int m = rem >> 1;
-        const int k = 2 * kb + (rem & 1);
-        if (k > half) continue;
-        const size_t rowoff = (size_t)(mb + m) * 2;
-        const cf a = k < nk ? ldcf(spec + (size_t)(k >> 1) * P.Ntheta * 2 + rowoff + (k & 1)) : cf{0.f, 0.f};
-        cf* Z = X + m * M;
-        if (k == 0) {
-            Z[sw(__ldg(P.rpos))] = c2r_pre_dc(a);
-            continue;
+    constexpr int U = 4;                          // pairs per thread whose spectrum loads go out together
+    for (int i0 = threadIdx.x; i0 < total; i0 += U * blockDim.x) {
+        cf a[U], b[U];
+        int kk[U], mm[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = i0 + u * (int)blockDim.x;
+            const int kb = idx / per_kb;
+            const int rem = idx - kb * per_kb;
+            const int m = rem >> 1;
+            const int k = 2 * kb + (rem & 1);
+            kk[u] = idx < total && k <= half ? k : -1;
+            mm[u] = m;
+            a[u] = b[u] = cf{0.f, 0.f};
+            if (kk[u] < 0) continue;
+            const size_t rowoff = (size_t)(mb + m) * 2;
+            const int k2 = M - k;
+            if (k < nk) a[u] = ldcf(spec + (size_t)(k >> 1) * P.Ntheta * 2 + rowoff + (k & 1));
+            if (k > 0 && k2 < nk) b[u] = ldcf(spec + (size_t)(k2 >> 1) * P.Ntheta * 2 + rowoff + (k2 & 1));
         }
-        const int k2 = M - k;
-        const cf b = k2 < nk ? ldcf(spec + (size_t)(k2 >> 1) * P.Ntheta * 2 + rowoff + (k2 & 1)) : cf{0.f, 0.f};
-        cf zk, zmk;
-        c2r_pre_vals(a, b, ldcf(P.twP + k), zk, zmk);
-        Z[sw(__ldg(P.rpos + k))] = zk;
-        Z[sw(__ldg(P.rpos + k2))] = zmk;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = kk[u];
+            if (k < 0) continue;
+            cf* Z = X + mm[u] * row_stride(M);
+            if (k == 0) {
+                Z[sw(__ldg(P.rpos))] = c2r_pre_dc(a[u]);
+                continue;
+            }
+            cf zk, zmk;
+            c2r_pre_vals(a[u], b[u], ldcf(P.twP + k), zk, zmk);
+            Z[sw(__ldg(P.rpos + k))] = zk;
+            Z[sw(__ldg(P.rpos + M - k))] = zmk;
+        }
     }
 }
 
@@ -534,7 +559,7 @@ template <class Src>
 __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src B) {
     int bx;
     const PieceDev& P = piece_of(B, bx);
-    if (P.CB != 2 || (size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
+    if (P.CB != 2 || rows_smem(P) > dyn_smem_bytes()) return;
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int M = P.Prho / 2;
@@ -671,7 +696,7 @@ template <class Src>
 __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Src B) {
     int band;
     const PieceDev& P = piece_of(B, band);
-    if (P.CB != 2 || (size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
+    if (P.CB != 2 || rows_smem(P) > dyn_smem_bytes()) return;
     const float* __restrict__ h = P.prof;
     const int hp = P.hpitch;
     const int mb = band * P.R;
@@ -705,7 +730,7 @@ __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Sr
 #pragma unroll
         for (int r = 0; r < kMaxBandRows; ++r) {
             if (r < nrows) {
-                float* row = smem_f + r * Pr;
+                float* row = smem_f + r * 2 * row_stride(Pr / 2);
                 const int n = 4 * n4;
                 row[swr(n)] = acc[r].x;
                 row[swr(n + 1)] = acc[r].y;
@@ -929,7 +954,7 @@ template <class Src>
 __global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ Src B) {
     int bx;
     const PieceDev& P = piece_of(B, bx);
-    if (P.CB != 2 || (size_t)P.R * P.Prho * sizeof(float) > dyn_smem_bytes()) return;
+    if (P.CB != 2 || rows_smem(P) > dyn_smem_bytes()) return;
     const int mb = bx * P.R;
     const int nrows = min(P.R, P.Ntheta - mb);
     const int M = P.Prho / 2;
@@ -1263,9 +1288,7 @@ static int check_launch() {
     return e == cudaSuccess ? 0 : (int)e;
 }
 
-size_t scatter_smem_bytes(const PieceDev& P) {
-    return (size_t)P.R * P.Prho * sizeof(float);
-}
+size_t scatter_smem_bytes(const PieceDev& P) { return rows_smem(P); }
 
 size_t colconv_smem_bytes(const PieceDev& P) { return colconv_smem(P.Ptheta, P.k1max + 1, P.twT_len); }
 

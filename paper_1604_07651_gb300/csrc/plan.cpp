@@ -748,7 +748,8 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
                         " above the FFT passes' limit (4096, 6144 = 3*2048 or 5120 = 5*1024)");
     // rows per band: any value up to what shared memory allows gives the same
     // results; the descriptor's choice, else 3 until the plan times them
-    const int Rmax = (int)std::min<size_t>(kMaxBandRows, (size_t)smem_max / (h.Prho * sizeof(float)));
+    // (the row kernels pad each row of their band by one complex element)
+    const int Rmax = (int)std::min<size_t>(kMaxBandRows, (size_t)smem_max / ((h.Prho + 2) * sizeof(float)));
     if (Rmax < 1) return fail(RADON_ERR_UNSUPPORTED, "row FFT length too large for shared memory");
     h.Rmax = Rmax;
     const int R = std::min(Rmax, d.rows_per_band > 0 ? d.rows_per_band : 3);
