@@ -373,8 +373,10 @@ def batched_uneven(dev, n: int, rank: int = 0, world: int = 1) -> dict:
              float(np.linalg.norm(ai[kk, jj] - refa) / np.linalg.norm(refa)),
              float(np.linalg.norm(gi[li[late], ii[late]] - ref[late]) / np.linalg.norm(ref[late])), None, None]
         if lo + i < 8:    # the first gathers also against the FP64 log-polar oracle, every output
+            d = batch.plan_desc(i)
             lp = LogPolar(Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
-                               sigma=1.25, omega_c=0.35, tsplits=(0.25, 0.5)))
+                               sigma=d.sigma, omega_c=d.omega_c,
+                               tsplits=tuple(d.tsplit[t] for t in range(d.n_tsplit))))
             r1, r2 = lp.forward(fi), lp.adjoint(gi)
             e[3] = float(np.linalg.norm(gi - r1) / np.linalg.norm(r1))
             e[4] = float(np.linalg.norm(ai - r2) / np.linalg.norm(r2))
@@ -492,9 +494,11 @@ def cpu_logpolar(N: int = 512) -> dict:
     kernel spectra built first (untimed), then one forward + adjoint pair."""
     import synth
     from oracle.logpolar import Desc, LogPolar
+    import paper_1604_07651_gb300 as hr
+    m = hr.default_method()   # the library's defaults, read on the host
     geo, f = synth.sweep_gather(N)
     lp = LogPolar(Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
-                       sigma=1.25, omega_c=0.35, tsplits=(0.25, 0.5)))
+                       sigma=m["sigma"], omega_c=m["omega_c"], tsplits=m["tsplit"]))
     t0 = time.perf_counter()
     lp.adjoint(lp.forward(f))
     t = time.perf_counter() - t0

@@ -115,7 +115,7 @@ typedef struct {
 
 /*
  * Fill *d with the default method parameters for the given problem:
- * tau0 = 0, dtau = (Nt-1) dt/(Ntau-1), sigma = 1.25, omega_c = 0.35,
+ * tau0 = 0, dtau = (Nt-1) dt/(Ntau-1), sigma = 1.1, omega_c = 0.4,
  * time splits at 0.25 T and 0.5 T, one slowness piece, current device,
  * 3 rows per band.
  * Returns RADON_ERR_INVALID_ARG for a NULL d.

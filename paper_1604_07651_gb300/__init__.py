@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import RadonError, RadonDesc, RadonPieceInfo
 
 __all__ = ["Plan", "Batch", "radon", "radon_adjoint", "radon_adj", "direct_forward", "direct_adjoint", "RadonError",
-           "HRadon"]
+           "HRadon", "default_method"]
 
 
 def _stream_ptr(device: torch.device):
@@ -36,6 +36,16 @@ def _check_tensor(t: torch.Tensor, shape, name: str, device: torch.device):
         raise ValueError(f"{name} must be a contiguous float32 tensor on {device}")
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def default_method() -> dict:
+    """The library's default method parameters (``radon_desc_init``; host
+    only, no device needed): ``sigma``, ``omega_c`` and the time splits
+    ``tsplit`` (fractions of T)."""
+    lib = _lib.load()
+    d = RadonDesc()
+    _lib.check(lib.radon_desc_init(ctypes.byref(d), 2, 2, 2, 1, 1.0, 1.0, 0.0, 1.0))
+    return {"sigma": d.sigma, "omega_c": d.omega_c, "tsplit": tuple(d.tsplit[i] for i in range(d.n_tsplit))}
 
 
 class Plan:
@@ -316,6 +326,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def plan_desc(self, i: int) -> RadonDesc:
+        """The resolved descriptor of gather i's plan (``radon_batch_plan``)."""
+        d = RadonDesc()
+        _lib.check(_lib.load().radon_batch_plan(self._handle, i, ctypes.byref(d)))
+        return d
 
     def pack(self, gathers: Sequence[torch.Tensor], dtype=torch.float32) -> torch.Tensor:
         """The packed gather buffer of the batch's layout."""

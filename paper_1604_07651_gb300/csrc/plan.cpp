@@ -1007,8 +1007,8 @@ extern "C" radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau,
     d->qmax = qmax;
     d->tau0 = 0.0;
     d->dtau = 0.0;
-    d->sigma = 1.25;
-    d->omega_c = 0.35;
+    d->sigma = 1.1;
+    d->omega_c = 0.4;
     d->n_tsplit = 2;
     d->tsplit[0] = 0.25;
     d->tsplit[1] = 0.5;

@@ -61,9 +61,12 @@ def _small_batch():
     return geos, [synth.batch_gather(g, 100 + i) for i, g in enumerate(geos)]
 
 
-def _oracle(geo, **kw):
+def _oracle(geo, d):
+    """The FP64 log-polar oracle with the method parameters of the library's
+    resolved descriptor d (the batch's own plan of this gather)."""
     return LogPolar(Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
-                         sigma=1.25, omega_c=0.35, tsplits=(0.25, 0.5), **kw))
+                         sigma=d.sigma, omega_c=d.omega_c, tsplits=tuple(d.tsplit[i] for i in range(d.n_tsplit)),
+                         n_qsplit=d.n_qsplit))
 
 
 def test_batch_against_oracle_fp32_and_bf16(hr):
@@ -76,8 +79,8 @@ def test_batch_against_oracle_fp32_and_bf16(hr):
     gimg = [synth.random_radon_image(g, 200 + i) for i, g in enumerate(geos)]
     fa = batch.unpack_gathers(batch.adjoint(torch.cat([torch.tensor(x, dtype=torch.float32).reshape(-1)
                                                        for x in gimg]).cuda()))
-    for geo, x, a, b, gi, fi in zip(geos, gathers, g32, gb, gimg, fa):
-        lp = _oracle(geo)
+    for i, (geo, x, a, b, gi, fi) in enumerate(zip(geos, gathers, g32, gb, gimg, fa)):
+        lp = _oracle(geo, batch.plan_desc(i))
         assert_parity(a.cpu().numpy(), lp.forward(x), what="batch FP32 forward")
         xb = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
         ref_b = lp.forward(xb)

@@ -49,6 +49,18 @@ def _pair(hr, geo, sigma=1.25, omega_c=0.35, tsplit=(0.25, 0.5), nq=1, tau0=0.0,
     return plan, desc
 
 
+def _default_pair(hr, geo, **kw):
+    """A plan with the library's default method parameters and the FP64
+    oracle descriptor of the same lattices (from the plan's resolved
+    descriptor)."""
+    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, **kw)
+    d = plan.desc
+    desc = Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, tau0=d.tau0, dtau=d.dtau,
+                sigma=d.sigma, omega_c=d.omega_c, tsplits=tuple(d.tsplit[i] for i in range(d.n_tsplit)),
+                n_qsplit=d.n_qsplit)
+    return plan, desc
+
+
 def _cuda(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
 
@@ -111,8 +123,9 @@ def test_dot_test_fp32(hr):
 
 
 def test_matches_direct_sum_band_limited_512(hr, oracle_direct):
+    """Default method parameters, band-limited 512^2 gather, every output."""
     geo, f = synth.sweep_gather(512, noise=0.0, nu_range=(8.0, 12.0))
-    plan, _ = _pair(hr, geo)
+    plan, _ = _default_pair(hr, geo)
     g_or = oracle_direct.fwd(f, geo.dt, geo.dx, geo.tau(), geo.q())
     g = plan.forward(_cuda(f)).cpu().numpy()
     assert _rel(g, g_or) < METHOD_TOL
@@ -123,7 +136,7 @@ def test_full_size_2048_sampled_against_direct_sum(hr, oracle_direct):
     noise, default method parameters): forward on 4096 sampled outputs and
     adjoint on 4096 sampled gather points against the FP64 direct sum."""
     geo, f = synth.sweep_gather(2048, noise=0.05)
-    plan, _ = _pair(hr, geo)
+    plan, _ = _default_pair(hr, geo)
     rng = np.random.default_rng(2048)
     ii = rng.integers(0, geo.Ntau, 4096)
     li = rng.integers(0, geo.Nq, 4096)
@@ -145,7 +158,7 @@ def test_large_4096_sampled_against_direct_sum(hr, oracle_direct):
     random outputs and adjoint on 4096 random gather points against the FP64
     direct sum, O(N) per point."""
     geo, f = synth.large_gather(4096)
-    plan, _ = _pair(hr, geo)
+    plan, _ = _default_pair(hr, geo)
     assert max(max(p["Ptheta"], p["Prho"]) for p in plan.pieces()) > 4096
     rng = np.random.default_rng(4096)
     ii = rng.integers(0, geo.Ntau, 4096)
@@ -166,10 +179,11 @@ def test_full_size_2048_against_logpolar_oracle(hr):
     """The benchmark workload and plan (2048^2 gather, default method), every
     output, against the FP64 log-polar oracle on the same lattices: the
     forward of the benchmark gather, and the adjoint of a random Radon image
-    and of a band-limited one (Gaussian blobs in tau and q). Rows per band
-    tuned at plan creation, as the benchmark plans it."""
+    and of a band-limited one (Gaussian blobs in tau and q). Default method
+    parameters and rows per band tuned at plan creation, as the benchmark
+    plans it."""
     geo, f = synth.sweep_gather(2048, noise=0.05)
-    plan, desc = _pair(hr, geo, rows_per_band=0)
+    plan, desc = _default_pair(hr, geo, rows_per_band=0)
     lp = LogPolar(desc)
     assert_parity(plan.forward(_cuda(f)).cpu().numpy(), lp.forward(f), what="2048 forward")
     for name, gg in (("random", synth.random_radon_image(geo, 33)), ("blobs", synth.smooth_radon_image(geo, 77))):
@@ -341,7 +355,7 @@ def test_forward_and_adjoint_are_bitwise_reproducible(hr):
     tiles are summed in a fixed order; other launches run in between so that
     the units are scheduled differently."""
     geo, f = synth.sweep_gather(2048, noise=0.05)
-    plan, _ = _pair(hr, geo, rows_per_band=0)
+    plan, _ = _default_pair(hr, geo, rows_per_band=0)
     ft = _cuda(f)
     gg = _cuda(synth.smooth_radon_image(geo, 77))
     g0, a0 = plan.forward(ft), plan.adjoint(gg)
