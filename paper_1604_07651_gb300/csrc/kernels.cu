@@ -583,47 +583,6 @@ __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src
 // plain per-thread sum over the band's columns in a fixed order: the adjoint
 // interpolation has no floating-point atomics and is deterministic.
 
-// One group of 32 consecutive outputs of a column (rho tap n0 nondecreasing
-// in the lane index) onto the column's fixed-point profile. When neighbouring
-// lanes share a first tap -- small intercept times put dozens of outputs in
-// one cell -- the lanes of each run of equal n0 are summed first with a
-// segmented warp scan and only the run's last lane adds to shared memory.
-__device__ __forceinline__ void profile_group(int2 e, float v, int* prof, int lane) {
-    const unsigned FULL = 0xffffffffu;
-    const bool valid = e.x >= 0;
-    const int key = valid ? e.x : -1 - lane;
-    float wr[4] = {0.f, 0.f, 0.f, 0.f};
-    if (valid) b3_weights(__int_as_float(e.y), wr);
-    float s0 = v * wr[0], s1 = v * wr[1], s2 = v * wr[2], s3 = v * wr[3];
-    const int kprev = __shfl_up_sync(FULL, key, 1);
-    const bool head = lane == 0 || kprev != key;
-    bool write = valid;
-    if (__any_sync(FULL, !head)) {
-        int h = head;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const float t0 = __shfl_up_sync(FULL, s0, d), t1 = __shfl_up_sync(FULL, s1, d);
-            const float t2 = __shfl_up_sync(FULL, s2, d), t3 = __shfl_up_sync(FULL, s3, d);
-            const int th = __shfl_up_sync(FULL, h, d);
-            if (lane >= d && !h) {
-                s0 += t0;
-                s1 += t1;
-                s2 += t2;
-                s3 += t3;
-                h |= th;
-            }
-        }
-        const int knext = __shfl_down_sync(FULL, key, 1);
-        write = valid && (lane == 31 || knext != key);
-    }
-    if (write) {
-        red_fixed(prof + e.x, s0);
-        red_fixed(prof + e.x + 1, s1);
-        red_fixed(prof + e.x + 2, s2);
-        red_fixed(prof + e.x + 3, s3);
-    }
-}
-
 // One CTA per output column of the piece: P.prof[lc][0..Nrho) (pitch hpitch) of
 // the column's outputs g[l_lo + lc][*], scaled by the column's output scale.
 // Fixed point with the bound max|g| of the column times the column's
@@ -640,7 +599,7 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
     const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * P.Ntau);
     float* hl = P.prof + (size_t)lc * hp;
     for (int n = threadIdx.x; n < P.Nrho; n += blockDim.x) prof[n] = 0;
-    constexpr int Q = 8;                        // outputs per thread in flight
+    constexpr int Q = 8;                        // outputs per thread
     const int chunk = Q * (int)blockDim.x;
     float m = 0.f;
     for (int i0 = 0; i0 < P.Ntau; i0 += chunk) {
@@ -664,25 +623,66 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
     }
     const Pow2Scale scl(__ldg(P.colsh + lc) - ilogbf(vmax));
     const float sc = __ldg(P.colscale + lc);
-    const int lane = threadIdx.x & 31;
     // only the column's valid outputs (the max above still sees every output,
     // so a non-finite value anywhere in the column poisons the profile)
     const int2 rg = __ldg(P.rrange + lc);
-    for (int i0 = rg.x & ~31; i0 <= rg.y; i0 += chunk) {   // uniform over the block: every lane takes part
+    // every thread takes Q consecutive outputs: their first rho tap is
+    // nondecreasing, so their contributions collect in a 4-cell register
+    // window that slides one cell as the tap advances (the departing cell goes
+    // to the shared profile) and is flushed whole on a longer jump; dozens of
+    // outputs that share a cell at small intercept times cost one add
+    for (int i0 = rg.x & ~7; i0 <= rg.y; i0 += Q * (int)blockDim.x) {
+        const int ib = i0 + Q * (int)threadIdx.x;
         int2 e[Q];
         float v[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int i = i0 + q * (int)blockDim.x + threadIdx.x;   // a warp: 32 consecutive outputs
+            const int i = ib + q;
             e[q] = make_int2(-1, 0);
             v[q] = 0.f;
-            if (i <= rg.y) {
+            if (i >= rg.x && i <= rg.y) {
                 e[q] = __ldg(rt + i);
                 v[q] = __ldg(gl + i);
             }
         }
+        float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
+        int wn = -1;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) profile_group(e[q], scl.up(v[q] * sc), prof, lane);
+        for (int q = 0; q < Q; ++q) {
+            const int n0 = e[q].x;
+            if (n0 < 0) continue;
+            if (wn < 0) {
+                wn = n0;
+            } else if (n0 != wn) {
+                if (n0 == wn + 1) {
+                    red_fixed(prof + wn, w0);
+                    w0 = w1;
+                    w1 = w2;
+                    w2 = w3;
+                    w3 = 0.f;
+                } else {
+                    red_fixed(prof + wn, w0);
+                    red_fixed(prof + wn + 1, w1);
+                    red_fixed(prof + wn + 2, w2);
+                    red_fixed(prof + wn + 3, w3);
+                    w0 = w1 = w2 = w3 = 0.f;
+                }
+                wn = n0;
+            }
+            float wr[4];
+            b3_weights(__int_as_float(e[q].y), wr);
+            const float x = scl.up(v[q] * sc);
+            w0 = fmaf(x, wr[0], w0);
+            w1 = fmaf(x, wr[1], w1);
+            w2 = fmaf(x, wr[2], w2);
+            w3 = fmaf(x, wr[3], w3);
+        }
+        if (wn >= 0) {
+            red_fixed(prof + wn, w0);
+            red_fixed(prof + wn + 1, w1);
+            red_fixed(prof + wn + 2, w2);
+            red_fixed(prof + wn + 3, w3);
+        }
     }
     __syncthreads();
     for (int n = threadIdx.x; n < hp; n += blockDim.x) hl[n] = n < P.Nrho ? scl.down(prof[n]) : 0.f;
