@@ -66,6 +66,11 @@ class Desc:
     largest) in place of ``k dx``, and ``q_values`` the Nq slownesses (s/km,
     strictly increasing, >= 0) in place of the regular q grid. Time and
     intercept time stay regular.
+
+    ``order`` is the degree of the B-spline of the gridding, the
+    deconvolution and the interpolation (Eq. (14)-(17)): 3 (cubic, the
+    paper's) or 5 (quintic, the higher-order kernel Section 7 proposes);
+    the lattice keeps (order + 1) / 2 guard cells per side.
     """
     Nt: int
     Nx: int
@@ -83,8 +88,11 @@ class Desc:
     n_qsplit: int = 1
     x: tuple | None = None
     q_values: tuple | None = None
+    order: int = 3
 
     def __post_init__(self):
+        if self.order not in (3, 5):
+            raise ValueError("order: the B-spline degree, 3 (cubic) or 5 (quintic)")
         if self.x is not None:
             x = np.asarray(self.x, dtype=np.float64)
             if x.shape != (self.Nx,) or self.Nx < 2 or x[0] < 0 or not np.all(np.diff(x) > 0):
@@ -194,6 +202,7 @@ class Partition:
     k1max: int
     k2max: int
     jfirst: np.ndarray  # per trace k: first gridded sample index (mute)
+    order: int = 3      # B-spline degree (Desc.order)
 
 
 def fft_size(n: int) -> int:
@@ -393,7 +402,7 @@ def make_partition(desc: Desc, jt: tuple[int, int, int], lq: tuple[int, int]) ->
         jfirst[k] = j0 + int(ok[0]) if ok.size else j1 + 1
 
     part = Partition(tp, j0, j1, l0, l1, s0, s1, m_lo, m_hi, alpha, beta, a, O1, O2,
-                     c_min, k2, 0.0, 0.0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, jfirst)
+                     c_min, k2, 0.0, 0.0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, jfirst, desc.order)
     # Data region of the piece: [s0, s1] x [0, 1] minus the muted triangle.
     poly = _clip_region(s0, s1, c_min, k2)
     u1, u2 = map_T(part, poly[:, 0], poly[:, 1])
@@ -415,8 +424,9 @@ def make_partition(desc: Desc, jt: tuple[int, int, int], lq: tuple[int, int]) ->
                float(np.max(np.abs(np.diff(eta, axis=0)))) if eta.shape[0] > 1 else 0.0)
     part.dphi_rule, part.deta_rule = dphi, deta
 
-    # Lattice: spacing of Eq. (18) divided by sigma, two guard cells per side,
-    # over [-beta/2, beta/2] x [log a_r, log r_max].
+    # Lattice: spacing of Eq. (18) divided by sigma, (order + 1) / 2 guard
+    # cells per side (the taps of a position reach that far beyond it), over
+    # [-beta/2, beta/2] x [log a_r, log r_max].
     n_theta = max(1, int(math.ceil(desc.sigma * beta / dphi - 1e-9)))
     L_rho = math.log(part.r_max) - math.log(part.a_r)
     n_rho = max(1, int(math.ceil(desc.sigma * L_rho / deta - 1e-9)))
@@ -424,9 +434,10 @@ def make_partition(desc: Desc, jt: tuple[int, int, int], lq: tuple[int, int]) ->
     drho = L_rho / n_rho
     part.n_theta, part.n_rho = n_theta, n_rho
     part.dtheta, part.drho = dtheta, drho
-    part.theta0 = -beta / 2 - 2 * dtheta
-    part.rho0 = math.log(part.a_r) - 2 * drho
-    part.Ntheta, part.Nrho = n_theta + 5, n_rho + 5
+    g = guard_cells(desc.order)
+    part.theta0 = -beta / 2 - g * dtheta
+    part.rho0 = math.log(part.a_r) - g * drho
+    part.Ntheta, part.Nrho = n_theta + 2 * g + 1, n_rho + 2 * g + 1
 
     # Kernel window and zero padding (Section 2.1, after Eq. (7)): the
     # convolution only ever pairs lattice points whose theta-difference is at
@@ -451,7 +462,7 @@ def plan(desc: Desc) -> list[Partition]:
 
 
 # --------------------------------------------------------------------------
-# Cubic B-spline and the kernel spectrum
+# B-splines and the kernel spectrum
 # --------------------------------------------------------------------------
 
 
@@ -465,6 +476,31 @@ def b3(x):
 def b3_hat(w):
     """Fourier transform of B3 at frequency w (cycles per cell): sinc^4."""
     return np.sinc(w) ** 4
+
+
+def b5(x):
+    """Centred quintic cardinal B-spline, support (-3, 3), from its
+    definition as the 6-fold convolution of the unit box: the truncated
+    powers (3-|x|)^5 - 6 (2-|x|)^5 + 15 (1-|x|)^5, each term only where its
+    base is positive, over 5! = 120."""
+    ax = np.abs(np.asarray(x, dtype=np.float64))
+    tp = lambda u: np.where(u > 0.0, u, 0.0) ** 5
+    return (tp(3.0 - ax) - 6.0 * tp(2.0 - ax) + 15.0 * tp(1.0 - ax)) / 120.0
+
+
+def bspline(order: int, x):
+    """The centred cardinal B-spline of degree 3 or 5."""
+    return b3(x) if order == 3 else b5(x)
+
+
+def bspline_hat(order: int, w):
+    """Its Fourier transform at frequency w (cycles per cell): sinc^(order+1)."""
+    return np.sinc(w) ** (order + 1)
+
+
+def guard_cells(order: int) -> int:
+    """Guard cells per lattice side: (order + 1) / 2, the reach of the taps."""
+    return (order + 1) // 2
 
 
 def gl_nodes(theta_m: float, cycles: float, nodes_per_panel: int = 20, extra_panels: int = 4):
@@ -512,11 +548,12 @@ def zeta_hat(theta_m: float, w1, w2):
 
 
 def kernel_spectrum(part: Partition) -> np.ndarray:
-    """K = chi_L * zeta_hat / (B3_hat_theta B3_hat_rho)^2 on the rfft2 grid
+    """K = chi_L * zeta_hat / (B_hat_theta B_hat_rho)^2 on the rfft2 grid
     [P_theta][P_rho//2 + 1] (Eq. (14), (16)-(17)).
 
     Reading: ``F B3`` is the continuous transform sinc^4 of the B-spline in
-    cell units (the USFFT convention the paper cites); L is the rectangle
+    cell units (the USFFT convention the paper cites; sinc^6 for the quintic
+    B-spline of ``Desc.order`` = 5); L is the rectangle
     |k1|/P_theta <= omega_c, k2/P_rho <= omega_c; the Nyquist bins are always
     outside L.
     """
@@ -525,7 +562,7 @@ def kernel_spectrum(part: Partition) -> np.ndarray:
     k1 = np.arange(0, part.k1max + 1)
     k2 = np.arange(0, part.k2max + 1)
     z = zeta_hat(part.theta_m, k1 / (Pt * part.dtheta), k2 / (Pr * part.drho))
-    den = (b3_hat(k1 / Pt)[:, None] * b3_hat(k2 / Pr)[None, :]) ** 2
+    den = (bspline_hat(part.order, k1 / Pt)[:, None] * bspline_hat(part.order, k2 / Pr)[None, :]) ** 2
     Kh = z / den
     K[:part.k1max + 1, :part.k2max + 1] = Kh
     K[Pt - part.k1max:, :part.k2max + 1] = Kh[:0:-1]  # even in k1
@@ -622,30 +659,32 @@ def radon_points(desc: Desc, part: Partition):
 # --------------------------------------------------------------------------
 
 
-def _taps(x):
-    i0 = np.floor(x).astype(np.int64) - 1
-    return i0, [b3(x - i0 - d) for d in range(4)]
+def _taps(x, order: int = 3):
+    """The order + 1 lattice points whose B-spline reaches position x: first
+    tap floor(x) - (order - 1) / 2, and each tap's weight."""
+    i0 = np.floor(x).astype(np.int64) - (order - 1) // 2
+    return i0, [bspline(order, x - i0 - d) for d in range(order + 1)]
 
 
 def grid_fwd(part: Partition, xth, xrh, w) -> np.ndarray:
-    """Smearing, Eq. (15): G[m][n] = sum_s W_s B3(.)B3(.) / (dtheta drho)."""
+    """Smearing, Eq. (15): G[m][n] = sum_s W_s B(.)B(.) / (dtheta drho)."""
     G = np.zeros((part.Ntheta, part.Nrho))
-    m0, wt = _taps(xth)
-    n0, wr = _taps(xrh)
+    m0, wt = _taps(xth, part.order)
+    n0, wr = _taps(xrh, part.order)
     sc = w / (part.dtheta * part.drho)
-    for a in range(4):
-        for b in range(4):
+    for a in range(part.order + 1):
+        for b in range(part.order + 1):
             np.add.at(G, (m0 + a, n0 + b), sc * wt[a] * wr[b])
     return G
 
 
 def grid_adj(part: Partition, G, xth, xrh) -> np.ndarray:
     """Transpose of ``grid_fwd`` (per-sample sums; weights applied by caller)."""
-    m0, wt = _taps(xth)
-    n0, wr = _taps(xrh)
+    m0, wt = _taps(xth, part.order)
+    n0, wr = _taps(xrh, part.order)
     acc = np.zeros(xth.shape)
-    for a in range(4):
-        for b in range(4):
+    for a in range(part.order + 1):
+        for b in range(part.order + 1):
             acc += G[m0 + a, n0 + b] * wt[a] * wr[b]
     return acc / (part.dtheta * part.drho)
 
@@ -662,13 +701,15 @@ def conv(part: Partition, G, K, adjoint=False) -> np.ndarray:
 
 
 def interp_fwd(part: Partition, Q, xth, xrh, valid, scale) -> np.ndarray:
-    """Cubic B-spline interpolation of Eq. (17) at the output coordinates."""
-    m0, wt = _taps(xth)
-    xr = np.where(valid, xrh, 2.0)
-    n0, wr = _taps(xr)
+    """B-spline interpolation of Eq. (17) at the output coordinates (lines
+    that miss the piece take a dummy in-range position and give 0)."""
+    g = guard_cells(part.order)
+    m0, wt = _taps(xth, part.order)
+    xr = np.where(valid, xrh, float(g))
+    n0, wr = _taps(xr, part.order)
     acc = np.zeros(xth.shape)
-    for a in range(4):
-        for b in range(4):
+    for a in range(part.order + 1):
+        for b in range(part.order + 1):
             acc += Q[m0 + a, n0 + b] * wt[a] * wr[b]
     return np.where(valid, scale * acc, 0.0)
 
@@ -676,12 +717,13 @@ def interp_fwd(part: Partition, Q, xth, xrh, valid, scale) -> np.ndarray:
 def interp_adj(part: Partition, vals, xth, xrh, valid, scale) -> np.ndarray:
     """Transpose of ``interp_fwd``."""
     Q = np.zeros((part.Ntheta, part.Nrho))
-    m0, wt = _taps(xth)
-    xr = np.where(valid, xrh, 2.0)
-    n0, wr = _taps(xr)
+    g = guard_cells(part.order)
+    m0, wt = _taps(xth, part.order)
+    xr = np.where(valid, xrh, float(g))
+    n0, wr = _taps(xr, part.order)
     v = np.where(valid, scale * vals, 0.0)
-    for a in range(4):
-        for b in range(4):
+    for a in range(part.order + 1):
+        for b in range(part.order + 1):
             np.add.at(Q, (m0 + a, n0 + b), v * wt[a] * wr[b])
     return Q
 

@@ -208,8 +208,8 @@ def test_mutant_output_scale_caught(monkeypatch):
 
 def test_mutant_single_deconvolution_caught(monkeypatch):
     """Dividing by the B-spline symbol once instead of twice breaks C4."""
-    orig = LP.b3_hat
-    monkeypatch.setattr(LP, "b3_hat", lambda w: np.sqrt(orig(w)))
+    orig = LP.bspline_hat
+    monkeypatch.setattr(LP, "bspline_hat", lambda order, w: np.sqrt(orig(order, w)))
     assert _blob_error() > 1e-3
 
 
@@ -267,3 +267,65 @@ def test_lattice_spacing_rule_by_brute_force():
             if not tsplits:
                 # both neighbour directions matter here: each decides one spacing
                 assert by_t[0] > by_x[0] * 1.01 and by_x[1] > by_t[1] * 1.01, (by_t, by_x)
+
+
+# ---- the quintic B-spline option (Section 7: higher-order kernels) --------
+
+def test_b5_from_convolutions_partition_of_unity_and_transform():
+    """B5 against two things that do not use its truncated-power formula:
+    the convolution B3 * box * box evaluated numerically, and the transform
+    sinc^6 by quadrature; plus the partition of unity."""
+    h = 1e-3
+    t = np.arange(-4.0, 4.0 + h / 2, h)
+    box = np.where(np.abs(t) < 0.5 - h / 4, 1.0, np.where(np.abs(t) < 0.5 + h / 4, 0.5, 0.0))   # trapezoid edges
+    conv = np.convolve(np.convolve(LP.b3(t), box, mode="same") * h, box, mode="same") * h
+    np.testing.assert_allclose(conv, LP.b5(t), atol=2e-6)
+    x = np.linspace(-4, 4, 1001)
+    np.testing.assert_allclose(sum(LP.b5(x - k) for k in range(-8, 9)), 1.0, atol=1e-14)
+    for w in (0.0, 0.11, 0.29, 0.5):
+        val = quad(lambda u: LP.b5(np.array(u)) * math.cos(2 * math.pi * w * u), -3, 3,
+                   points=[-2, -1, 0, 1, 2], epsabs=1e-15)[0]
+        assert abs(val - LP.bspline_hat(5, w)) < 1e-13
+
+
+@pytest.mark.parametrize("tsplits,nq", [((), 1), ((0.3, 0.6), 2)])
+def test_quintic_blob_line_integral_and_transpose(tsplits, nq):
+    """C4 with the quintic kernel: the Gaussian blob's closed-form line
+    integral to 1e-5 (cubic: 5e-5), and the exact transpose to 1e-12."""
+    N = 256
+    geo = synth.Geometry(N, N, N, N, 2.0 / (N - 1), 2.0 / (N - 1), 0.2, 0.7)
+    d = Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+             sigma=2.0, omega_c=0.25, tsplits=tsplits, n_qsplit=nq, order=5)
+    lp = LogPolar(d)
+    assert all(p.Ntheta == p.n_theta + 7 and p.Nrho == p.n_rho + 7 for p in lp.parts)   # 3 guard cells
+    for c1, c2, w in BLOBS:
+        f = cf.blob_sy_gather(geo.t(), geo.x(), geo.T, geo.X, c1, c2, w)
+        g_ex = cf.blob_sy_radon(geo.tau(), geo.q(), geo.T, geo.X, c1, c2, w)
+        assert _rel(lp.forward(f), g_ex) < 1e-5, (c1, c2, w)
+    rng = np.random.default_rng(55)
+    f = rng.standard_normal((geo.Nx, geo.Nt))
+    g = rng.standard_normal((geo.Nq, geo.Ntau))
+    lhs, rhs = float(np.sum(lp.forward(f) * g)), float(np.sum(f * lp.adjoint(g)))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-12
+
+
+def test_quintic_agrees_with_direct_sum_band_limited(oracle_direct):
+    N = 512
+    geo = synth.Geometry(N, N, N, N, 2.0 / (N - 1), 2.0 / (N - 1), 0.2, 0.7)
+    f = synth.band_limited_gather(geo, 21, n_events=10, nu=12.0)
+    g_or = oracle_direct.fwd(f, geo.dt, geo.dx, geo.tau(), geo.q())
+    d = Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+             sigma=2.0, omega_c=0.25, tsplits=(0.3, 0.6), order=5)
+    assert _rel(LogPolar(d).forward(f), g_or) < 1e-2
+
+
+def test_mutant_quintic_with_cubic_symbol_caught(monkeypatch):
+    """Deconvolving the quintic gridding by the cubic symbol sinc^4 breaks C4."""
+    monkeypatch.setattr(LP, "bspline_hat", lambda order, w: np.sinc(w) ** 4)
+    N = 128
+    geo = synth.Geometry(N, N, N, N, 2.0 / (N - 1), 2.0 / (N - 1), 0.2, 0.7)
+    d = Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, order=5)
+    c1, c2, w = BLOBS[0]
+    f = cf.blob_sy_gather(geo.t(), geo.x(), geo.T, geo.X, c1, c2, w)
+    g_ex = cf.blob_sy_radon(geo.tau(), geo.q(), geo.T, geo.X, c1, c2, w)
+    assert _rel(LogPolar(d).forward(f), g_ex) > 1e-4
