@@ -80,6 +80,12 @@ typedef struct radon_plan_s* radon_plan;
  *             every descriptor asks for it) time each feasible value on the
  *             device and keep the fastest; radon_plan_desc reports the choice.
  *             It changes the work split only, not the results.
+ *   spline_order: degree of the B-spline of the gridding, the deconvolution
+ *             and the interpolation (Eq. (14)-(17)): 3 (cubic, the default)
+ *             or 5 (quintic, the higher-order kernel of Section 7: six taps
+ *             per axis, three guard cells per lattice side; more accurate
+ *             on smooth data, about twice the tap work). The plans of one
+ *             batch must share it.
  */
 typedef struct {
     int Nt, Nx, Ntau, Nq;
@@ -92,6 +98,7 @@ typedef struct {
     int n_qsplit;
     int device;
     int rows_per_band;
+    int spline_order;
 } radon_desc;
 
 /* Geometry of one sub-problem of a plan (for tests and diagnostics). */
@@ -117,7 +124,7 @@ typedef struct {
  * Fill *d with the default method parameters for the given problem:
  * tau0 = 0, dtau = (Nt-1) dt/(Ntau-1), sigma = 1.1, omega_c = 0.4,
  * time splits at 0.25 T and 0.5 T, one slowness piece, current device,
- * 3 rows per band.
+ * 3 rows per band, cubic B-splines.
  * Returns RADON_ERR_INVALID_ARG for a NULL d.
  */
 radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau, int Nq, double dt,

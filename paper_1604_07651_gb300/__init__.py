@@ -57,7 +57,8 @@ class Plan:
     ``[qmin, qmax]``; method parameters ``sigma``, ``omega_c``, ``tsplit``
     (split points of Eq. (19) as fractions of T), ``n_qsplit``;
     ``rows_per_band`` (1..6, or 0 to time them at plan creation; the plan's
-    ``desc.rows_per_band`` reports the value in use). Unequally spaced grids
+    ``desc.rows_per_band`` reports the value in use); ``spline_order`` 3
+    (cubic B-splines, the default) or 5 (quintic). Unequally spaced grids
     (``radon_plan_create_grid``): ``x`` gives the Nx offsets (km) in place of
     ``k*dx``, ``q`` the Nq slownesses (s/km) in place of the regular grid.
     """
@@ -67,7 +68,8 @@ class Plan:
                  sigma: float | None = None, omega_c: float | None = None,
                  tsplit: Sequence[float] | None = None, n_qsplit: int = 1,
                  rows_per_band: int | None = None, device: int | torch.device | None = None,
-                 x: Sequence[float] | None = None, q: Sequence[float] | None = None):
+                 x: Sequence[float] | None = None, q: Sequence[float] | None = None,
+                 spline_order: int | None = None):
         lib = _lib.load()
         d = RadonDesc()
         _lib.check(lib.radon_desc_init(ctypes.byref(d), Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax))
@@ -85,6 +87,8 @@ class Plan:
                 d.tsplit[i] = v
         if rows_per_band is not None:
             d.rows_per_band = rows_per_band
+        if spline_order is not None:
+            d.spline_order = spline_order
         if device is None:
             dev = torch.cuda.current_device()
         else:
@@ -262,7 +266,7 @@ def _grid_array(v, n, name):
 
 
 def _desc(Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax, tau0=0.0, dtau=0.0, sigma=None, omega_c=None,
-          tsplit=None, n_qsplit=1, rows_per_band=None, device=0) -> RadonDesc:
+          tsplit=None, n_qsplit=1, rows_per_band=None, device=0, spline_order=None) -> RadonDesc:
     d = RadonDesc()
     _lib.check(_lib.load().radon_desc_init(ctypes.byref(d), Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax))
     d.tau0, d.dtau, d.n_qsplit, d.device = tau0, dtau, n_qsplit, device
@@ -279,6 +283,8 @@ def _desc(Nt, Nx, Ntau, Nq, dt, dx, qmin, qmax, tau0=0.0, dtau=0.0, sigma=None, 
             d.tsplit[i] = v
     if rows_per_band is not None:
         d.rows_per_band = rows_per_band
+    if spline_order is not None:
+        d.spline_order = spline_order
     return d
 
 
@@ -289,7 +295,8 @@ class Batch:
     ``geometries``: a list of dicts with the ``Plan`` arguments (``Nt``,
     ``Nx``, ``Ntau``, ``Nq``, ``dt``, ``dx``, ``qmin``, ``qmax`` and
     optionally ``tau0``, ``dtau``, ``sigma``, ``omega_c``, ``tsplit``,
-    ``n_qsplit``, ``rows_per_band``; 0 in every geometry times the feasible
+    ``n_qsplit``, ``rows_per_band``, ``spline_order`` (one value for the
+    whole batch); 0 in every ``rows_per_band`` times the feasible
     values over the whole batch; ``x`` / ``q``: given offsets / slownesses as
     in ``Plan``). Data are packed back to back (``f_offsets``,
     ``g_offsets``): gather i is ``f[f_offsets[i]:f_offsets[i+1]]`` viewed as

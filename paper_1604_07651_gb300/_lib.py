@@ -19,7 +19,7 @@ class RadonDesc(ctypes.Structure):
                 ("tau0", _c_double), ("dtau", _c_double), ("sigma", _c_double),
                 ("omega_c", _c_double), ("n_tsplit", _c_int),
                 ("tsplit", _c_double * MAX_TSPLIT), ("n_qsplit", _c_int), ("device", _c_int),
-                ("rows_per_band", _c_int)]
+                ("rows_per_band", _c_int), ("spline_order", _c_int)]
 
 
 class RadonPieceInfo(ctypes.Structure):

@@ -32,6 +32,33 @@ HD void b3_weights(float f, float w[4]) {
     w[3] = f3 * (1.0f / 6.0f);
 }
 
+// Quintic B-spline weights of the six taps i0 .. i0+5, i0 = floor(x) - 2, at
+// fractional part t: B5(t+2), B5(t+1), B5(t), B5(t-1), B5(t-2), B5(t-3), the
+// pieces of (3-|x|)^5 - 6 (2-|x|)^5 + 15 (1-|x|)^5 over 120 (terms with a
+// positive base only), expanded in t; weights d and 5-d are mirror images
+// (t -> 1 - t).
+HD void b5_weights(float t, float w[6]) {
+    const float s = 1.0f - t;
+    const float t2 = t * t, s2 = s * s;
+    const float k = 1.0f / 120.0f;
+    w[0] = s2 * s2 * s * k;
+    w[5] = t2 * t2 * t * k;
+    // 5 t^5 - 20 t^4 + 20 t^3 + 20 t^2 - 50 t + 26 and its mirror
+    w[1] = ((((5.0f * t - 20.0f) * t + 20.0f) * t + 20.0f) * t - 50.0f) * t * k + 26.0f * k;
+    w[4] = ((((5.0f * s - 20.0f) * s + 20.0f) * s + 20.0f) * s - 50.0f) * s * k + 26.0f * k;
+    // -10 t^5 + 30 t^4 - 60 t^2 + 66 and its mirror
+    w[2] = (((-10.0f * t + 30.0f) * t2 - 60.0f) * t2 + 66.0f) * k;
+    w[3] = (((-10.0f * s + 30.0f) * s2 - 60.0f) * s2 + 66.0f) * k;
+}
+
+// B-spline weights of NT = order + 1 taps: cubic (4) or quintic (6).
+template <int NT>
+HD void bspline_weights(float f, float w[NT]);
+template <>
+HD void bspline_weights<4>(float f, float w[4]) { b3_weights(f, w); }
+template <>
+HD void bspline_weights<6>(float f, float w[6]) { b5_weights(f, w); }
+
 // Shared-memory layout of every FFT buffer: element i of a sequence lives at
 // sw(i). XOR-ing the low four bits with the next four spreads the strided
 // stores of the first radix-16 stage (stride 16 elements) over all banks and

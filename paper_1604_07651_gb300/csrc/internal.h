@@ -38,6 +38,7 @@ struct TableArgs {
     double n_t, T, tau0, dtau;
     const double* xb;       // [Nx] rescaled offsets x_k / X (device)
     int jt_lo, nj, Nx, Ntheta, Nrho, Ntau, ncol;
+    int ntaps;              // B-spline taps per axis: 4 (cubic) or 6 (quintic)
 };
 
 // Device-visible description of one sub-problem (one time piece of one
@@ -45,6 +46,7 @@ struct TableArgs {
 struct PieceDev {
     // lattice
     int Ntheta, Nrho, Ptheta, Prho;
+    int ntaps;              // B-spline taps per axis: 4 (cubic) or 6 (quintic)
     int k1max, k2max;
     int CB;                 // spectrum columns per block of the blocked layout
     int nkb;                // number of column blocks: ceil((k2max+1)/CB)
@@ -71,7 +73,8 @@ struct PieceDev {
     const int4* chunks;     // (trace k, first sample j, count <= 8, 0), grouped by tile
     const int2* lband;      // [nbands] candidate output-column range of each band
     const int* colsh;       // [ncol] 28 - ilogb(cell weight bound) of the adjoint column profiles
-    const float4* colw;     // [ncol] theta tap weights of each column
+    const float4* colw;     // [ncol] theta tap weights of each column (taps 0 .. 3)
+    const float2* colw2;    // [ncol] theta tap weights 4 and 5 (six taps only; else null)
     const int* colm0;       // [ncol] first theta tap of each column
     const float* colscale;  // [ncol] output scale 2 X cos(psi) / a
     const cf* K;            // [nkb][k1max+1][CB] kernel spectrum (normalised)
@@ -121,7 +124,10 @@ constexpr int kUnitChunks = 256;
 constexpr int kMaxBandRows = 6;
 
 // Launchers (kernels.cu). The batched ones take n <= kMaxBatch pieces (host
-// copies of the descriptors) and launch one grid over all of them.
+// copies of the descriptors) and launch one grid over all of them. Every
+// piece of one launch has the same number of B-spline taps (`ntaps`, or the
+// first descriptor's); another number than 4 or 6 returns
+// cudaErrorInvalidValue.
 int launch_grid_tiles(const PieceDev* P, int n, const float* f, void* stream);
 int launch_rows_r2c(const PieceDev* P, int n, void* stream);
 int launch_col_profiles(const PieceDev* P, int n, const float* g, void* stream);
@@ -130,10 +136,10 @@ int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream);
 int launch_rows_c2r(const PieceDev* P, int n, void* stream);
 // The same stages over a device-resident batch: `nblocks` blocks, map in S,
 // `smem` the largest dynamic shared memory any piece of the launch needs.
-int launch_grid_tiles_dev(const DevBatch& S, int nblocks, const void* f, int in_type, void* stream);
+int launch_grid_tiles_dev(const DevBatch& S, int nblocks, int ntaps, const void* f, int in_type, void* stream);
 int launch_rows_r2c_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
-int launch_col_profiles_dev(const DevBatch& S, int nblocks, size_t smem, const float* g, void* stream);
-int launch_band_rows_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
+int launch_col_profiles_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, const float* g, void* stream);
+int launch_band_rows_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, void* stream);
 int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream);
 int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
 // Output interpolation: one CTA per output column; cmap[b] = (first piece,
@@ -143,14 +149,14 @@ int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
 // number of time pieces of a column (<= kMaxColPieces); shared memory
 // np_max * nrho_max floats.
 int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,
-                          int ntau_all, int np_all, float* g, void* stream);
+                          int ntau_all, int np_all, int ntaps, float* g, void* stream);
 // Adjoint gather: one CTA per kSampleBlock samples of one gather;
 // smap[b] = (first piece, number of pieces, first sample, 0), or, when
 // np_all > 0 (one gather of Nt_all x Nx_all samples in np_all pieces),
 // samples [b kSampleBlock, (b + 1) kSampleBlock).
 constexpr int kSampleBlock = 256;
 int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, int np_all, int Nt_all,
-                          int Nx_all, void* stream);
+                          int Nx_all, int ntaps, void* stream);
 size_t rows_smem_bytes(const PieceDev& P);
 size_t profile_smem_bytes(const PieceDev& P);
 int launch_sample_table(const TableArgs& A, const double* cj, const double* wk, const int* jfirst,
@@ -181,6 +187,6 @@ size_t colconv_smem_bytes(const PieceDev& P);
 int max_smem_optin();
 // Dynamic shared memory available to the output interpolation's profiles
 // (the opt-in limit less the kernel's static shared memory); 0 on error.
-size_t interp_smem_limit();
+size_t interp_smem_limit(int ntaps);
 
 }  // namespace hr

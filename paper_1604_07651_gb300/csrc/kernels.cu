@@ -276,14 +276,17 @@ __device__ __forceinline__ void rows_pre(const PieceDev& P, cf* X, int mb, int n
     }
 }
 
-// Shared gridding tile: the kTileRows x kTileCols cells plus a halo of 3
-// cells on every side, so that every tap of a sample whose footprint meets
-// the tile lands in it without a bounds check (the halo is dropped at the
-// end: the neighbouring tiles' units add those cells). The odd pitch puts
-// the rows on different banks.
-constexpr int kHalo = 3;
-constexpr int kTilePitch = kTileCols + 2 * kHalo + 1;
-constexpr int kTileRowsH = kTileRows + 2 * kHalo;
+// Shared gridding tile: the kTileRows x kTileCols cells plus a halo of
+// NT - 1 cells on every side (NT taps per axis: 4 cubic, 6 quintic), so that
+// every tap of a sample whose footprint meets the tile lands in it without a
+// bounds check (the halo is dropped at the end: the neighbouring tiles'
+// units add those cells). The odd pitch puts the rows on different banks.
+template <int NT>
+struct GridTile {
+    static constexpr int halo = NT - 1;
+    static constexpr int pitch = kTileCols + 2 * halo + 1;
+    static constexpr int rows = kTileRows + 2 * halo;
+};
 
 // Fixed-point accumulation in shared memory. Integer adds to shared memory
 // are single fire-and-forget instructions, float adds are compare-and-swap
@@ -334,68 +337,69 @@ __device__ __forceinline__ float block_max_abs(float v, float* red) {
 
 // Forward gridding (Eq. (15)) of the gather f[Nx][Nt] onto the lattice
 // P.lat (zeroed before). The plan lists, per tile of kTileRows x kTileCols
-// cells, chunks of at most 8 consecutive samples of one trace whose 4x4
+// cells, chunks of at most 8 consecutive samples of one trace whose NT x NT
 // footprint meets the tile, and cuts every tile's list into work units of at
 // most kUnitChunks chunks (sample density varies by two orders of magnitude
 // over the lattice, so units, not tiles, balance the CTAs), each with the
 // largest total B-spline weight one of its cells can collect. A CTA takes one
 // unit, each thread one chunk: neighbouring threads are 8 samples apart, so
 // their footprints rarely meet, and a thread sums its samples in registers
-// in a 4x4 register window over the cells of its current footprint. When the
+// in an NT x NT register window over the cells of its current footprint. When the
 // first tap (m0, n0) moves by one cell along either axis (consecutive samples
 // of a trace mostly do), only the row or column that leaves the window goes
 // to the fixed-point shared tile and the window slides; a longer jump flushes
 // the whole window. The tile's touched cells are then added to P.lat. A
 // non-finite sample makes the unit's tile NaN (the FFTs that follow would
 // spread it over the whole piece in any case).
-// The window acc[4 a + c] holds cells (wm + a, wn + c); t points at (wm, wn)
-// in the shared tile.
-__device__ __forceinline__ void flush_window(int* t, const float acc[16]) {
+// The window acc[NT a + c] holds cells (wm + a, wn + c); t points at
+// (wm, wn) in the shared tile.
+template <int NT>
+__device__ __forceinline__ void flush_window(int* t, const float (&acc)[NT * NT]) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < NT; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) red_fixed(t + a * kTilePitch + c, acc[4 * a + c]);
+        for (int c = 0; c < NT; ++c) red_fixed(t + a * GridTile<NT>::pitch + c, acc[NT * a + c]);
 }
-// window one row down (row wm leaves) / up (row wm + 3 leaves)
-__device__ __forceinline__ void slide_rows_down(int* t, float acc[16]) {
+// window one row down (row wm leaves) / up (row wm + NT - 1 leaves)
+template <int NT>
+__device__ __forceinline__ void slide_rows_down(int* t, float (&acc)[NT * NT]) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < NT; ++c) {
         red_fixed(t + c, acc[c]);
-        acc[c] = acc[4 + c];
-        acc[4 + c] = acc[8 + c];
-        acc[8 + c] = acc[12 + c];
-        acc[12 + c] = 0.f;
+#pragma unroll
+        for (int a = 0; a + 1 < NT; ++a) acc[NT * a + c] = acc[NT * (a + 1) + c];
+        acc[NT * (NT - 1) + c] = 0.f;
     }
 }
-__device__ __forceinline__ void slide_rows_up(int* t, float acc[16]) {
+template <int NT>
+__device__ __forceinline__ void slide_rows_up(int* t, float (&acc)[NT * NT]) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        red_fixed(t + 3 * kTilePitch + c, acc[12 + c]);
-        acc[12 + c] = acc[8 + c];
-        acc[8 + c] = acc[4 + c];
-        acc[4 + c] = acc[c];
+    for (int c = 0; c < NT; ++c) {
+        red_fixed(t + (NT - 1) * GridTile<NT>::pitch + c, acc[NT * (NT - 1) + c]);
+#pragma unroll
+        for (int a = NT - 1; a > 0; --a) acc[NT * a + c] = acc[NT * (a - 1) + c];
         acc[c] = 0.f;
     }
 }
-// window one column right (column wn leaves) / left (column wn + 3 leaves)
-__device__ __forceinline__ void slide_cols_right(int* t, float acc[16]) {
+// window one column right (column wn leaves) / left (column wn + NT - 1 leaves)
+template <int NT>
+__device__ __forceinline__ void slide_cols_right(int* t, float (&acc)[NT * NT]) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        red_fixed(t + a * kTilePitch, acc[4 * a]);
-        acc[4 * a] = acc[4 * a + 1];
-        acc[4 * a + 1] = acc[4 * a + 2];
-        acc[4 * a + 2] = acc[4 * a + 3];
-        acc[4 * a + 3] = 0.f;
+    for (int a = 0; a < NT; ++a) {
+        red_fixed(t + a * GridTile<NT>::pitch, acc[NT * a]);
+#pragma unroll
+        for (int c = 0; c + 1 < NT; ++c) acc[NT * a + c] = acc[NT * a + c + 1];
+        acc[NT * a + NT - 1] = 0.f;
     }
 }
-__device__ __forceinline__ void slide_cols_left(int* t, float acc[16]) {
+template <int NT>
+__device__ __forceinline__ void slide_cols_left(int* t, float (&acc)[NT * NT]) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        red_fixed(t + a * kTilePitch + 3, acc[4 * a + 3]);
-        acc[4 * a + 3] = acc[4 * a + 2];
-        acc[4 * a + 2] = acc[4 * a + 1];
-        acc[4 * a + 1] = acc[4 * a];
-        acc[4 * a] = 0.f;
+    for (int a = 0; a < NT; ++a) {
+        red_fixed(t + a * GridTile<NT>::pitch + NT - 1, acc[NT * a + NT - 1]);
+#pragma unroll
+        for (int c = NT - 1; c > 0; --c) acc[NT * a + c] = acc[NT * a + c - 1];
+        acc[NT * a] = 0.f;
     }
 }
 
@@ -444,17 +448,18 @@ __device__ __forceinline__ void grid_merge_split(const PieceDev& P, int4 us, int
     if (threadIdx.x == 0) *counter = 0;
 }
 
-template <class Src, class T>
-__global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_constant__ Src B,
-                                                               const T* __restrict__ f) {
-    __shared__ int tile[kTileRowsH * kTilePitch];
+template <class Src, class T, int NT>
+__global__ void __launch_bounds__(kUnitChunks, NT == 4 ? 4 : 2) k_grid_tiles(const __grid_constant__ Src B,
+                                                                             const T* __restrict__ f) {
+    using Tile = GridTile<NT>;
+    __shared__ int tile[Tile::rows * Tile::pitch];
     __shared__ float red[kUnitChunks / 32];
     int bx;
     const PieceDev& P = piece_of(B, bx);
     const int4 u = __ldg(P.units + bx);           // (tile, first chunk, end chunk, 28 - ec)
     const int ti = u.x / P.ntc, tj = u.x - ti * P.ntc;
     const int m_lo = ti * kTileRows, n_lo = tj * kTileCols;
-    for (int i = threadIdx.x; i < kTileRowsH * kTilePitch; i += blockDim.x) tile[i] = 0;
+    for (int i = threadIdx.x; i < Tile::rows * Tile::pitch; i += blockDim.x) tile[i] = 0;
     // one chunk per thread: issue every load of the chunk before the first is used
     const int c = u.y + threadIdx.x;
     int4 ent[8];
@@ -501,9 +506,9 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
     const Pow2Scale sc(u.w - ilogbf(vmax));
 #pragma unroll
     for (int s = 0; s < 8; ++s) v[s] = sc.up(v[s]);
-    float acc[16];
+    float acc[NT * NT];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+    for (int q = 0; q < NT * NT; ++q) acc[q] = 0.f;
     int* win = nullptr;                                  // shared-tile address of the window's (wm, wn)
     int wm = 0, wn = 0;
 #pragma unroll
@@ -514,40 +519,42 @@ __global__ void __launch_bounds__(kUnitChunks, 4) k_grid_tiles(const __grid_cons
         const int dm = m0 - wm, dn = n0 - wn;
         if (win == nullptr || dm < -1 || dm > 1 || dn < -1 || dn > 1) {
             if (win != nullptr) {
-                flush_window(win, acc);
+                flush_window<NT>(win, acc);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+                for (int q = 0; q < NT * NT; ++q) acc[q] = 0.f;
             }
         } else {
-            if (dm == 1) slide_rows_down(win, acc);
-            else if (dm == -1) slide_rows_up(win, acc);
-            win += dm * kTilePitch;
-            if (dn == 1) slide_cols_right(win, acc);
-            else if (dn == -1) slide_cols_left(win, acc);
+            if (dm == 1) slide_rows_down<NT>(win, acc);
+            else if (dm == -1) slide_rows_up<NT>(win, acc);
+            win += dm * Tile::pitch;
+            if (dn == 1) slide_cols_right<NT>(win, acc);
+            else if (dn == -1) slide_cols_left<NT>(win, acc);
         }
         wm = m0;
         wn = n0;
-        win = tile + (m0 - m_lo + kHalo) * kTilePitch + n0 - n_lo + kHalo;
-        float wt[4], wr[4];
-        b3_weights(__int_as_float(e.y), wt);
-        b3_weights(__int_as_float(e.z), wr);
+        win = tile + (m0 - m_lo + Tile::halo) * Tile::pitch + n0 - n_lo + Tile::halo;
+        float wt[NT], wr[NT];
+        bspline_weights<NT>(__int_as_float(e.y), wt);
+        bspline_weights<NT>(__int_as_float(e.z), wr);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < NT; ++a) {
             const float va = v[s] * wt[a];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[4 * a + q] = fmaf(va, wr[q], acc[4 * a + q]);
+            for (int q = 0; q < NT; ++q) acc[NT * a + q] = fmaf(va, wr[q], acc[NT * a + q]);
         }
     }
-    if (win != nullptr) flush_window(win, acc);
+    if (win != nullptr) flush_window<NT>(win, acc);
     __syncthreads();
     if (us.y > 1) {
         grid_merge_split(P, us, m_lo, n_lo, nr, nc,
-                         [&](int i) { return sc.down(tile[(i / kTileCols + kHalo) * kTilePitch + i % kTileCols + kHalo]); });
+                         [&](int i) {
+                             return sc.down(tile[(i / kTileCols + Tile::halo) * Tile::pitch + i % kTileCols + Tile::halo]);
+                         });
         return;
     }
     for (int i = threadIdx.x; i < kTileRows * kTileCols; i += blockDim.x) {   // the tile's only unit
         const int m = i / kTileCols, n = i - m * kTileCols;
-        const int t = tile[(m + kHalo) * kTilePitch + n + kHalo];
+        const int t = tile[(m + Tile::halo) * Tile::pitch + n + Tile::halo];
         if (t != 0 && m < nr && n < nc) P.lat[(size_t)(m_lo + m) * P.Nrho + n_lo + n] = sc.down(t);
     }
 }
@@ -587,7 +594,7 @@ __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src
 // the column's outputs g[l_lo + lc][*], scaled by the column's output scale.
 // Fixed point with the bound max|g| of the column times the column's
 // plan-time weight bound; a non-finite g makes the profile NaN.
-template <class Src>
+template <class Src, int NT>
 __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Src B, const float* __restrict__ g) {
     int* prof = reinterpret_cast<int*>(smem_f);
     __shared__ float red[8];
@@ -627,7 +634,7 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
     // so a non-finite value anywhere in the column poisons the profile)
     const int2 rg = __ldg(P.rrange + lc);
     // every thread takes Q consecutive outputs: their first rho tap is
-    // nondecreasing, so their contributions collect in a 4-cell register
+    // nondecreasing, so their contributions collect in an NT-cell register
     // window that slides one cell as the tap advances (the departing cell goes
     // to the shared profile) and is flushed whole on a longer jump; dozens of
     // outputs that share a cell at small intercept times cost one add
@@ -645,7 +652,9 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
                 v[q] = __ldg(gl + i);
             }
         }
-        float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
+        float w[NT];
+#pragma unroll
+        for (int c = 0; c < NT; ++c) w[c] = 0.f;
         int wn = -1;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -655,33 +664,28 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
                 wn = n0;
             } else if (n0 != wn) {
                 if (n0 == wn + 1) {
-                    red_fixed(prof + wn, w0);
-                    w0 = w1;
-                    w1 = w2;
-                    w2 = w3;
-                    w3 = 0.f;
+                    red_fixed(prof + wn, w[0]);
+#pragma unroll
+                    for (int c = 0; c + 1 < NT; ++c) w[c] = w[c + 1];
+                    w[NT - 1] = 0.f;
                 } else {
-                    red_fixed(prof + wn, w0);
-                    red_fixed(prof + wn + 1, w1);
-                    red_fixed(prof + wn + 2, w2);
-                    red_fixed(prof + wn + 3, w3);
-                    w0 = w1 = w2 = w3 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < NT; ++c) {
+                        red_fixed(prof + wn + c, w[c]);
+                        w[c] = 0.f;
+                    }
                 }
                 wn = n0;
             }
-            float wr[4];
-            b3_weights(__int_as_float(e[q].y), wr);
+            float wr[NT];
+            bspline_weights<NT>(__int_as_float(e[q].y), wr);
             const float x = scl.up(v[q] * sc);
-            w0 = fmaf(x, wr[0], w0);
-            w1 = fmaf(x, wr[1], w1);
-            w2 = fmaf(x, wr[2], w2);
-            w3 = fmaf(x, wr[3], w3);
+#pragma unroll
+            for (int c = 0; c < NT; ++c) w[c] = fmaf(x, wr[c], w[c]);
         }
         if (wn >= 0) {
-            red_fixed(prof + wn, w0);
-            red_fixed(prof + wn + 1, w1);
-            red_fixed(prof + wn + 2, w2);
-            red_fixed(prof + wn + 3, w3);
+#pragma unroll
+            for (int c = 0; c < NT; ++c) red_fixed(prof + wn + c, w[c]);
         }
     }
     __syncthreads();
@@ -689,10 +693,10 @@ __global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Sr
 }
 
 // One band of R <= kMaxBandRows lattice rows: G' rows from the profiles of
-// the band's candidate columns (theta taps of each column from the plan),
+// the band's candidate columns (NT theta taps of each column from the plan),
 // then the row FFT into the half spectrum. Each thread owns four rho cells
 // of every row of the band and sums the columns in order in registers.
-template <class Src>
+template <class Src, int NT>
 __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Src B) {
     int band;
     const PieceDev& P = piece_of(B, band);
@@ -713,12 +717,14 @@ __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Sr
                 const int lc = l - P.l_lo;
                 const int a0 = mb - __ldg(P.colm0 + lc);     // tap of the band's first row
                 const float4 w4 = __ldg(P.colw + lc);
+                const float2 w2 = NT > 4 ? __ldg(P.colw2 + lc) : make_float2(0.f, 0.f);
                 const float4 hv = __ldg(reinterpret_cast<const float4*>(h + (size_t)lc * hp) + n4);
 #pragma unroll
                 for (int r = 0; r < kMaxBandRows; ++r) {
                     const int a = a0 + r;
-                    if (r < nrows && a >= 0 && a < 4) {
-                        const float w = a == 0 ? w4.x : a == 1 ? w4.y : a == 2 ? w4.z : w4.w;
+                    if (r < nrows && a >= 0 && a < NT) {
+                        const float w = a == 0 ? w4.x : a == 1 ? w4.y : a == 2 ? w4.z : a == 3 ? w4.w
+                                      : a == 4 ? w2.x : w2.y;
                         acc[r].x = fmaf(w, hv.x, acc[r].x);
                         acc[r].y = fmaf(w, hv.y, acc[r].y);
                         acc[r].z = fmaf(w, hv.z, acc[r].z);
@@ -977,14 +983,17 @@ __global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ Src
 // Gathers.
 // --------------------------------------------------------------------------
 
-__device__ __forceinline__ float taps16(const float* __restrict__ lat, int Nr, int m0, int n0,
-                                        const float wt[4], const float wr[4]) {
+// NT x NT taps of the lattice at first tap (m0, n0).
+template <int NT>
+__device__ __forceinline__ float taps_nt(const float* __restrict__ lat, int Nr, int m0, int n0,
+                                         const float (&wt)[NT], const float (&wr)[NT]) {
     float s = 0.f;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < NT; ++a) {
         const float* row = lat + (size_t)(m0 + a) * Nr + n0;
-        const float r = __ldg(row) * wr[0] + __ldg(row + 1) * wr[1] + __ldg(row + 2) * wr[2] +
-                        __ldg(row + 3) * wr[3];
+        float r = __ldg(row) * wr[0];
+#pragma unroll
+        for (int c = 1; c < NT; ++c) r += __ldg(row + c) * wr[c];
         s += wt[a] * r;
     }
     return s;
@@ -993,12 +1002,14 @@ __device__ __forceinline__ float taps16(const float* __restrict__ lat, int Nr, i
 // Forward output interpolation (Eq. (17)): one CTA per output column, summed
 // over the time pieces of its slowness piece; cmap[b] = (first piece, number
 // of pieces, column l). As in the adjoint, the column's outputs share its
-// theta taps, so the 4x4 taps separate: the CTA first spreads the four
+// theta taps, so the NT x NT taps separate: the CTA first spreads the NT
 // lattice rows of the column's angle into a rho profile in shared memory,
-//   r[n] = sum_a B3(theta_l - theta_{m0+a}) H[m0 + a][n],
+//   r[n] = sum_a B(theta_l - theta_{m0+a}) H[m0 + a][n],
 // for every time piece at once (shared memory: [np][nrho_max] profiles),
-// then every output takes 4 taps of each piece's profile and sums the pieces
-// in a fixed order. Outputs outside a piece's valid range skip its table.
+// then every output takes NT taps of each piece's profile and sums the
+// pieces in a fixed order. Outputs outside a piece's valid range skip its
+// table.
+template <int NT>
 __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restrict__ pieces,
                                                         const int4* __restrict__ cmap, int nrho_max,
                                                         int ntau_all, int np_all, float* __restrict__ g) {
@@ -1010,6 +1021,7 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
     if (np > kMaxColPieces || (size_t)np * nrho_max * sizeof(float) > dyn_smem_bytes()) return;
     // per-piece column data, loaded for all pieces at once
     __shared__ float4 s_w4[kMaxColPieces];
+    __shared__ float2 s_w2[NT > 4 ? kMaxColPieces : 1];
     __shared__ const float* s_r0[kMaxColPieces];
     __shared__ const int2* s_rt[kMaxColPieces];
     __shared__ float s_sc[kMaxColPieces];
@@ -1019,6 +1031,7 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
         const PieceDev& P = pieces[c.x + threadIdx.x];
         const int lc = l - P.l_lo;
         s_w4[threadIdx.x] = __ldg(P.colw + lc);
+        if (NT > 4) s_w2[threadIdx.x] = __ldg(P.colw2 + lc);
         s_sc[threadIdx.x] = __ldg(P.colscale + lc);
         s_r0[threadIdx.x] = P.lat + (size_t)__ldg(P.colm0 + lc) * P.Nrho;
         s_rt[threadIdx.x] = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * Ntau);
@@ -1026,7 +1039,7 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
         s_nr[threadIdx.x] = P.Nrho;
     }
     __syncthreads();
-    // theta taps (the column's four lattice rows) of every piece: the rho
+    // theta taps (the column's NT lattice rows) of every piece: the rho
     // profiles, np * nrho_max floats; all pieces' loads in flight together
     for (int p = 0; p < np; ++p) {
         const int Nr = s_nr[p];
@@ -1037,7 +1050,13 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
         for (int n = threadIdx.x; n < Nr; n += blockDim.x) {
             const float a0 = __ldg(r0 + n), a1 = __ldg(r0 + Nr + n);
             const float a2 = __ldg(r0 + 2 * Nr + n), a3 = __ldg(r0 + 3 * Nr + n);
-            prof[n] = w4.x * a0 + w4.y * a1 + w4.z * a2 + w4.w * a3;
+            if (NT > 4) {
+                const float2 w2 = s_w2[p];
+                const float a4 = __ldg(r0 + 4 * Nr + n), a5 = __ldg(r0 + 5 * Nr + n);
+                prof[n] = w4.x * a0 + w4.y * a1 + w4.z * a2 + w4.w * a3 + w2.x * a4 + w2.y * a5;
+            } else {
+                prof[n] = w4.x * a0 + w4.y * a1 + w4.z * a2 + w4.w * a3;
+            }
         }
     }
     __syncthreads();
@@ -1064,10 +1083,13 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (e[u].x < 0) continue;
-                float wr[4];
-                b3_weights(__int_as_float(e[u].y), wr);
+                float wr[NT];
+                bspline_weights<NT>(__int_as_float(e[u].y), wr);
                 const float* r = rp + e[u].x;
-                acc[u] += scp * (wr[0] * r[0] + wr[1] * r[1] + wr[2] * r[2] + wr[3] * r[3]);
+                float t = wr[0] * r[0];
+#pragma unroll
+                for (int c = 1; c < NT; ++c) t += wr[c] * r[c];
+                acc[u] += scp * t;
             }
         }
 #pragma unroll
@@ -1079,10 +1101,11 @@ __global__ void __launch_bounds__(256) k_interp_columns(const PieceDev* __restri
 }
 
 // Adjoint of the gridding (transpose of Eq. (15)): every gather sample reads
-// the 4x4 taps of each sub-problem that holds it. One CTA per kSampleBlock
+// the NT x NT taps of each sub-problem that holds it. One CTA per kSampleBlock
 // samples of one gather: smap[b] = (first piece, number of pieces, first
 // sample of the block within the gather).
-__global__ void __launch_bounds__(kSampleBlock, 8) k_gather_samples(const PieceDev* __restrict__ pieces,
+template <int NT>
+__global__ void __launch_bounds__(kSampleBlock, NT == 4 ? 8 : 4) k_gather_samples(const PieceDev* __restrict__ pieces,
                                                                     const int4* __restrict__ smap,
                                                                     float* __restrict__ f, int np_all, int Nt_all,
                                                                     int Nx_all) {
@@ -1102,10 +1125,10 @@ __global__ void __launch_bounds__(kSampleBlock, 8) k_gather_samples(const PieceD
         const int4 e = __ldg(reinterpret_cast<const int4*>(P.stab + (size_t)k * P.nj + (j - P.jt_lo)));
         const float w = __int_as_float(e.w);
         if (w == 0.f) continue;
-        float wt[4], wr[4];
-        b3_weights(__int_as_float(e.y), wt);
-        b3_weights(__int_as_float(e.z), wr);
-        acc += w * taps16(P.lat, P.Nrho, e.x >> 16, e.x & 0xffff, wt, wr);
+        float wt[NT], wr[NT];
+        bspline_weights<NT>(__int_as_float(e.y), wt);
+        bspline_weights<NT>(__int_as_float(e.z), wr);
+        acc += w * taps_nt<NT>(P.lat, P.Nrho, e.x >> 16, e.x & 0xffff, wt, wr);
     }
     f[(np_all > 0 ? 0 : pieces[m.x].f_off) + idx] = acc;
 }
@@ -1129,9 +1152,10 @@ __global__ void k_sample_table(TableArgs A, const double* __restrict__ cj, const
     const double xth = (atan2(u2, u1) - A.theta0) / A.dtheta;
     const double xrh = (0.5 * log(r2) - A.rho0) / A.drho;
     const double fm = floor(xth), fn = floor(xrh);
-    int m0 = (int)fm - 1, n0 = (int)fn - 1;
+    const int back = A.ntaps / 2 - 1;            // first tap: floor - (order - 1) / 2
+    int m0 = (int)fm - back, n0 = (int)fn - back;
     double w = (j >= jfirst[k]) ? cj[jl] * wk[k] / sqrt(r2) : 0.0;
-    if (m0 < 0 || m0 + 3 >= A.Ntheta || n0 < 0 || n0 + 3 >= A.Nrho) {
+    if (m0 < 0 || m0 + A.ntaps - 1 >= A.Ntheta || n0 < 0 || n0 + A.ntaps - 1 >= A.Nrho) {
         w = 0.0;
         m0 = 0;
         n0 = 0;
@@ -1160,8 +1184,8 @@ __global__ void k_radon_table(TableArgs A, const double* __restrict__ qb2, Radon
     if (e >= A.a_r && e <= A.r_max) {
         const double xrh = (log(e) - A.rho0) / A.drho;
         const double fn = floor(xrh);
-        const int n0 = (int)fn - 1;
-        if (n0 >= 0 && n0 + 3 < A.Nrho) {
+        const int n0 = (int)fn - (A.ntaps / 2 - 1);
+        if (n0 >= 0 && n0 + A.ntaps - 1 < A.Nrho) {
             r.n0 = n0;
             r.fr = (float)(xrh - fn);
         }
@@ -1339,10 +1363,26 @@ static int make_batch(const PieceDev* P, int n, PieceBatch& B, F&& count) {
     return total;
 }
 
+// Kernels with B-spline taps exist for 4 (cubic) and 6 (quintic) taps per
+// axis; every piece of one launch has the same number.
+#define HR_TAPS(NTAPS, ...)                                           \
+    do {                                                              \
+        if ((NTAPS) == 6) {                                           \
+            constexpr int NT = 6;                                     \
+            __VA_ARGS__;                                              \
+        } else if ((NTAPS) == 4) {                                    \
+            constexpr int NT = 4;                                     \
+            __VA_ARGS__;                                              \
+        } else {                                                      \
+            return (int)cudaErrorInvalidValue;                        \
+        }                                                             \
+    } while (0)
+
 int launch_grid_tiles(const PieceDev* P, int n, const float* f, void* stream) {
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nunits; });
-    if (nb > 0) k_grid_tiles<PieceBatch, float><<<nb, kUnitChunks, 0, (cudaStream_t)stream>>>(B, f);
+    if (nb > 0)
+        HR_TAPS(P[0].ntaps, (k_grid_tiles<PieceBatch, float, NT><<<nb, kUnitChunks, 0, (cudaStream_t)stream>>>(B, f)));
     return check_launch();
 }
 
@@ -1372,17 +1412,22 @@ int launch_rows_r2c(const PieceDev* P, int n, void* stream) {
 
 int launch_col_profiles(const PieceDev* P, int n, const float* g, void* stream) {
     const size_t sm = max_over(P, n, profile_smem_bytes);
-    if (int e = set_smem((const void*)k_col_profiles<PieceBatch>, sm)) return e;
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.l_hi - q.l_lo + 1; });
-    if (nb > 0) k_col_profiles<PieceBatch><<<nb, 256, sm, (cudaStream_t)stream>>>(B, g);
+    HR_TAPS(P[0].ntaps, {
+        if (int e = set_smem((const void*)k_col_profiles<PieceBatch, NT>, sm)) return e;
+        if (nb > 0) k_col_profiles<PieceBatch, NT><<<nb, 256, sm, (cudaStream_t)stream>>>(B, g);
+    });
     return check_launch();
 }
 
 int launch_band_rows(const PieceDev* P, int n, void* stream) {
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
-    return set_and_launch(k_band_rows<PieceBatch>, nb, max_over(P, n, rows_smem_bytes), B, stream);
+    const size_t sm = max_over(P, n, rows_smem_bytes);
+    if (P[0].ntaps == 6) return set_and_launch(k_band_rows<PieceBatch, 6>, nb, sm, B, stream);
+    if (P[0].ntaps == 4) return set_and_launch(k_band_rows<PieceBatch, 4>, nb, sm, B, stream);
+    return (int)cudaErrorInvalidValue;
 }
 
 int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream) {
@@ -1400,13 +1445,15 @@ int launch_rows_c2r(const PieceDev* P, int n, void* stream) {
     return set_and_launch(k_rows_c2r<PieceBatch>, nb, max_over(P, n, rows_smem_bytes), B, stream);
 }
 
-int launch_grid_tiles_dev(const DevBatch& S, int nblocks, const void* f, int in_type, void* stream) {
+int launch_grid_tiles_dev(const DevBatch& S, int nblocks, int ntaps, const void* f, int in_type, void* stream) {
     if (nblocks <= 0) return 0;
-    if (in_type == kInBF16)
-        k_grid_tiles<DevBatch, __nv_bfloat16><<<nblocks, kUnitChunks, 0, (cudaStream_t)stream>>>(
-            S, (const __nv_bfloat16*)f);
-    else
-        k_grid_tiles<DevBatch, float><<<nblocks, kUnitChunks, 0, (cudaStream_t)stream>>>(S, (const float*)f);
+    HR_TAPS(ntaps, {
+        if (in_type == kInBF16)
+            k_grid_tiles<DevBatch, __nv_bfloat16, NT><<<nblocks, kUnitChunks, 0, (cudaStream_t)stream>>>(
+                S, (const __nv_bfloat16*)f);
+        else
+            k_grid_tiles<DevBatch, float, NT><<<nblocks, kUnitChunks, 0, (cudaStream_t)stream>>>(S, (const float*)f);
+    });
     return check_launch();
 }
 
@@ -1414,14 +1461,18 @@ int launch_rows_r2c_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
     return set_and_launch(k_rows_r2c<DevBatch>, nblocks, smem, S, stream);
 }
 
-int launch_col_profiles_dev(const DevBatch& S, int nblocks, size_t smem, const float* g, void* stream) {
-    if (int e = set_smem((const void*)k_col_profiles<DevBatch>, smem)) return e;
-    if (nblocks > 0) k_col_profiles<DevBatch><<<nblocks, 256, smem, (cudaStream_t)stream>>>(S, g);
+int launch_col_profiles_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, const float* g, void* stream) {
+    HR_TAPS(ntaps, {
+        if (int e = set_smem((const void*)k_col_profiles<DevBatch, NT>, smem)) return e;
+        if (nblocks > 0) k_col_profiles<DevBatch, NT><<<nblocks, 256, smem, (cudaStream_t)stream>>>(S, g);
+    });
     return check_launch();
 }
 
-int launch_band_rows_dev(const DevBatch& S, int nblocks, size_t smem, void* stream) {
-    return set_and_launch(k_band_rows<DevBatch>, nblocks, smem, S, stream);
+int launch_band_rows_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, void* stream) {
+    if (ntaps == 6) return set_and_launch(k_band_rows<DevBatch, 6>, nblocks, smem, S, stream);
+    if (ntaps == 4) return set_and_launch(k_band_rows<DevBatch, 4>, nblocks, smem, S, stream);
+    return (int)cudaErrorInvalidValue;
 }
 
 int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream) {
@@ -1436,9 +1487,10 @@ int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
 
 // Dynamic shared memory the output interpolation may take on the current
 // device: the opt-in limit less the kernel's own static shared arrays.
-size_t interp_smem_limit() {
+size_t interp_smem_limit(int ntaps) {
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, (const void*)k_interp_columns) != cudaSuccess) {
+    const void* fn = ntaps == 6 ? (const void*)k_interp_columns<6> : (const void*)k_interp_columns<4>;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1447,19 +1499,22 @@ size_t interp_smem_limit() {
 }
 
 int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,
-                          int ntau_all, int np_all, float* g, void* stream) {
+                          int ntau_all, int np_all, int ntaps, float* g, void* stream) {
     if (np_max > kMaxColPieces) return (int)cudaErrorInvalidValue;
     const size_t sm = (size_t)np_max * nrho_max * sizeof(float);
-    if (int e = set_smem((const void*)k_interp_columns, sm)) return e;
-    if (ncols > 0)
-        k_interp_columns<<<ncols, 256, sm, (cudaStream_t)stream>>>(pieces, cmap, nrho_max, ntau_all, np_all, g);
+    HR_TAPS(ntaps, {
+        if (int e = set_smem((const void*)k_interp_columns<NT>, sm)) return e;
+        if (ncols > 0)
+            k_interp_columns<NT><<<ncols, 256, sm, (cudaStream_t)stream>>>(pieces, cmap, nrho_max, ntau_all, np_all, g);
+    });
     return check_launch();
 }
 
 int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, int np_all, int Nt_all,
-                          int Nx_all, void* stream) {
+                          int Nx_all, int ntaps, void* stream) {
     if (nblocks > 0)
-        k_gather_samples<<<nblocks, kSampleBlock, 0, (cudaStream_t)stream>>>(pieces, smap, f, np_all, Nt_all, Nx_all);
+        HR_TAPS(ntaps, (k_gather_samples<NT><<<nblocks, kSampleBlock, 0, (cudaStream_t)stream>>>(pieces, smap, f, np_all,
+                                                                                                Nt_all, Nx_all)));
     return check_launch();
 }
 

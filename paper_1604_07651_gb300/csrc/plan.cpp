@@ -257,10 +257,14 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
     std::sort(x.begin(), x.end());
 }
 
-double sinc4(double w) {
+// Fourier transform of the centred B-spline of degree `order` (3 or 5) at
+// frequency w in cycles per cell: sinc^(order + 1).
+double bspline_symbol(double w, int order) {
     if (w == 0.0) return 1.0;
-    double s = std::sin(kPi * w) / (kPi * w);
-    return s * s * s * s;
+    const double s = std::sin(kPi * w) / (kPi * w);
+    double r = 1.0;
+    for (int i = 0; i <= order; ++i) r *= s;
+    return r;
 }
 
 double b3(double x) {
@@ -268,6 +272,26 @@ double b3(double x) {
     if (ax < 1.0) return 2.0 / 3.0 - ax * ax + 0.5 * ax * ax * ax;
     if (ax < 2.0) return (2.0 - ax) * (2.0 - ax) * (2.0 - ax) / 6.0;
     return 0.0;
+}
+
+// Centred quintic B-spline: truncated powers (3-|x|)^5 - 6 (2-|x|)^5 +
+// 15 (1-|x|)^5 over 120, each term only where its base is positive.
+double b5(double x) {
+    const double a = std::fabs(x);
+    auto tp = [](double u) { return u > 0 ? u * u * u * u * u : 0.0; };
+    return (tp(3 - a) - 6 * tp(2 - a) + 15 * tp(1 - a)) / 120.0;
+}
+
+double bspline(double x, int order) { return order == 5 ? b5(x) : b3(x); }
+
+// Taps per axis (order + 1) and guard cells per lattice side ((order + 1) / 2).
+int spline_taps(int order) { return order + 1; }
+int guard_cells(int order) { return (order + 1) / 2; }
+
+// The kernels' float tap weights (4 or 6 taps) at fractional part f.
+void spline_weights(int ntaps, float f, float* w) {
+    if (ntaps == 6) bspline_weights<6>(f, w);
+    else bspline_weights<4>(f, w);
 }
 
 }  // namespace
@@ -283,6 +307,7 @@ struct HostPiece {
     std::vector<int> jfirst;
     int Rmax = 1;                                  // most rows per band shared memory allows
     int max_tile_chunks = 0;                       // most gridding chunks of one tile
+    int order = 3;                                 // B-spline degree
     const int2* lband_R[kMaxBandRows + 1] = {};    // band column ranges for each rows-per-band
     PieceDev dev{};
 };
@@ -391,7 +416,9 @@ radon_status check_desc(const radon_desc* d) {
     if (d->n_qsplit < 1 || d->n_qsplit > 64)
         return fail(RADON_ERR_INVALID_ARG, "need 1 <= n_qsplit <= 64");
     if (d->rows_per_band < 0 || d->rows_per_band > kMaxBandRows)
-        return fail(RADON_ERR_INVALID_ARG, "need 0 <= rows_per_band <= 4");
+        return fail(RADON_ERR_INVALID_ARG, "need 0 <= rows_per_band <= 6");
+    if (d->spline_order != 3 && d->spline_order != 5)
+        return fail(RADON_ERR_INVALID_ARG, "spline_order must be 3 (cubic) or 5 (quintic)");
     return RADON_OK;
 }
 
@@ -427,6 +454,7 @@ radon_status make_geometry(const radon_desc& d, const Grid& g, const TPiece& tp,
     const double T = n_t * d.dt, X = offset_X(d, g);
     const std::vector<double> q = q_grid(d, g);
     const std::vector<double> xbar = offsets_bar(d, g);
+    h.order = d.spline_order;
     h.tpiece = tp.idx;
     h.jt_lo = tp.lo;
     h.jt_hi = tp.hi;
@@ -523,10 +551,11 @@ radon_status make_geometry(const radon_desc& d, const Grid& g, const TPiece& tp,
     h.n_rho = std::max(1, (int)std::ceil(d.sigma * L_rho / deta - 1e-9));
     h.dtheta = h.beta / h.n_theta;
     h.drho = L_rho / h.n_rho;
-    h.theta0 = -h.beta / 2 - 2 * h.dtheta;
-    h.rho0 = std::log(h.a_r) - 2 * h.drho;
-    h.Ntheta = h.n_theta + 5;
-    h.Nrho = h.n_rho + 5;
+    const int guard = guard_cells(h.order);
+    h.theta0 = -h.beta / 2 - guard * h.dtheta;
+    h.rho0 = std::log(h.a_r) - guard * h.drho;
+    h.Ntheta = h.n_theta + 2 * guard + 1;
+    h.Nrho = h.n_rho + 2 * guard + 1;
     h.theta_m = std::min((h.Ntheta - 1) * h.dtheta, std::acos(std::exp(-(h.Nrho - 1) * h.drho)));
     const int Ka = (int)std::ceil(h.theta_m / h.dtheta - 1e-9);
     const int Kr = (int)std::ceil(-std::log(std::cos(h.theta_m)) / h.drho - 1e-9);
@@ -602,9 +631,9 @@ radon_status kernel_spectrum(radon_plan_s* p, const HostPiece& h, int CB, int nk
     const double norm = 1.0 / (2.0 * h.Ptheta * h.Prho);
     Kout.assign((size_t)nkb * n1 * CB, cf{0.f, 0.f});
     for (int k1 = 0; k1 < n1; ++k1) {
-        const double s1 = sinc4((double)k1 / h.Ptheta);
+        const double s1 = bspline_symbol((double)k1 / h.Ptheta, h.order);
         for (int k2 = 0; k2 < n2; ++k2) {
-            const double s2 = sinc4((double)k2 / h.Prho);
+            const double s2 = bspline_symbol((double)k2 / h.Prho, h.order);
             const double den = (s1 * s2) * (s1 * s2);
             const double zr = 2.0 * Zr[(size_t)k1 * n2 + k2], zi = 2.0 * Zi[(size_t)k1 * n2 + k2];
             const int kb = k2 / CB, c = k2 % CB;
@@ -617,10 +646,11 @@ radon_status kernel_spectrum(radon_plan_s* p, const HostPiece& h, int CB, int nk
 // Tile lists of the forward gridding, built from the device's own position
 // table (copied back once) so that membership matches the kernel exactly:
 // for every tile, the chunks of at most 8 consecutive samples of one trace
-// whose 4x4 footprint meets it (along a trace the footprint moves
+// whose NT x NT footprint meets it (along a trace the footprint moves
 // monotonically, so each trace meets a tile in one run of samples).
 radon_status build_tile_lists(radon_plan_s* p, HostPiece& h, PieceDev& P) {
     const int TR = kTileRows, TC = kTileCols;
+    const int NT = P.ntaps;
     P.ntr = (h.Ntheta + TR - 1) / TR;
     P.ntc = (h.Nrho + TC - 1) / TC;
     const int ntiles = P.ntr * P.ntc;
@@ -635,8 +665,8 @@ radon_status build_tile_lists(radon_plan_s* p, HostPiece& h, PieceDev& P) {
             if (e.w == 0.f) continue;
             const int m0 = e.mn >> 16, n0 = e.mn & 0xffff;
             const int j = P.jt_lo + jl;
-            for (int ti = m0 / TR; ti <= (m0 + 3) / TR && ti < P.ntr; ++ti)
-                for (int tj = n0 / TC; tj <= (n0 + 3) / TC && tj < P.ntc; ++tj) {
+            for (int ti = m0 / TR; ti <= (m0 + NT - 1) / TR && ti < P.ntr; ++ti)
+                for (int tj = n0 / TC; tj <= (n0 + NT - 1) / TC && tj < P.ntc; ++tj) {
                     const int t = ti * P.ntc + tj;
                     if (last_k[t] == k && last_j[t] == j - 1 && runs[t].back().z < 8) {
                         runs[t].back().z += 1;
@@ -668,12 +698,12 @@ radon_status build_tile_lists(radon_plan_s* p, HostPiece& h, PieceDev& P) {
                 w += ch.z;
                 for (int sidx = 0; sidx < ch.z; ++sidx) {
                     const SampleEnt& se = tab[(size_t)ch.x * P.nj + (ch.y - P.jt_lo) + sidx];
-                    float wt[4], wr[4];
-                    b3_weights(se.ft, wt);
-                    b3_weights(se.fr, wr);
+                    float wt[6], wr[6];
+                    spline_weights(NT, se.ft, wt);
+                    spline_weights(NT, se.fr, wr);
                     const int m0 = (se.mn >> 16) - m_lo, n0 = (se.mn & 0xffff) - n_lo;
-                    for (int a = 0; a < 4; ++a)
-                        for (int b = 0; b < 4; ++b) {
+                    for (int a = 0; a < NT; ++a)
+                        for (int b = 0; b < NT; ++b) {
                             const int m = m0 + a, n = n0 + b;
                             if (m >= 0 && m < TR && n >= 0 && n < TC) cell[(size_t)m * TC + n] += (double)wt[a] * wr[b];
                         }
@@ -732,6 +762,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     PieceDev& P = h.dev;
     P.Ntheta = h.Ntheta;
     P.Nrho = h.Nrho;
+    P.ntaps = spline_taps(h.order);
     P.Ptheta = h.Ptheta;
     P.Prho = h.Prho;
     P.k1max = h.k1max;
@@ -786,7 +817,9 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     // output columns: theta taps, scale, e^rho polynomial; band column ranges
     const std::vector<double> q = q_grid(d, p->grid);
     const int ncol = h.l_hi - h.l_lo + 1;
+    const int NT = P.ntaps;
     std::vector<float4> colw(ncol);
+    std::vector<float2> colw2(NT > 4 ? ncol : 0);
     std::vector<int> colm0(ncol);
     std::vector<float> colscale(ncol);
     std::vector<double> qb2(ncol);
@@ -798,23 +831,25 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
         const double theta = h.alpha - psi;
         const double xth = (theta - h.theta0) / h.dtheta;
         const double fl = std::floor(xth);
-        int m0 = (int)fl - 1;
-        m0 = std::min(std::max(m0, 0), h.Ntheta - 4);
-        const double fr = xth - (m0 + 1);
+        int m0 = (int)fl - (NT / 2 - 1);              // first tap: floor - (order - 1) / 2
+        m0 = std::min(std::max(m0, 0), h.Ntheta - NT);
+        double w[6];
+        for (int a = 0; a < NT; ++a) w[a] = bspline(xth - (m0 + a), h.order);
         colm0[lc] = m0;
-        colw[lc] = make_float4((float)b3(fr + 1.0), (float)b3(fr), (float)b3(fr - 1.0), (float)b3(fr - 2.0));
+        colw[lc] = make_float4((float)w[0], (float)w[1], (float)w[2], (float)w[3]);
+        if (NT > 4) colw2[lc] = make_float2((float)w[4], (float)w[5]);
         colscale[lc] = (float)(2.0 * X * std::cos(psi) / h.a);
         qb2[lc] = m;
     }
-    // candidate output columns of every band of rb rows: those whose four
-    // theta taps m0 .. m0+3 meet the band
+    // candidate output columns of every band of rb rows: those whose NT
+    // theta taps m0 .. m0+NT-1 meet the band
     for (int rb = 1; rb <= Rmax; ++rb) {
         const int nbands = (h.Ntheta + rb - 1) / rb;
         std::vector<int2> lband(nbands, int2{1, 0});
         for (int lc = 0; lc < ncol; ++lc) {
             const int m0 = colm0[lc];                        // >= 0
             const int first = (m0 + rb) / rb - 1;             // ceil((m0 + 1) / rb) - 1
-            const int last = std::min(nbands - 1, (m0 + 3) / rb);
+            const int last = std::min(nbands - 1, (m0 + NT - 1) / rb);
             for (int b = first; b <= last; ++b) {
                 int2& r = lband[b];
                 const int l = h.l_lo + lc;
@@ -846,6 +881,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     if (radon_status s = kernel_spectrum(p, h, CB, P.nkb, K)) return s;
 
     radon_status s = RADON_OK;
+    if (NT > 4 && (s = dev_upload(p, colw2, &P.colw2))) return s;
     if ((s = dev_upload(p, colw, &P.colw)) || (s = dev_upload(p, colm0, &P.colm0)) ||
         (s = dev_upload(p, colscale, &P.colscale)) || (s = dev_upload(p, K, &P.K)) ||
         (s = dev_upload(p, twM, &P.twM)) || (s = dev_upload(p, twP, &P.twP)) || (s = dev_upload(p, rpos, &P.rpos)) ||
@@ -876,6 +912,7 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
     A.Nrho = h.Nrho;
     A.Ntau = d.Ntau;
     A.ncol = ncol;
+    A.ntaps = NT;
     const double *dcj = nullptr, *dwk = nullptr, *dqb2 = nullptr, *dxb = nullptr;
     const int* djf = nullptr;
     void* tab = nullptr;
@@ -911,9 +948,9 @@ radon_status build_piece_tables(radon_plan_s* p, HostPiece& h, const std::vector
                 if (e.n0 < 0) continue;
                 rrange[lc].x = std::min(rrange[lc].x, i);
                 rrange[lc].y = std::max(rrange[lc].y, i);
-                float wr[4];
-                b3_weights(e.fr, wr);
-                for (int c = 0; c < 4; ++c) prof[e.n0 + c] += (double)colscale[lc] * wr[c];
+                float wr[6];
+                spline_weights(NT, e.fr, wr);
+                for (int c = 0; c < NT; ++c) prof[e.n0 + c] += (double)colscale[lc] * wr[c];
             }
             const double cmax = *std::max_element(prof.begin(), prof.end());
             colsh[lc] = 28 - std::ilogb(cmax > 0 ? cmax : 1.0);
@@ -1015,6 +1052,7 @@ extern "C" radon_status radon_desc_init(radon_desc* d, int Nt, int Nx, int Ntau,
     d->n_qsplit = 1;
     d->device = -1;
     d->rows_per_band = 3;
+    d->spline_order = 3;
     return RADON_OK;
 }
 
@@ -1226,7 +1264,7 @@ extern "C" radon_status radon_plan_create_grid(radon_plan* out, const radon_desc
     for (const int4& c : cmap) p->col_pieces = std::max(p->col_pieces, c.y);
     p->nsblocks = (int)smap.size();
     // the output interpolation holds one rho profile per time piece of a column
-    if ((size_t)p->col_pieces * p->nrho_max * sizeof(float) > interp_smem_limit()) {
+    if ((size_t)p->col_pieces * p->nrho_max * sizeof(float) > interp_smem_limit(spline_taps(p->d.spline_order))) {
         destroy_plan(p);
         return fail(RADON_ERR_UNSUPPORTED, "too many time pieces for the lattice length along rho "
                                            "(the output interpolation's profiles exceed shared memory)");
@@ -1298,7 +1336,8 @@ static radon_status run_forward(radon_plan_s* p, const PieceDev* P, const PieceD
     if (radon_status s = cuda_status(
             timed(p, 4, b_lat + gb, stream,
                   [&] { return launch_interp_columns(dP, p->cmap, p->ncols, p->nrho_max, p->col_pieces, p->d.Ntau,
-                                               p->qpieces.size() == 1 ? np : 0, g, stream); }),
+                                               p->qpieces.size() == 1 ? np : 0, spline_taps(p->d.spline_order), g,
+                                               stream); }),
             "interpolation"))
         return s;
     return RADON_OK;
@@ -1356,7 +1395,7 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
     return cuda_status(timed(p, 8, b_lat + 4.0 * p->d.Nt * p->d.Nx, stream,
                              [&] {
                                  return launch_gather_samples(p->dev_pieces, p->smap, p->nsblocks, f, np, p->d.Nt,
-                                                              p->d.Nx, stream);
+                                                              p->d.Nx, spline_taps(p->d.spline_order), stream);
                              }),
                        "adjoint gridding");
 }
@@ -1528,6 +1567,7 @@ struct radon_batch_s {
     int ncols = 0, nsblocks = 0, col_pieces = 0;
     size_t smem_rows = 0, smem_cols = 0, smem_prof = 0;
     int nrho_max = 0;
+    int ntaps = 4;                             // B-spline taps per axis of every gather
     float* lat_all = nullptr;
     size_t lat_bytes = 0;
 };
@@ -1549,6 +1589,9 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
     if (!out) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || !descs) return fail(RADON_ERR_INVALID_ARG, "a batch needs n >= 1 descriptors");
+    for (int i = 1; i < n; ++i)
+        if (descs[i].spline_order != descs[0].spline_order)
+            return fail(RADON_ERR_UNSUPPORTED, "the gathers of a batch must share the B-spline order");
     arm_alloc_hook();
     radon_batch_s* b = new (std::nothrow) radon_batch_s();
     if (!b) return fail(RADON_ERR_OOM, "host allocation failed");
@@ -1597,6 +1640,7 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
         destroy_batch(b);
         return fail(first_err, first_msg);
     }
+    b->ntaps = spline_taps(descs[0].spline_order);
     b->f_off.push_back(0);
     b->g_off.push_back(0);
     for (radon_plan_s* p : b->plans) {
@@ -1673,7 +1717,7 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
     b->ncols = (int)cmap.size();
     for (const int4& c : cmap) b->col_pieces = std::max(b->col_pieces, c.y);
     b->nsblocks = (int)smap.size();
-    if ((size_t)b->col_pieces * b->nrho_max * sizeof(float) > interp_smem_limit()) {
+    if ((size_t)b->col_pieces * b->nrho_max * sizeof(float) > interp_smem_limit(b->ntaps)) {
         destroy_batch(b);
         return fail(RADON_ERR_UNSUPPORTED, "too many time pieces for the lattice length along rho "
                                            "(the output interpolation's profiles exceed shared memory)");
@@ -1717,7 +1761,7 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
                 if ((st = apply(R))) return 1;
                 const DevBatch Bd{b->pieces, b->map_bands};
                 if (int e = launch_rows_r2c_dev(Bd, b->n_bands, b->smem_rows, nullptr)) return e;
-                if (int e = launch_band_rows_dev(Bd, b->n_bands, b->smem_rows, nullptr)) return e;
+                if (int e = launch_band_rows_dev(Bd, b->n_bands, b->ntaps, b->smem_rows, nullptr)) return e;
                 if (int e = launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, nullptr)) return e;
                 return 0;
             },
@@ -1769,13 +1813,13 @@ extern "C" radon_status radon_batch_fwd(radon_batch b, const void* f, int in_typ
     const DevBatch U{b->pieces, b->map_units}, Bd{b->pieces, b->map_bands}, K{b->pieces, b->map_kb};
     if (cudaError_t e = cudaMemsetAsync(b->lat_all, 0, b->lat_bytes, (cudaStream_t)stream))
         return cuda_status((int)e, "clearing the lattices");
-    if (radon_status s = cuda_status(launch_grid_tiles_dev(U, b->n_units, f, in_type, stream), "gridding")) return s;
+    if (radon_status s = cuda_status(launch_grid_tiles_dev(U, b->n_units, b->ntaps, f, in_type, stream), "gridding")) return s;
     if (radon_status s = cuda_status(launch_rows_r2c_dev(Bd, b->n_bands, b->smem_rows, stream), "row FFT")) return s;
     if (radon_status s = cuda_status(launch_colconv_dev(K, b->n_kb, b->smem_cols, 0, stream), "convolution"))
         return s;
     if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
         return s;
-    return cuda_status(launch_interp_columns(b->pieces, b->cmap, b->ncols, b->nrho_max, b->col_pieces, 0, 0, g, stream),
+    return cuda_status(launch_interp_columns(b->pieces, b->cmap, b->ncols, b->nrho_max, b->col_pieces, 0, 0, b->ntaps, g, stream),
                        "interpolation");
 }
 
@@ -1784,17 +1828,17 @@ extern "C" radon_status radon_batch_adj(radon_batch b, const float* g, float* f,
     if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
     DeviceGuard guard(b->device);
     const DevBatch C{b->pieces, b->map_cols}, Bd{b->pieces, b->map_bands}, K{b->pieces, b->map_kb};
-    if (radon_status s = cuda_status(launch_col_profiles_dev(C, b->n_cols, b->smem_prof, g, stream),
+    if (radon_status s = cuda_status(launch_col_profiles_dev(C, b->n_cols, b->ntaps, b->smem_prof, g, stream),
                                      "adjoint interpolation (profiles)"))
         return s;
-    if (radon_status s = cuda_status(launch_band_rows_dev(Bd, b->n_bands, b->smem_rows, stream),
+    if (radon_status s = cuda_status(launch_band_rows_dev(Bd, b->n_bands, b->ntaps, b->smem_rows, stream),
                                      "adjoint interpolation (bands)"))
         return s;
     if (radon_status s = cuda_status(launch_colconv_dev(K, b->n_kb, b->smem_cols, 1, stream), "adjoint convolution"))
         return s;
     if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
         return s;
-    return cuda_status(launch_gather_samples(b->pieces, b->smap, b->nsblocks, f, 0, 0, 0, stream), "adjoint gridding");
+    return cuda_status(launch_gather_samples(b->pieces, b->smap, b->nsblocks, f, 0, 0, 0, b->ntaps, stream), "adjoint gridding");
 }
 
 // ---------------------------------------------------------------------------

@@ -225,6 +225,28 @@ static double b3_error() {
     return e;
 }
 
+// The quintic weights against the truncated-power definition of B5.
+static double b5_error() {
+    auto B5 = [](double x) {
+        const double a = std::fabs(x);
+        auto tp = [](double u) { return u > 0 ? u * u * u * u * u : 0.0; };
+        return (tp(3 - a) - 6 * tp(2 - a) + 15 * tp(1 - a)) / 120.0;
+    };
+    double e = 0;
+    for (int i = 0; i <= 1000; ++i) {
+        const float f = i / 1000.0f;
+        float w[6];
+        b5_weights(f, w);
+        double sum = 0;
+        for (int d = 0; d < 6; ++d) {
+            e = std::max(e, std::fabs(w[d] - B5(f + 2 - d)));
+            sum += w[d];
+        }
+        e = std::max(e, std::fabs(sum - 1.0));
+    }
+    return e;
+}
+
 int main() {
     std::mt19937 rng(1604);
     double e = 0;
@@ -242,6 +264,7 @@ int main() {
     for (int P : {64, 768}) e = std::max(e, irfft_error(P, P / 5, rng));
     std::printf("irfft_rel_l2 %.3e\n", e);
     std::printf("b3_weights %.3e\n", b3_error());
+    std::printf("b5_weights %.3e\n", b5_error());
     e = 0;
     int bad_freq = 0;
     for (int n : {2, 3, 4, 5, 6, 8, 9, 10, 12, 16, 18, 20, 24, 32, 36, 40, 48, 64, 72, 80, 96, 128, 144, 160, 192,

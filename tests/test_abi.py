@@ -47,10 +47,11 @@ def test_host_side_argument_checks(lib):
     d = _lib.RadonDesc()
     assert L.radon_desc_init(ctypes.byref(d), 256, 64, 256, 64, 0.004, 0.025, 0.2, 0.7) == 0
     # the binding's struct matches the header's layout up to the last field
-    assert (d.device, d.rows_per_band, d.n_qsplit, d.n_tsplit) == (-1, 3, 1, 2)
+    assert (d.device, d.rows_per_band, d.n_qsplit, d.n_tsplit, d.spline_order) == (-1, 3, 1, 2, 3)
     h = ctypes.c_void_p()
     for field, value in [("Nt", 1), ("dt", 0.0), ("qmin", -1.0), ("omega_c", 0.6), ("sigma", 0.0),
-                         ("n_qsplit", 0), ("n_tsplit", 9), ("rows_per_band", 7), ("rows_per_band", -1)]:
+                         ("n_qsplit", 0), ("n_tsplit", 9), ("rows_per_band", 7), ("rows_per_band", -1),
+                         ("spline_order", 4), ("spline_order", 1), ("spline_order", 0)]:
         bad = _lib.RadonDesc.from_buffer_copy(d)
         setattr(bad, field, value)
         assert L.radon_plan_create_ex(ctypes.byref(h), ctypes.byref(bad)) == 1, field

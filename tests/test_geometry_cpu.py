@@ -28,6 +28,11 @@ CASES = [
          omega_c=0.35, tsplits=(0.25, 0.5)),
     dict(Nt=1024, Nx=1024, Ntau=1024, Nq=1024, dt=0.002, dx=2.0 / 1023, qmin=0.1, qmax=0.7,
          tsplits=(0.25, 0.5)),
+    # quintic B-splines: three guard cells per side
+    dict(Nt=256, Nx=96, Ntau=200, Nq=64, dt=0.004, dx=0.02, qmin=0.2, qmax=0.7, sigma=1.1,
+         omega_c=0.4, tsplits=(0.25, 0.5), order=5),
+    dict(Nt=2048, Nx=2048, Ntau=2048, Nq=2048, dt=2.0 / 2047, dx=2.0 / 2047, qmin=0.2, qmax=0.7,
+         sigma=1.1, omega_c=0.4, tsplits=(0.25, 0.5), order=5),
 ]
 
 
@@ -46,6 +51,7 @@ def _lib_geometry(c, x=None, q=None):
     for i, v in enumerate(ts):
         d.tsplit[i] = v
     d.n_qsplit = c.get("n_qsplit", 1)
+    d.spline_order = c.get("order", 3)
     n = ctypes.c_int()
     infos = (_lib.RadonPieceInfo * 64)()
     arr = lambda v: None if v is None else (ctypes.c_double * len(v))(*v)
@@ -74,7 +80,7 @@ def _check(c, x=None, q=None):
     desc = Desc(c["Nt"], c["Nx"], c["Ntau"], c["Nq"], c["dt"], c["dx"], c["qmin"], c["qmax"],
                 tau0=c.get("tau0", 0.0), dtau=c.get("dtau", 0.0), sigma=c.get("sigma", 2.0),
                 omega_c=c.get("omega_c", 0.25), tsplits=c.get("tsplits", ()),
-                n_qsplit=c.get("n_qsplit", 1), x=x, q_values=q)
+                n_qsplit=c.get("n_qsplit", 1), x=x, q_values=q, order=c.get("order", 3))
     parts = oracle_plan(desc)
     lib = {(p["jt_lo"], p["l_lo"]): p for p in _lib_geometry(c, x, q)}
     assert len(lib) == len(parts)

@@ -48,6 +48,12 @@ def test_b3_weights(results):
     assert results["b3_weights"] < 1e-6
 
 
+def test_b5_weights(results):
+    """Quintic tap weights against the truncated-power definition of B5 and
+    their partition of unity."""
+    assert results["b5_weights"] < 1e-6
+
+
 def test_shared_memory_swizzle_is_a_permutation(results):
     assert results["swizzle_violations"] == 0
     # 2^a <= 4096, 3 2^a <= 6144, 5 2^a <= 5120 and 9 2^a <= 2304: 13 + 12 + 11 + 9 lengths
