@@ -265,42 +265,69 @@ def size_sweep(dev, sizes=(512, 1024, 4096), steps: int = 20) -> dict:
     import paper_1604_07651_gb300 as hr
     paper = {512: 1.0 / (1.9e-3 + 2.3e-3), 1024: 1.0 / (7.4e-3 + 8.7e-3), 2048: 1.0 / (2.9e-2 + 3.2e-2),
              4096: 1.0 / (1.1e-1 + 1.3e-1)}
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     out = {}
     for N in sizes:
         geo, f_np = synth.sweep_gather(N)
         plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
                        rows_per_band=0, device=dev.index)
         f = torch.tensor(f_np, dtype=torch.float32, device=dev)
-        g = torch.empty((geo.Nq, geo.Ntau), dtype=torch.float32, device=dev)
-        fa = torch.empty_like(f)
-        for _ in range(3):
-            plan.forward(f, out=g)
-            plan.adjoint(g, out=fa)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            plan.forward(f, out=g)
-            plan.adjoint(g, out=fa)
-        graph.replay()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for a, b in ev:
-            flush.fill_(1.0)
-            a.record()
-            graph.replay()
-            b.record()
-        torch.cuda.synchronize()
-        ms = sorted(a.elapsed_time(b) for a, b in ev)
-        med = ms[len(ms) // 2]
-        out[str(N)] = {"pairs_per_s": 1e3 / med, "ms_per_pair_median": med, "ms_p10": ms[len(ms) // 10],
-                       "ms_p90": ms[(9 * len(ms)) // 10], "paper_gtx970_pairs_per_s": paper.get(N),
-                       "lattices": [(p["Ntheta"], p["Nrho"], p["Ptheta"], p["Prho"]) for p in plan.pieces()]}
+        out[str(N)] = dict(time_pair_graph(plan, f, dev, steps), paper_gtx970_pairs_per_s=paper.get(N))
         plan.close()
-        del f, g, fa, graph
+        del f
     return {"workload": "sweep gathers N x N (T = 2 s, X = 2 km, 32 Ricker events 20-40 Hz + 5 % noise), "
                         "default method, fwd + adj as one CUDA graph, L2 flushed per step",
             "sizes": out}
+
+
+def time_pair_graph(plan, f, dev, steps: int = 20) -> dict:
+    """Median fwd + adj pair time of a plan, the pair replayed as one CUDA
+    graph, L2 flushed (256 MiB write) before every step, input resident."""
+    import torch
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    d = plan.desc
+    g = torch.empty((d.Nq, d.Ntau), dtype=torch.float32, device=dev)
+    fa = torch.empty_like(f)
+    for _ in range(3):
+        plan.forward(f, out=g)
+        plan.adjoint(g, out=fa)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.forward(f, out=g)
+        plan.adjoint(g, out=fa)
+    graph.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.fill_(1.0)
+        a.record()
+        graph.replay()
+        b.record()
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    med = ms[len(ms) // 2]
+    return {"pairs_per_s": 1e3 / med, "ms_per_pair_median": med, "ms_p10": ms[len(ms) // 10],
+            "ms_p90": ms[(9 * len(ms)) // 10],
+            "lattices": [(p["Ntheta"], p["Nrho"], p["Ptheta"], p["Prho"]) for p in plan.pieces()]}
+
+
+def quintic_option(dev, geo, f, points) -> dict:
+    """The quintic B-spline option on the main workload (default method
+    parameters, six taps per axis): pairs/s as in the size sweep, and its
+    accuracy against the FP64 direct sum on the main run's sampled points
+    (forward of the gather; adjoint of the cubic path's image)."""
+    import torch
+    import paper_1604_07651_gb300 as hr
+    ii, li, ref, jj, kk, gsm, refa = points
+    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+                   rows_per_band=0, spline_order=5, device=dev.index)
+    out = {"workload": "the main workload with spline_order = 5", **time_pair_graph(plan, f, dev)}
+    gq = plan.forward(f).cpu().numpy()
+    out["fwd_rel_l2_vs_direct_sum_4096_points"] = float(np.linalg.norm(gq[li, ii] - ref) / np.linalg.norm(ref))
+    fq = plan.adjoint(torch.tensor(gsm, dtype=torch.float32, device=dev)).cpu().numpy()
+    out["adj_rel_l2_vs_direct_sum_4096_points"] = float(np.linalg.norm(fq[kk, jj] - refa) / np.linalg.norm(refa))
+    plan.close()
+    return out
 
 
 def batched_uneven(dev, n: int, rank: int = 0, world: int = 1) -> dict:
@@ -565,6 +592,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch every timed step eagerly")
     ap.add_argument("--no-sweep", action="store_true", help="skip the N = 512, 1024, 4096 sweep")
+    ap.add_argument("--no-quintic", action="store_true", help="skip the quintic B-spline option's line")
     ap.add_argument("--rows-per-band", type=int, default=0,
                     help="rows per band of the row-FFT kernels; 0 times them at plan creation")
     ap.add_argument("--batch-gathers", type=int, default=256)
@@ -798,6 +826,8 @@ def main():
         fanp = fa.cpu().numpy()
         acc["adj_rel_l2_vs_direct_sum_4096_points"] = float(np.linalg.norm(fanp[kk, jj] - refa) / np.linalg.norm(refa))
         result["accuracy"] = acc
+        if not args.no_quintic:
+            result["quintic"] = quintic_option(dev, geo, f, (ii, li, ref, jj, kk, gsm, refa))
 
         if not args.no_direct:
             # the plain form: direct summation over hyperbolas on this GPU

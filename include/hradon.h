@@ -205,6 +205,35 @@ radon_status radon_geometry(const radon_desc* d, int* npieces, radon_piece_info*
 radon_status radon_geometry_grid(const radon_desc* d, const double* x, const double* q, int* npieces,
                                  radon_piece_info* infos, int max_infos);
 
+/*
+ * Inspection of one sub-problem (0 <= piece < num_pieces), for tests and
+ * diagnostics. Both calls synchronise the device and copy to host memory.
+ *
+ * radon_plan_piece_lattice: the lattice [Ntheta][Nrho] (row-major floats) as
+ * the last radon_fwd or radon_adj on the plan left it: after radon_fwd the
+ * convolved lattice of Eq. (16)-(17), Q = IFFT(FFT(G) K) restricted to the
+ * lattice, which the output interpolation reads; after radon_adj the
+ * lattice of the transposed convolution (conj K) of the interpolation's
+ * transpose, which the adjoint gridding reads. (radon_fwd_noalloc works in
+ * the caller's area and leaves the plan's lattice as it was.) `count` is the
+ * room of `out` in floats; less than Ntheta * Nrho is RADON_ERR_INVALID_ARG.
+ *
+ * radon_plan_piece_samples: the lattice position and weight of every gather
+ * sample of the piece's time range, [Nx][jt_hi - jt_lo + 1] entries (trace
+ * major): theta[e] and rho[e] in cells (theta index (phi - theta0) / dtheta
+ * and rho index (eta - rho0) / drho of Eq. (10)), weight[e] the gridding
+ * weight of Eq. (14)-(15) without the sample value (window, 2 a^2 tb e^-eta,
+ * quadrature weights, 1 / (dtheta drho)). A weight of 0 marks a sample the
+ * piece does not grid (muted, or outside the piece's window); its positions
+ * are then undefined. Computed in FP64 at plan creation, stored as first
+ * tap and FP32 fraction (positions to about 6e-8 cells). Any of the three
+ * outputs may be NULL; `count` less than the number of entries is
+ * RADON_ERR_INVALID_ARG.
+ */
+radon_status radon_plan_piece_lattice(radon_plan p, int piece, float* out, size_t count);
+radon_status radon_plan_piece_samples(radon_plan p, int piece, double* theta, double* rho, float* weight,
+                                      size_t count);
+
 /* The descriptor the plan was built from (defaults resolved). */
 radon_status radon_plan_desc(radon_plan p, radon_desc* d);
 

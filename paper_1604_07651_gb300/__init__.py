@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes
 from typing import Sequence
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -133,6 +134,28 @@ class Plan:
             _lib.check(lib.radon_plan_piece_info(self._handle, p, ctypes.byref(info)))
             out.append({name: getattr(info, name) for name, _ in RadonPieceInfo._fields_})
         return out
+
+    def piece_lattice(self, piece: int) -> np.ndarray:
+        """Lattice [Ntheta][Nrho] of sub-problem `piece` as the last forward
+        (convolved lattice) or adjoint (lattice the adjoint gridding reads)
+        left it; synchronises the device (``radon_plan_piece_lattice``)."""
+        info = self.pieces()[piece]
+        out = np.empty((info["Ntheta"], info["Nrho"]), np.float32)
+        _lib.check(_lib.load().radon_plan_piece_lattice(self._handle, piece, out.ctypes.data, out.size))
+        return out
+
+    def piece_samples(self, piece: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """Lattice positions (theta, rho, in cells) and gridding weights of the
+        gather samples of sub-problem `piece`, each [Nx][jt_hi - jt_lo + 1];
+        weight 0 marks a sample the piece does not grid
+        (``radon_plan_piece_samples``)."""
+        info = self.pieces()[piece]
+        shape = (self.desc.Nx, info["jt_hi"] - info["jt_lo"] + 1)
+        th, rh = np.empty(shape), np.empty(shape)
+        w = np.empty(shape, np.float32)
+        _lib.check(_lib.load().radon_plan_piece_samples(self._handle, piece, th.ctypes.data, rh.ctypes.data,
+                                                        w.ctypes.data, w.size))
+        return th, rh, w
 
     def device_bytes(self) -> int:
         v = ctypes.c_size_t()

@@ -55,6 +55,8 @@ SIGNATURES = {
                                      ctypes.POINTER(_c_double), ctypes.POINTER(_c_int),
                                      ctypes.POINTER(RadonPieceInfo), _c_int]),
     "radon_plan_device_bytes": (_c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "radon_plan_piece_lattice": (_c_int, [_vp, _c_int, _vp, ctypes.c_size_t]),
+    "radon_plan_piece_samples": (_c_int, [_vp, _c_int, _vp, _vp, _vp, ctypes.c_size_t]),
     "radon_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(RadonDesc)]),
     "radon_batch_create_grid": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(RadonDesc),
                                          ctypes.POINTER(ctypes.POINTER(_c_double)),

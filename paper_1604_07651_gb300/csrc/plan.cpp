@@ -1444,6 +1444,43 @@ extern "C" radon_status radon_plan_piece_info(radon_plan p, int piece, radon_pie
     return RADON_OK;
 }
 
+extern "C" radon_status radon_plan_piece_lattice(radon_plan p, int piece, float* out, size_t count) {
+    if (!p || !out) return fail(RADON_ERR_INVALID_ARG, "NULL argument");
+    if (piece < 0 || piece >= (int)p->pieces.size()) return fail(RADON_ERR_INVALID_ARG, "piece out of range");
+    const PieceDev& P = p->pieces[piece].dev;
+    const size_t n = (size_t)P.Ntheta * P.Nrho;
+    if (count < n)
+        return fail(RADON_ERR_INVALID_ARG,
+                    "out holds " + std::to_string(count) + " floats, the lattice has " + std::to_string(n));
+    DeviceGuard guard(p->device);
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(out, P.lat, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(RADON_ERR_CUDA, std::string("lattice copy failed: ") + cudaGetErrorString(cudaGetLastError()));
+    return RADON_OK;
+}
+
+extern "C" radon_status radon_plan_piece_samples(radon_plan p, int piece, double* theta, double* rho, float* weight,
+                                                 size_t count) {
+    if (!p) return fail(RADON_ERR_INVALID_ARG, "plan is NULL");
+    if (piece < 0 || piece >= (int)p->pieces.size()) return fail(RADON_ERR_INVALID_ARG, "piece out of range");
+    const PieceDev& P = p->pieces[piece].dev;
+    const size_t n = (size_t)P.nj * P.Nx;
+    if (count < n)
+        return fail(RADON_ERR_INVALID_ARG,
+                    "the outputs hold " + std::to_string(count) + " entries, the piece has " + std::to_string(n));
+    std::vector<SampleEnt> tab(n);
+    DeviceGuard guard(p->device);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(tab.data(), P.stab, n * sizeof(SampleEnt), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(RADON_ERR_CUDA, std::string("table copy failed: ") + cudaGetErrorString(cudaGetLastError()));
+    const int back = P.ntaps / 2 - 1;       // first tap = floor(position) - back
+    for (size_t e = 0; e < n; ++e) {
+        if (theta) theta[e] = (double)((tab[e].mn >> 16) + back) + (double)tab[e].ft;
+        if (rho) rho[e] = (double)((tab[e].mn & 0xffff) + back) + (double)tab[e].fr;
+        if (weight) weight[e] = tab[e].w;
+    }
+    return RADON_OK;
+}
+
 extern "C" radon_status radon_geometry(const radon_desc* din, int* npieces, radon_piece_info* infos,
                                        int max_infos) {
     return radon_geometry_grid(din, nullptr, nullptr, npieces, infos, max_infos);
