@@ -198,8 +198,99 @@ __device__ __forceinline__ void rows_last_lat(const cf* X, float* lat, int Nr, i
     case 3: CALL(3); break;   \
     default: CALL(2); break;
 
+// The same passes for the row lengths M = R0 * 256 with radices R0, 16, 16
+// (the plans of the 2048^2 and 4096^2 workloads), every length, stride and
+// count a compile-time constant (the index arithmetic folds to shifts and
+// constant divisions). Same arithmetic as the general passes.
+template <int R, int S, int M, bool INV>
+__device__ __forceinline__ void rows_pass_c(cf* X, int nrows, const cf* __restrict__ T) {
+    constexpr int nb = M / R;
+    const int tot = nb * nrows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int row = idx / nb;
+        const int b = idx - row * nb;
+        const int q = b / S, m = b - q * S;
+        const int base = q * S * R + m;
+        cf* Z = X + row * row_stride(M);
+        cf x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = Z[sw(base + r * S)];
+        if (INV) row_inv<R>(x, T, S, m);
+        else row_fwd<R>(x, T, S, m);
+#pragma unroll
+        for (int r = 0; r < R; ++r) Z[sw(base + r * S)] = x[r];
+    }
+}
+template <int R0>
+__device__ __forceinline__ void rows_first_lat_c(cf* X, const float* __restrict__ lat, int Nr, int nrows,
+                                                 const cf* __restrict__ T) {
+    constexpr int S = 256, M = R0 * 256;
+    const int tot = S * nrows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int row = idx / S, m = idx % S;
+        const float* src = lat + (size_t)row * Nr;
+        cf x[R0];
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+            const int n2 = 2 * (m + r * S);
+            x[r].x = n2 < Nr ? __ldg(src + n2) : 0.f;
+            x[r].y = n2 + 1 < Nr ? __ldg(src + n2 + 1) : 0.f;
+        }
+        row_fwd<R0>(x, T, S, m);
+        cf* Z = X + row * row_stride(M);
+#pragma unroll
+        for (int r = 0; r < R0; ++r) Z[sw(m + r * S)] = x[r];
+    }
+}
+template <int R0>
+__device__ __forceinline__ void rows_last_lat_c(const cf* X, float* lat, int Nr, int nrows, const cf* __restrict__ T) {
+    constexpr int S = 256, M = R0 * 256;
+    const int tot = S * nrows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int row = idx / S, m = idx % S;
+        const cf* Z = X + row * row_stride(M);
+        cf x[R0];
+#pragma unroll
+        for (int r = 0; r < R0; ++r) x[r] = Z[sw(m + r * S)];
+        row_inv<R0>(x, T, S, m);
+        float* dst = lat + (size_t)row * Nr;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+            const int n2 = 2 * (m + r * S);
+            if (n2 < Nr) dst[n2] = x[r].x;
+            if (n2 + 1 < Nr) dst[n2 + 1] = x[r].y;
+        }
+    }
+}
+// R0 of a plan of length R0 * 256 with radices R0, 16, 16, else 0.
+__device__ __forceinline__ int plan_x256(const FftPlan& fp) {
+    return (fp.nst == 3 && fp.st[0] == 256 && fp.rad[1] == 16 && fp.rad[2] == 16) ? fp.rad[0] : 0;
+}
+#define HR_X256_CASES(CALL) \
+    case 4: CALL(4); break;  \
+    case 6: CALL(6); break;  \
+    case 8: CALL(8); break;  \
+    case 9: CALL(9); break;  \
+    case 10: CALL(10); break; \
+    case 12: CALL(12); break;
+
 // Forward passes p0 .. s-1 in shared memory (p0 = 1 after rows_first_lat).
 __device__ __forceinline__ void rows_fwd_passes(cf* X, int M, int nrows, const FftPlan& fp, const cf* T, int p0) {
+    switch (plan_x256(fp)) {
+#define HR_RX(R0)                                                                    \
+    if (p0 == 0) {                                                                   \
+        rows_pass_c<R0, 256, R0 * 256, false>(X, nrows, T);                          \
+        __syncthreads();                                                             \
+    }                                                                                \
+    rows_pass_c<16, 16, R0 * 256, false>(X, nrows, T + fp.tw[1]);                    \
+    __syncthreads();                                                                 \
+    rows_pass_c<16, 1, R0 * 256, false>(X, nrows, T);                                \
+    __syncthreads();                                                                 \
+    return;
+        HR_X256_CASES(HR_RX)
+#undef HR_RX
+        default: break;
+    }
     for (int p = p0; p < fp.nst; ++p) {
 #define HR_RF(RR) rows_pass<RR, false>(X, M, nrows, fp.st[p], T + fp.tw[p])
         switch (fp.rad[p]) { HR_RADIX_CASES(HR_RF) }
@@ -214,19 +305,20 @@ __device__ __forceinline__ void rows_post(const PieceDev& P, const cf* Z0, int m
     cf* __restrict__ spec = P.spec;
     const int M = P.Prho / 2;
     const int nk = P.k2max + 1;
-    const int per_kb = nrows * P.CB;
+    const int per_kb = nrows * 2;                 // (row, c) of a column block (CB = 2), c fastest
     const int total = P.nkb * per_kb;
+    const float inv_per_kb = 1.0f / (float)per_kb;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int kb = idx / per_kb;
+        const int kb = (int)(((float)idx + 0.5f) * inv_per_kb);   // exact for idx < 2^22
         const int rem = idx - kb * per_kb;
-        const int m = rem / P.CB;
-        const int c = rem - m * P.CB;
-        const int k = kb * P.CB + c;
+        const int m = rem >> 1;
+        const int c = rem & 1;
+        const int k = kb * 2 + c;
         cf X = {0.f, 0.f};
         if (k < nk)
             X = r2c_post_at(Z0 + m * row_stride(M), sw(__ldg(P.rpos + k)), sw(__ldg(P.rpos + (k == 0 ? 0 : M - k))), k,
                             P.twP);
-        spec[((size_t)kb * P.Ntheta + (mb + m)) * P.CB + c] = X;
+        spec[((size_t)kb * P.Ntheta + (mb + m)) * 2 + c] = X;
     }
 }
 
@@ -240,13 +332,14 @@ __device__ __forceinline__ void rows_pre(const PieceDev& P, cf* X, int mb, int n
     const int per_kb = nrows * 2;                 // (row, c) of a column block, c fastest
     const int total = (half / 2 + 1) * per_kb;    // k = 2 kb + c <= half
     constexpr int U = 4;                          // pairs per thread whose spectrum loads go out together
+    const float inv_per_kb = 1.0f / (float)per_kb;
     for (int i0 = threadIdx.x; i0 < total; i0 += U * blockDim.x) {
         cf a[U], b[U];
         int kk[U], mm[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int idx = i0 + u * (int)blockDim.x;
-            const int kb = idx / per_kb;
+            const int kb = (int)(((float)idx + 0.5f) * inv_per_kb);   // exact for idx < 2^22
             const int rem = idx - kb * per_kb;
             const int m = rem >> 1;
             const int k = 2 * kb + (rem & 1);
@@ -572,9 +665,15 @@ __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src
     const int M = P.Prho / 2;
     cf* X = reinterpret_cast<cf*>(smem_f);
     const FftPlan& fp = P.fftM;
-#define HR_RL(RR) rows_first_lat<RR>(X, P.lat + (size_t)mb * P.Nrho, P.Nrho, M, nrows, fp.st[0], P.twM)
-    switch (fp.rad[0]) { HR_RADIX_CASES(HR_RL) }
+    switch (plan_x256(fp)) {
+#define HR_RL(R0) rows_first_lat_c<R0>(X, P.lat + (size_t)mb * P.Nrho, P.Nrho, nrows, P.twM); break;
+        HR_X256_CASES(HR_RL)
 #undef HR_RL
+        default:
+#define HR_RL(RR) rows_first_lat<RR>(X, P.lat + (size_t)mb * P.Nrho, P.Nrho, M, nrows, fp.st[0], P.twM)
+            switch (fp.rad[0]) { HR_RADIX_CASES(HR_RL) }
+#undef HR_RL
+    }
     __syncthreads();
     rows_fwd_passes(X, M, nrows, fp, P.twM, 1);
     rows_post(P, X, mb, nrows);
@@ -883,6 +982,57 @@ __device__ __forceinline__ void c1_kernel(cf* A, const FftPlan& fp, const cf* K,
     }
 }
 
+// The pair for Ptheta = R0 * 256 (radices R0, 16, 16: the plans of the
+// 2048^2 workload) with every stride and count a compile-time constant: one
+// butterfly per thread and pass (256 threads per column), the stride-1
+// pass's first frequency b / 16 + R0 (b mod 16) without the general digit
+// loop. Same arithmetic as the general passes.
+template <int R0>
+__device__ __forceinline__ void c1_x256(cf* A, cf* col, int Nth, const cf* Tg, const cf* Ts, const cf* K, int k1n,
+                                        int adjoint, int t, int c) {
+    constexpr int n = R0 * 256, nb = R0 * 16;
+    c1_first<R0>(A, col, Nth, 256, Tg, t, 256, c);
+    cp_async_wait_all();
+    __syncthreads();
+    const cf* T1 = Ts + 256 * (R0 - 1);
+    const int q = t >> 4, m = t & 15;
+    if (t < nb) {
+        cf x[16];
+        c1_ld<16>(A, q * 256 + m, 16, c, x);
+        c1_fwd<16>(x, T1, 16, m);
+        c1_st<16>(A, q * 256 + m, 16, c, x);
+    }
+    __syncthreads();
+    if (t < nb) {
+        const int fb = q + R0 * m;
+        cf x[16];
+        c1_ld<16>(A, t * 16, 1, c, x);
+        dft_small<16>(x, -1);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int f = fb + nb * k;
+            const int kk = f <= n - f ? f : n - f;
+            if (kk < k1n) {
+                const cf kv = K[2 * kk + c];
+                x[k] = adjoint ? cmulc(x[k], kv) : cmul(x[k], kv);
+            } else {
+                x[k] = cf{0.f, 0.f};
+            }
+        }
+        dft_small<16>(x, +1);
+        c1_st<16>(A, t * 16, 1, c, x);
+    }
+    __syncthreads();
+    if (t < nb) {
+        cf x[16];
+        c1_ld<16>(A, q * 256 + m, 16, c, x);
+        c1_inv<16>(x, T1, 16, m);
+        c1_st<16>(A, q * 256 + m, 16, c, x);
+    }
+    __syncthreads();
+    c1_last<R0>(A, col, Nth, 256, Ts, t, 256, c);
+}
+
 // Shared memory of the column kernel: the column block [Ptheta] (16-byte
 // elements), its slice of K [k1max + 1] (16 bytes each), the twiddle tables
 // (twlen complex, a multiple of 2).
@@ -924,6 +1074,15 @@ __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src 
         __syncthreads();
         for (int m = threadIdx.x; m < Nth; m += blockDim.x) reinterpret_cast<float4*>(col)[m] = A4[swc(m)];
         return;
+    }
+    if (s == 3 && S0 == 256 && fp.rad[1] == 16 && fp.rad[2] == 16 && blockDim.x == 512) {
+        switch (R0) {
+            case 8: c1_x256<8>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
+            case 9: c1_x256<9>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
+            case 10: c1_x256<10>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
+            case 12: c1_x256<12>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
+            default: break;
+        }
     }
 #define HR_FIRST(RR) c1_first<RR>(A, col, Nth, S0, P.twT, t, nt, c)
     switch (R0) { HR_RADIX_CASES(HR_FIRST) }
@@ -968,6 +1127,18 @@ __global__ void __launch_bounds__(512, 2) k_rows_c2r(const __grid_constant__ Src
     const FftPlan& fp = P.fftM;
     rows_pre(P, X, mb, nrows);
     __syncthreads();
+    switch (plan_x256(fp)) {
+#define HR_CX(R0)                                                                    \
+    rows_pass_c<16, 1, R0 * 256, true>(X, nrows, P.twM);                             \
+    __syncthreads();                                                                 \
+    rows_pass_c<16, 16, R0 * 256, true>(X, nrows, P.twM + fp.tw[1]);                 \
+    __syncthreads();                                                                 \
+    rows_last_lat_c<R0>(X, P.lat + (size_t)mb * P.Nrho, P.Nrho, nrows, P.twM);       \
+    return;
+        HR_X256_CASES(HR_CX)
+#undef HR_CX
+        default: break;
+    }
     for (int p = fp.nst - 1; p >= 1; --p) {
 #define HR_RI(RR) rows_pass<RR, true>(X, M, nrows, fp.st[p], P.twM + fp.tw[p])
         switch (fp.rad[p]) { HR_RADIX_CASES(HR_RI) }
