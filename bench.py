@@ -134,7 +134,7 @@ STAGE_KERNEL = {"grid_fwd": "k_grid_tiles", "rows_r2c_fwd": "k_rows_r2c", "colco
                 "rows_c2r_fwd": "k_rows_c2r", "interp_fwd": "k_interp_columns",
                 "bandrows_rowfft_adj": "k_band_rows", "colconv_adj": "k_colconv",
                 "rows_c2r_adj": "k_rows_c2r", "gather_adj": "k_gather_samples",
-                "profiles_adj": "k_col_profiles"}
+                "profiles_adj": "k_col_profiles_cols"}
 
 # DRAM bytes (read + write) per launch recorded from one ncu capture of the
 # benchmark workload, valid only for the kernel source they were taken on:
@@ -148,7 +148,7 @@ MEASURED_TRAFFIC = {
     "k_colconv": ("3386401af41f00ec", 48.37e6),
     "k_rows_c2r": ("3386401af41f00ec", 28.91e6),
     "k_interp_columns": ("3386401af41f00ec", 102.15e6),
-    "k_col_profiles": ("3386401af41f00ec", 108.89e6),
+    "k_col_profiles_cols": ("3386401af41f00ec", 108.89e6),
     "k_band_rows": ("3386401af41f00ec", 46.22e6),
     "k_gather_samples": ("3386401af41f00ec", 106.87e6),
 }

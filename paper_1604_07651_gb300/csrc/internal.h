@@ -130,7 +130,6 @@ constexpr int kMaxBandRows = 6;
 // cudaErrorInvalidValue.
 int launch_grid_tiles(const PieceDev* P, int n, const float* f, void* stream);
 int launch_rows_r2c(const PieceDev* P, int n, void* stream);
-int launch_col_profiles(const PieceDev* P, int n, const float* g, void* stream);
 int launch_band_rows(const PieceDev* P, int n, void* stream);
 int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream);
 int launch_rows_c2r(const PieceDev* P, int n, void* stream);
@@ -138,7 +137,6 @@ int launch_rows_c2r(const PieceDev* P, int n, void* stream);
 // `smem` the largest dynamic shared memory any piece of the launch needs.
 int launch_grid_tiles_dev(const DevBatch& S, int nblocks, int ntaps, const void* f, int in_type, void* stream);
 int launch_rows_r2c_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
-int launch_col_profiles_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, const float* g, void* stream);
 int launch_band_rows_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, void* stream);
 int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream);
 int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
@@ -150,6 +148,10 @@ int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
 // np_max * nrho_max floats.
 int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,
                           int ntau_all, int np_all, int ntaps, float* g, void* stream);
+// Adjoint column profiles of every time piece of a column at once, one CTA
+// per output column (cmap / np_all / shared memory as the interpolation's).
+int launch_col_profiles_cols(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,
+                             int ntau_all, int np_all, int ntaps, const float* g, void* stream);
 // Adjoint gather: one CTA per kSampleBlock samples of one gather;
 // smap[b] = (first piece, number of pieces, first sample, 0), or, when
 // np_all > 0 (one gather of Nt_all x Nx_all samples in np_all pieces),
@@ -158,7 +160,6 @@ constexpr int kSampleBlock = 256;
 int launch_gather_samples(const PieceDev* pieces, const int4* smap, int nblocks, float* f, int np_all, int Nt_all,
                           int Nx_all, int ntaps, void* stream);
 size_t rows_smem_bytes(const PieceDev& P);
-size_t profile_smem_bytes(const PieceDev& P);
 int launch_sample_table(const TableArgs& A, const double* cj, const double* wk, const int* jfirst,
                         SampleEnt* out);
 int launch_radon_table(const TableArgs& A, const double* qb2, RadonEnt* out);

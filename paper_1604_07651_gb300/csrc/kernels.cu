@@ -12,7 +12,7 @@
 //   k_interp_columns   cubic B-spline interpolation at (phi, eta) = P2 S(tau^2,
 //                      q^2) (Eq. (17)), summed over the time pieces.
 // Adjoint (Eq. (16), Section 3): the same kernels with the roles exchanged:
-//   k_col_profiles -> k_band_rows -> k_colconv (conjugate kernel) -> k_rows_c2r ->
+//   k_col_profiles_cols -> k_band_rows -> k_colconv (conjugate kernel) -> k_rows_c2r ->
 //   k_gather_samples.
 //
 // Lattice positions do not depend on the data: the plan computes them once in
@@ -499,9 +499,11 @@ __device__ __forceinline__ void slide_cols_left(int* t, float (&acc)[NT * NT]) {
 // Split tiles: the unit's partial tile (value(i) of cell i, row-major over
 // the kTileRows x kTileCols cells) goes to its slot; the unit that finds it
 // is the tile's last to arrive (the others' slots are then complete and
-// visible: each writer fences before it counts) sums every slot of the tile
-// in slot order into the lattice and clears the counter. The result does
-// not depend on which unit runs first.
+// visible) sums every slot of the tile in slot order into the lattice and
+// clears the counter. The result does not depend on which unit runs first.
+// Ordering: the block's slot stores, a barrier, then one thread's fence and
+// count (release, cumulative over the block through the barrier); on the
+// reading side that thread's fence after the count, a barrier, and L2 loads.
 template <class F>
 __device__ __forceinline__ void grid_merge_split(const PieceDev& P, int4 us, int m_lo, int n_lo, int nr, int nc,
                                                  F&& value) {
@@ -509,13 +511,16 @@ __device__ __forceinline__ void grid_merge_split(const PieceDev& P, int4 us, int
     constexpr int kCells = kTileRows * kTileCols;
     float* slot0 = P.slots + (size_t)us.x * kCells;
     for (int i = threadIdx.x; i < kCells; i += blockDim.x) slot0[(size_t)us.z * kCells + i] = value(i);
-    __threadfence();
     __syncthreads();
     int* counter = reinterpret_cast<int*>(P.lat + (size_t)P.Ntheta * P.Nrho) + us.w;
-    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1) == us.y - 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int last = atomicAdd(counter, 1) == us.y - 1;
+        if (last) __threadfence();
+        s_last = last;
+    }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     // each thread sums its kCells / kUnitChunks cells over the slots in slot
     // order, all its cells' loads of two slots in flight together
     constexpr int kPer = kCells / kUnitChunks;
@@ -683,112 +688,146 @@ __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src
 // along the two axes. Every output of a slowness column has the same theta
 // taps (the column's angle), so the transpose is a 1-D scatter along rho per
 // column followed by a 4-tap spread of the column profiles over theta:
-//   h_l[n]   = s_l sum_i g[l][i] B3(rho_il - rho_n)          (k_col_profiles)
+//   h_l[n]   = s_l sum_i g[l][i] B3(rho_il - rho_n)          (k_col_profiles_cols)
 //   G'[m][n] = sum_l B3(theta_l - theta_m) h_l[n]            (k_band_rows)
 // The profiles are summed in fixed point (order-independent), the spread is a
 // plain per-thread sum over the band's columns in a fixed order: the adjoint
 // interpolation has no floating-point atomics and is deterministic.
 
-// One CTA per output column of the piece: P.prof[lc][0..Nrho) (pitch hpitch) of
-// the column's outputs g[l_lo + lc][*], scaled by the column's output scale.
-// Fixed point with the bound max|g| of the column times the column's
-// plan-time weight bound; a non-finite g makes the profile NaN.
-template <class Src, int NT>
-__global__ void __launch_bounds__(256) k_col_profiles(const __grid_constant__ Src B, const float* __restrict__ g) {
+// The profiles P.prof[lc][0..Nrho) (pitch hpitch) of every time piece of
+// one output column, from the column's outputs g[l][*] scaled by each
+// piece's output scale: one CTA per column (cmap[b] = (first piece, number
+// of pieces, column l), or, when np_all > 0, column b of pieces[0..np_all)
+// with ntau_all outputs), so that the column's outputs are read once for the
+// scale and once for all its pieces ([np][nrho_max] in shared memory). Fixed
+// point with the bound max|g| of the column times each piece's plan-time
+// weight bound for the column; a non-finite g makes the profiles NaN.
+template <int NT>
+__global__ void __launch_bounds__(256) k_col_profiles_cols(const PieceDev* __restrict__ pieces,
+                                                           const int4* __restrict__ cmap, int nrho_max, int ntau_all,
+                                                           int np_all, const float* __restrict__ g) {
+    const int4 c = np_all > 0 ? make_int4(0, np_all, (int)blockIdx.x, 0) : __ldg(cmap + blockIdx.x);
+    const int l = c.z, np = c.y;
+    const int Ntau = np_all > 0 ? ntau_all : pieces[c.x].Ntau;
+    if (np > kMaxColPieces || (size_t)np * nrho_max * sizeof(int) > dyn_smem_bytes()) return;
     int* prof = reinterpret_cast<int*>(smem_f);
     __shared__ float red[8];
-    int lc;
-    const PieceDev& P = piece_of(B, lc);
-    if ((size_t)P.Nrho * sizeof(int) > dyn_smem_bytes()) return;
-    const int hp = P.hpitch;
-    const float* gl = g + P.g_off + (size_t)(P.l_lo + lc) * P.Ntau;
-    const int2* rt = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * P.Ntau);
-    float* hl = P.prof + (size_t)lc * hp;
-    for (int n = threadIdx.x; n < P.Nrho; n += blockDim.x) prof[n] = 0;
+    __shared__ const int2* s_rt[kMaxColPieces];
+    __shared__ float* s_hl[kMaxColPieces];
+    __shared__ float s_sc[kMaxColPieces];
+    __shared__ int s_sh[kMaxColPieces];
+    __shared__ int2 s_rg[kMaxColPieces];
+    __shared__ int s_nr[kMaxColPieces], s_hp[kMaxColPieces];
+    if ((int)threadIdx.x < np) {
+        const PieceDev& P = pieces[c.x + threadIdx.x];
+        const int lc = l - P.l_lo;
+        s_rt[threadIdx.x] = reinterpret_cast<const int2*>(P.rtab + (size_t)lc * Ntau);
+        s_hl[threadIdx.x] = P.prof + (size_t)lc * P.hpitch;
+        s_sc[threadIdx.x] = __ldg(P.colscale + lc);
+        s_sh[threadIdx.x] = __ldg(P.colsh + lc);
+        s_rg[threadIdx.x] = __ldg(P.rrange + lc);
+        s_nr[threadIdx.x] = P.Nrho;
+        s_hp[threadIdx.x] = P.hpitch;
+    }
+    for (int i = threadIdx.x; i < np * nrho_max; i += blockDim.x) prof[i] = 0;
+    const float* gl = g + (np_all > 0 ? 0 : pieces[c.x].g_off) + (size_t)l * Ntau;
     constexpr int Q = 8;                        // outputs per thread
     const int chunk = Q * (int)blockDim.x;
-    float m = 0.f;
-    for (int i0 = 0; i0 < P.Ntau; i0 += chunk) {
+    float mx = 0.f;
+    for (int i0 = 0; i0 < Ntau; i0 += chunk) {
         float v[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int i = i0 + q * (int)blockDim.x + threadIdx.x;
-            v[q] = i < P.Ntau ? __ldg(gl + i) : 0.f;
+            v[q] = i < Ntau ? __ldg(gl + i) : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const float a = fabsf(v[q]);
-            m = (a > m || a != a) ? a : m;
+            mx = (a > mx || a != a) ? a : mx;
         }
     }
-    const float vmax = block_max_abs(m, red);   // also orders the zeroing before the adds
+    const float vmax = block_max_abs(mx, red);   // also orders the zeroing and the column data before use
     if (!(vmax > 0.f && vmax <= 3.402823466e38f)) {
         const float fill = vmax == 0.f ? 0.f : __int_as_float(0x7fc00000);
-        for (int n = threadIdx.x; n < hp; n += blockDim.x) hl[n] = fill;
+        for (int p = 0; p < np; ++p)
+            for (int n = threadIdx.x; n < s_hp[p]; n += blockDim.x) s_hl[p][n] = fill;
         return;
     }
-    const Pow2Scale scl(__ldg(P.colsh + lc) - ilogbf(vmax));
-    const float sc = __ldg(P.colscale + lc);
-    // only the column's valid outputs (the max above still sees every output,
-    // so a non-finite value anywhere in the column poisons the profile)
-    const int2 rg = __ldg(P.rrange + lc);
+    const int ev = ilogbf(vmax);
+    int lo = Ntau, hi = -1;                     // outputs valid in some piece
+    for (int p = 0; p < np; ++p) {
+        lo = min(lo, s_rg[p].x);
+        hi = max(hi, s_rg[p].y);
+    }
     // every thread takes Q consecutive outputs: their first rho tap is
-    // nondecreasing, so their contributions collect in an NT-cell register
-    // window that slides one cell as the tap advances (the departing cell goes
-    // to the shared profile) and is flushed whole on a longer jump; dozens of
-    // outputs that share a cell at small intercept times cost one add
-    for (int i0 = rg.x & ~7; i0 <= rg.y; i0 += Q * (int)blockDim.x) {
+    // nondecreasing, so each piece's contributions collect in an NT-cell
+    // register window that slides one cell as the tap advances (the
+    // departing cell goes to the shared profile) and is flushed whole on a
+    // longer jump; dozens of outputs that share a cell at small intercept
+    // times cost one add
+    for (int i0 = lo & ~7; i0 <= hi; i0 += chunk) {
         const int ib = i0 + Q * (int)threadIdx.x;
-        int2 e[Q];
         float v[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int i = ib + q;
-            e[q] = make_int2(-1, 0);
-            v[q] = 0.f;
-            if (i >= rg.x && i <= rg.y) {
-                e[q] = __ldg(rt + i);
-                v[q] = __ldg(gl + i);
+        for (int q = 0; q < Q; ++q) v[q] = (ib + q >= lo && ib + q <= hi) ? __ldg(gl + ib + q) : 0.f;
+        for (int p = 0; p < np; ++p) {
+            const int2 rg = s_rg[p];
+            const int2* rt = s_rt[p];
+            int2 e[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int i = ib + q;
+                e[q] = (i >= rg.x && i <= rg.y) ? __ldg(rt + i) : make_int2(-1, 0);
             }
-        }
-        float w[NT];
+            const Pow2Scale scl(s_sh[p] - ev);
+            const float sc = s_sc[p];
+            int* pr = prof + p * nrho_max;
+            float w[NT];
 #pragma unroll
-        for (int c = 0; c < NT; ++c) w[c] = 0.f;
-        int wn = -1;
+            for (int k = 0; k < NT; ++k) w[k] = 0.f;
+            int wn = -1;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int n0 = e[q].x;
-            if (n0 < 0) continue;
-            if (wn < 0) {
-                wn = n0;
-            } else if (n0 != wn) {
-                if (n0 == wn + 1) {
-                    red_fixed(prof + wn, w[0]);
+            for (int q = 0; q < Q; ++q) {
+                const int n0 = e[q].x;
+                if (n0 < 0) continue;
+                if (wn < 0) {
+                    wn = n0;
+                } else if (n0 != wn) {
+                    if (n0 == wn + 1) {
+                        red_fixed(pr + wn, w[0]);
 #pragma unroll
-                    for (int c = 0; c + 1 < NT; ++c) w[c] = w[c + 1];
-                    w[NT - 1] = 0.f;
-                } else {
+                        for (int k = 0; k + 1 < NT; ++k) w[k] = w[k + 1];
+                        w[NT - 1] = 0.f;
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < NT; ++c) {
-                        red_fixed(prof + wn + c, w[c]);
-                        w[c] = 0.f;
+                        for (int k = 0; k < NT; ++k) {
+                            red_fixed(pr + wn + k, w[k]);
+                            w[k] = 0.f;
+                        }
                     }
+                    wn = n0;
                 }
-                wn = n0;
+                float wr[NT];
+                bspline_weights<NT>(__int_as_float(e[q].y), wr);
+                const float x = scl.up(v[q] * sc);
+#pragma unroll
+                for (int k = 0; k < NT; ++k) w[k] = fmaf(x, wr[k], w[k]);
             }
-            float wr[NT];
-            bspline_weights<NT>(__int_as_float(e[q].y), wr);
-            const float x = scl.up(v[q] * sc);
+            if (wn >= 0) {
 #pragma unroll
-            for (int c = 0; c < NT; ++c) w[c] = fmaf(x, wr[c], w[c]);
-        }
-        if (wn >= 0) {
-#pragma unroll
-            for (int c = 0; c < NT; ++c) red_fixed(prof + wn + c, w[c]);
+                for (int k = 0; k < NT; ++k) red_fixed(pr + wn + k, w[k]);
+            }
         }
     }
     __syncthreads();
-    for (int n = threadIdx.x; n < hp; n += blockDim.x) hl[n] = n < P.Nrho ? scl.down(prof[n]) : 0.f;
+    for (int p = 0; p < np; ++p) {
+        const Pow2Scale scl(s_sh[p] - ev);
+        const int* pr = prof + p * nrho_max;
+        const int nr = s_nr[p];
+        float* hl = s_hl[p];
+        for (int n = threadIdx.x; n < s_hp[p]; n += blockDim.x) hl[n] = n < nr ? scl.down(pr[n]) : 0.f;
+    }
 }
 
 // One band of R <= kMaxBandRows lattice rows: G' rows from the profiles of
@@ -1564,7 +1603,6 @@ static size_t max_over(const PieceDev* P, int n, size_t (*fn)(const PieceDev&)) 
 }
 
 size_t rows_smem_bytes(const PieceDev& P) { return scatter_smem_bytes(P); }
-size_t profile_smem_bytes(const PieceDev& P) { return (size_t)P.Nrho * sizeof(int); }
 
 // One stage over n <= kMaxBatch pieces (descriptors as a parameter) or over
 // a device-resident batch (descriptors and block map in device memory).
@@ -1579,17 +1617,6 @@ int launch_rows_r2c(const PieceDev* P, int n, void* stream) {
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nbands; });
     return set_and_launch(k_rows_r2c<PieceBatch>, nb, max_over(P, n, rows_smem_bytes), B, stream);
-}
-
-int launch_col_profiles(const PieceDev* P, int n, const float* g, void* stream) {
-    const size_t sm = max_over(P, n, profile_smem_bytes);
-    PieceBatch B;
-    const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.l_hi - q.l_lo + 1; });
-    HR_TAPS(P[0].ntaps, {
-        if (int e = set_smem((const void*)k_col_profiles<PieceBatch, NT>, sm)) return e;
-        if (nb > 0) k_col_profiles<PieceBatch, NT><<<nb, 256, sm, (cudaStream_t)stream>>>(B, g);
-    });
-    return check_launch();
 }
 
 int launch_band_rows(const PieceDev* P, int n, void* stream) {
@@ -1632,14 +1659,6 @@ int launch_rows_r2c_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
     return set_and_launch(k_rows_r2c<DevBatch>, nblocks, smem, S, stream);
 }
 
-int launch_col_profiles_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, const float* g, void* stream) {
-    HR_TAPS(ntaps, {
-        if (int e = set_smem((const void*)k_col_profiles<DevBatch, NT>, smem)) return e;
-        if (nblocks > 0) k_col_profiles<DevBatch, NT><<<nblocks, 256, smem, (cudaStream_t)stream>>>(S, g);
-    });
-    return check_launch();
-}
-
 int launch_band_rows_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, void* stream) {
     if (ntaps == 6) return set_and_launch(k_band_rows<DevBatch, 6>, nblocks, smem, S, stream);
     if (ntaps == 4) return set_and_launch(k_band_rows<DevBatch, 4>, nblocks, smem, S, stream);
@@ -1656,17 +1675,36 @@ int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* strea
     return set_and_launch(k_rows_c2r<DevBatch>, nblocks, smem, S, stream);
 }
 
-// Dynamic shared memory the output interpolation may take on the current
-// device: the opt-in limit less the kernel's own static shared arrays.
+// Dynamic shared memory the per-column profile kernels (the output
+// interpolation and its adjoint's profiles) may take on the current device:
+// the opt-in limit less the larger of the two kernels' static shared arrays.
 size_t interp_smem_limit(int ntaps) {
-    cudaFuncAttributes fa{};
-    const void* fn = ntaps == 6 ? (const void*)k_interp_columns<6> : (const void*)k_interp_columns<4>;
-    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
+    size_t stat = 0;
+    const void* fns[2] = {ntaps == 6 ? (const void*)k_interp_columns<6> : (const void*)k_interp_columns<4>,
+                          ntaps == 6 ? (const void*)k_col_profiles_cols<6> : (const void*)k_col_profiles_cols<4>};
+    for (const void* fn : fns) {
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        stat = std::max(stat, (size_t)fa.sharedSizeBytes);
     }
     const size_t lim = (size_t)max_smem_optin();
-    return lim > fa.sharedSizeBytes ? lim - fa.sharedSizeBytes : 0;
+    return lim > stat ? lim - stat : 0;
+}
+
+int launch_col_profiles_cols(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,
+                             int ntau_all, int np_all, int ntaps, const float* g, void* stream) {
+    if (np_max > kMaxColPieces) return (int)cudaErrorInvalidValue;
+    const size_t sm = (size_t)np_max * nrho_max * sizeof(int);
+    HR_TAPS(ntaps, {
+        if (int e = set_smem((const void*)k_col_profiles_cols<NT>, sm)) return e;
+        if (ncols > 0)
+            k_col_profiles_cols<NT><<<ncols, 256, sm, (cudaStream_t)stream>>>(pieces, cmap, nrho_max, ntau_all, np_all,
+                                                                              g);
+    });
+    return check_launch();
 }
 
 int launch_interp_columns(const PieceDev* pieces, const int4* cmap, int ncols, int nrho_max, int np_max,

@@ -1374,7 +1374,11 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
     };
     if (radon_status s = cuda_status(
             timed(p, 9, b_g + b_h, stream,
-                  [&] { return groups([&](const PieceDev* q, int n) { return launch_col_profiles(q, n, g, stream); }); }),
+                  [&] {
+                      return launch_col_profiles_cols(p->dev_pieces, p->cmap, p->ncols, p->nrho_max, p->col_pieces,
+                                                      p->d.Ntau, p->qpieces.size() == 1 ? np : 0,
+                                                      spline_taps(p->d.spline_order), g, stream);
+                  }),
             "adjoint interpolation (profiles)"))
         return s;
     if (radon_status s = cuda_status(
@@ -1597,12 +1601,12 @@ struct radon_batch_s {
     radon_plan_s* store = nullptr;             // owns the batch's own device allocations
     std::vector<long long> f_off, g_off;       // n + 1 prefix offsets (elements)
     const PieceDev* pieces = nullptr;          // every piece of every gather
-    const int2 *map_units = nullptr, *map_bands = nullptr, *map_kb = nullptr, *map_cols = nullptr;
-    int n_units = 0, n_bands = 0, n_kb = 0, n_cols = 0;
+    const int2 *map_units = nullptr, *map_bands = nullptr, *map_kb = nullptr;
+    int n_units = 0, n_bands = 0, n_kb = 0;
     const int4* cmap = nullptr;
     const int4* smap = nullptr;
     int ncols = 0, nsblocks = 0, col_pieces = 0;
-    size_t smem_rows = 0, smem_cols = 0, smem_prof = 0;
+    size_t smem_rows = 0, smem_cols = 0;
     int nrho_max = 0;
     int ntaps = 4;                             // B-spline taps per axis of every gather
     float* lat_all = nullptr;
@@ -1721,17 +1725,15 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
         prof = (char*)prof + piece_profile_bytes(P);
         b->smem_rows = std::max(b->smem_rows, rows_smem_bytes(P));
         b->smem_cols = std::max(b->smem_cols, colconv_smem_bytes(P));
-        b->smem_prof = std::max(b->smem_prof, profile_smem_bytes(P));
         b->nrho_max = std::max(b->nrho_max, P.Nrho);
     }
     // block maps of the stage launches and the maps of the two gathers
-    std::vector<int2> mu, mb, mk, mc;
+    std::vector<int2> mu, mb, mk;
     for (int gi = 0; gi < (int)host.size(); ++gi) {
         const PieceDev& P = host[gi];
         for (int u = 0; u < P.nunits; ++u) mu.push_back(int2{gi, u});
         for (int u = 0; u < P.nbands; ++u) mb.push_back(int2{gi, u});
         for (int u = 0; u < P.nkb; ++u) mk.push_back(int2{gi, u});
-        for (int u = 0; u < P.l_hi - P.l_lo + 1; ++u) mc.push_back(int2{gi, u});
     }
     std::vector<int4> cmap, smap;
     int base = 0;
@@ -1742,7 +1744,7 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
     }
     if ((s = dev_upload(b->store, host, &b->pieces)) || (s = dev_upload(b->store, mu, &b->map_units)) ||
         (s = dev_upload(b->store, mb, &b->map_bands)) || (s = dev_upload(b->store, mk, &b->map_kb)) ||
-        (s = dev_upload(b->store, mc, &b->map_cols)) || (s = dev_upload(b->store, cmap, &b->cmap)) ||
+        (s = dev_upload(b->store, cmap, &b->cmap)) ||
         (s = dev_upload(b->store, smap, &b->smap))) {
         destroy_batch(b);
         return s;
@@ -1750,7 +1752,6 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
     b->n_units = (int)mu.size();
     b->n_bands = (int)mb.size();
     b->n_kb = (int)mk.size();
-    b->n_cols = (int)mc.size();
     b->ncols = (int)cmap.size();
     for (const int4& c : cmap) b->col_pieces = std::max(b->col_pieces, c.y);
     b->nsblocks = (int)smap.size();
@@ -1864,8 +1865,9 @@ extern "C" radon_status radon_batch_adj(radon_batch b, const float* g, float* f,
     if (!b) return fail(RADON_ERR_INVALID_ARG, "batch is NULL");
     if (!f || !g) return fail(RADON_ERR_INVALID_ARG, "NULL data pointer");
     DeviceGuard guard(b->device);
-    const DevBatch C{b->pieces, b->map_cols}, Bd{b->pieces, b->map_bands}, K{b->pieces, b->map_kb};
-    if (radon_status s = cuda_status(launch_col_profiles_dev(C, b->n_cols, b->ntaps, b->smem_prof, g, stream),
+    const DevBatch Bd{b->pieces, b->map_bands}, K{b->pieces, b->map_kb};
+    if (radon_status s = cuda_status(launch_col_profiles_cols(b->pieces, b->cmap, b->ncols, b->nrho_max, b->col_pieces,
+                                                              0, 0, b->ntaps, g, stream),
                                      "adjoint interpolation (profiles)"))
         return s;
     if (radon_status s = cuda_status(launch_band_rows_dev(Bd, b->n_bands, b->ntaps, b->smem_rows, stream),
