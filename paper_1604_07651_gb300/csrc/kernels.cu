@@ -267,7 +267,10 @@ __device__ __forceinline__ int plan_x256(const FftPlan& fp) {
     return (fp.nst == 3 && fp.st[0] == 256 && fp.rad[1] == 16 && fp.rad[2] == 16) ? fp.rad[0] : 0;
 }
 #define HR_X256_CASES(CALL) \
+    case 2: CALL(2); break;  \
+    case 3: CALL(3); break;  \
     case 4: CALL(4); break;  \
+    case 5: CALL(5); break;  \
     case 6: CALL(6); break;  \
     case 8: CALL(8); break;  \
     case 9: CALL(9); break;  \
@@ -1116,6 +1119,8 @@ __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src 
     }
     if (s == 3 && S0 == 256 && fp.rad[1] == 16 && fp.rad[2] == 16 && blockDim.x == 512) {
         switch (R0) {
+            case 5: c1_x256<5>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
+            case 6: c1_x256<6>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
             case 8: c1_x256<8>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
             case 9: c1_x256<9>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
             case 10: c1_x256<10>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
