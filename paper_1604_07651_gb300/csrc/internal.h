@@ -117,8 +117,8 @@ enum { kInF32 = 0, kInBF16 = 1 };
 
 // Lattice tile of the forward gridding (rows x columns of cells) and the
 // largest work unit (chunks of <= 8 samples; one thread per chunk).
-constexpr int kTileRows = 16;
-constexpr int kTileCols = 128;
+constexpr int kTileRows = 32;
+constexpr int kTileCols = 64;
 constexpr int kUnitChunks = 256;
 // Most lattice rows one band of the row kernels holds.
 constexpr int kMaxBandRows = 6;
