@@ -1049,19 +1049,28 @@ __device__ __forceinline__ void c1_x256(cf* A, cf* col, int Nth, const cf* Tg, c
         const int fb = q + R0 * m;
         cf x[16];
         c1_ld<16>(A, t * 16, 1, c, x);
-        dft_small<16>(x, -1);
+        // forward DFT, product with K, inverse DFT as conj(DFT(conj(.))):
+        // one DFT body run twice (half the code of the pass)
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            dft_small<16>(x, -1);
+            if (h == 0) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int f = fb + nb * k;
-            const int kk = f <= n - f ? f : n - f;
-            if (kk < k1n) {
-                const cf kv = K[2 * kk + c];
-                x[k] = adjoint ? cmulc(x[k], kv) : cmul(x[k], kv);
+                for (int k = 0; k < 16; ++k) {
+                    const int f = fb + nb * k;
+                    const int kk = f <= n - f ? f : n - f;
+                    if (kk < k1n) {
+                        const cf kv = K[2 * kk + c];
+                        x[k] = cconj(adjoint ? cmulc(x[k], kv) : cmul(x[k], kv));
+                    } else {
+                        x[k] = cf{0.f, 0.f};
+                    }
+                }
             } else {
-                x[k] = cf{0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < 16; ++k) x[k] = cconj(x[k]);
             }
         }
-        dft_small<16>(x, +1);
         c1_st<16>(A, t * 16, 1, c, x);
     }
     __syncthreads();
