@@ -143,14 +143,14 @@ PROFILE_EVERY = 4   # eager steps with per-stage kernel events: one per PROFILE_
 
 MEASURED_TRAFFIC = {
     # kernel: (kernel_source_digest() when measured, bytes per launch averaged over a step's launches)
-    "k_grid_tiles": ("3386401af41f00ec", 127.48e6),
-    "k_rows_r2c": ("3386401af41f00ec", 28.50e6),
-    "k_colconv": ("3386401af41f00ec", 48.37e6),
-    "k_rows_c2r": ("3386401af41f00ec", 28.91e6),
-    "k_interp_columns": ("3386401af41f00ec", 102.15e6),
-    "k_col_profiles_cols": ("3386401af41f00ec", 108.89e6),
-    "k_band_rows": ("3386401af41f00ec", 46.22e6),
-    "k_gather_samples": ("3386401af41f00ec", 106.87e6),
+    "k_grid_tiles": ("fd793458bd5951f7", 123.85e6),
+    "k_rows_r2c": ("fd793458bd5951f7", 22.00e6),
+    "k_colconv": ("fd793458bd5951f7", 47.70e6),
+    "k_rows_c2r": ("fd793458bd5951f7", 25.81e6),
+    "k_interp_columns": ("fd793458bd5951f7", 94.80e6),
+    "k_col_profiles_cols": ("fd793458bd5951f7", 93.69e6),
+    "k_band_rows": ("fd793458bd5951f7", 40.33e6),
+    "k_gather_samples": ("fd793458bd5951f7", 104.29e6),
 }
 
 # FFT kernels run out of shared memory and are limited by instruction issue,
