@@ -1359,12 +1359,13 @@ extern "C" radon_status radon_adj(radon_plan p, const float* g, float* f, void* 
     DeviceGuard guard(p->device);
     const std::vector<PieceDev>& P = host_pieces(p);
     const int np = (int)P.size();
-    double b_lat = 0, b_spec = 0, b_ker = 0, b_g = 0, b_h = 0;
+    // the image is read once: every output column's CTA serves all its pieces
+    const double b_g = 4.0 * p->d.Ntau * p->d.Nq;
+    double b_lat = 0, b_spec = 0, b_ker = 0, b_h = 0;
     for (const PieceDev& q : P) {
         b_lat += bytes_lattice(q);
         b_spec += bytes_spectrum(q);
         b_ker += bytes_kernel(q);
-        b_g += 4.0 * q.Ntau * (q.l_hi - q.l_lo + 1);
         b_h += 4.0 * (q.l_hi - q.l_lo + 1) * q.Nrho;
     }
     auto groups = [&](auto&& launch) {
