@@ -386,7 +386,7 @@ radon_status radon_demultiple(radon_plan p, const float* f, double q0, double sl
  * array of RADON_NOALLOC_MAX_BYTES that every GPU loading this library holds
  * until the process exits; the plan's own work buffers are not used. Plans
  * whose work memory exceeds it (2048^2 gathers with default parameters need
- * about 56 MB) or that have more than 32 pieces are rejected with
+ * about 76 MB) or that have more than 32 pieces are rejected with
  * RADON_ERR_UNSUPPORTED and a message giving the bytes needed. The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.

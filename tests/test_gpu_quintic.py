@@ -2,9 +2,10 @@
 axis, three guard cells) on the GPU, through the C ABI, against the FP64
 log-polar oracle with order=5 on the same lattices: forward and adjoint
 element by element (tests/parity.py bounds) on small, ragged, multi-piece and
-full 2048^2 workloads, the closed-form line integral of a Gaussian blob more
-accurately than the cubic path, the FP32 inner-product test, batches of
-quintic gathers, and the refusal of a batch that mixes orders."""
+full 2048^2 workloads and on given offsets and slownesses, the closed-form
+line integral of a Gaussian blob more accurately than the cubic path, the
+FP32 inner-product test, batches of quintic gathers (FP32 and BF16 input),
+and the refusal of a batch that mixes orders."""
 import numpy as np
 import pytest
 import torch
@@ -145,6 +146,40 @@ def test_quintic_batch_against_oracle_and_mixed_orders_refused(hr):
     with pytest.raises(hr.RadonError) as ei:
         hr.Batch([_geo_dict(geos[0], spline_order=5), _geo_dict(geos[1])])
     assert ei.value.status == UNSUPPORTED and "order" in str(ei.value)
+
+
+def test_quintic_on_given_grids_matches_oracle(hr):
+    """Jittered offsets with a near-offset gap and slownesses denser towards
+    qmin (radon_plan_create_grid), two slowness pieces, quintic B-splines."""
+    geo = synth.irregular_geometry(256, 96, 256, 64, 0.004, 1.6, 0.2, 0.7, 11, jitter=0.4, near=0.1, q_power=1.5)
+    plan = hr.Plan(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, n_qsplit=2,
+                   x=geo.offsets, q=geo.slownesses, spline_order=5)
+    d = plan.desc
+    lp = LogPolar(Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax, sigma=d.sigma,
+                       omega_c=d.omega_c, tsplits=tuple(d.tsplit[i] for i in range(d.n_tsplit)), n_qsplit=2,
+                       x=geo.offsets, q_values=geo.slownesses, order=5))
+    f = synth.band_limited_gather(geo, 61, n_events=6, nu=10.0)
+    assert_parity(plan.forward(_cuda(f)).cpu().numpy(), lp.forward(f), what="quintic given grids forward")
+    gg = synth.random_radon_image(geo, 62)
+    assert_parity(plan.adjoint(_cuda(gg)).cpu().numpy(), lp.adjoint(gg), what="quintic given grids adjoint")
+    plan.close()
+
+
+def test_quintic_bf16_batch_against_oracle_on_rounded_input(hr):
+    geos = [synth.Geometry(300, 64, 280, 48, 0.004, 0.025, 0.2, 0.7),
+            synth.Geometry(180, 120, 200, 60, 0.004, 0.025, 0.15, 0.65)]
+    gathers = [synth.batch_gather(g, 500 + i) for i, g in enumerate(geos)]
+    batch = hr.Batch([_geo_dict(g, spline_order=5) for g in geos])
+    fb = batch.pack([torch.tensor(x, dtype=torch.float32) for x in gathers], dtype=torch.bfloat16)
+    imgs = batch.unpack_images(batch.forward(fb))
+    for i, (geo, x, a) in enumerate(zip(geos, gathers, imgs)):
+        d = batch.plan_desc(i)
+        lp = LogPolar(Desc(geo.Nt, geo.Nx, geo.Ntau, geo.Nq, geo.dt, geo.dx, geo.qmin, geo.qmax,
+                           sigma=d.sigma, omega_c=d.omega_c, tsplits=tuple(d.tsplit[k] for k in range(d.n_tsplit)),
+                           n_qsplit=d.n_qsplit, order=5))
+        xb = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+        assert_parity(a.cpu().numpy(), lp.forward(xb), what="quintic BF16 batch forward")
+    batch.close()
 
 
 def test_quintic_bitwise_reproducible(hr):

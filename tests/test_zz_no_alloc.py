@@ -64,6 +64,24 @@ def test_noalloc_forward_matches_regular_forward_twice(lib):
         L.radon_plan_destroy(plan)
 
 
+def test_noalloc_forward_with_quintic_splines(lib):
+    """The six-tap kernels through the static work area as well."""
+    L = lib.load()
+    geo = synth.Geometry(256, 96, 200, 64, 0.004, 0.02, 0.2, 0.7)
+    plan = _plan(lib, geo, spline_order=5)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    try:
+        f = torch.tensor(synth.band_limited_gather(geo, 53, n_events=6, nu=10.0), dtype=torch.float32, device="cuda")
+        g_ref = torch.empty((geo.Nq, geo.Ntau), dtype=torch.float32, device="cuda")
+        g = torch.full((geo.Nq, geo.Ntau), float("nan"), dtype=torch.float32, device="cuda")
+        lib.check(L.radon_fwd(plan, _ptr(f), _ptr(g_ref), stream))
+        lib.check(L.radon_fwd_noalloc(plan, _ptr(f), _ptr(g), stream))
+        torch.cuda.synchronize()
+        assert_parity(g.double().cpu().numpy(), g_ref.double().cpu().numpy(), what="quintic no-alloc")
+    finally:
+        L.radon_plan_destroy(plan)
+
+
 def test_noalloc_rejects_plans_beyond_the_static_area(lib):
     L = lib.load()
     geo = synth.Geometry(2048, 2048, 2048, 2048, 2.0 / 2047, 2.0 / 2047, 0.2, 0.7)
