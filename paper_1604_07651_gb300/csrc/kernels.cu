@@ -690,9 +690,10 @@ __global__ void __launch_bounds__(512, 2) k_rows_r2c(const __grid_constant__ Src
 // Adjoint of the output interpolation (transpose of Eq. (17)), separated
 // along the two axes. Every output of a slowness column has the same theta
 // taps (the column's angle), so the transpose is a 1-D scatter along rho per
-// column followed by a 4-tap spread of the column profiles over theta:
-//   h_l[n]   = s_l sum_i g[l][i] B3(rho_il - rho_n)          (k_col_profiles_cols)
-//   G'[m][n] = sum_l B3(theta_l - theta_m) h_l[n]            (k_band_rows)
+// column followed by an NT-tap spread of the column profiles over theta
+// (B the cubic or quintic B-spline, NT = 4 or 6 taps):
+//   h_l[n]   = s_l sum_i g[l][i] B(rho_il - rho_n)           (k_col_profiles_cols)
+//   G'[m][n] = sum_l B(theta_l - theta_m) h_l[n]             (k_band_rows)
 // The profiles are summed in fixed point (order-independent), the spread is a
 // plain per-thread sum over the band's columns in a fixed order: the adjoint
 // interpolation has no floating-point atomics and is deterministic.
@@ -893,14 +894,15 @@ __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Sr
 
 // --------------------------------------------------------------------------
 // Column pass: FFT along theta, product with K (or conj K), inverse FFT
-// (Eq. (16)-(17)). One CTA of 512 threads per block of two spectrum
+// (Eq. (16)-(17)). One CTA of kColThreads threads per block of two spectrum
 // columns, which the blocked layout [kb][m][2] stores as one 16-byte row per
 // lattice row; thread pairs (2 t, 2 t + 1) take the same butterfly of the two
 // columns, so every shared and global access of a pair is one 16-byte word
 // (shared buffer [Ptheta] of 16-byte elements, swizzled by swc). One column
-// per thread keeps a radix-16 butterfly in 64 registers: two CTAs (32 warps)
-// per SM hide the pass latencies (measured: 78 us against 90 us for both
-// columns per thread at 256 threads, 112 us for that at one CTA per SM).
+// per thread keeps a radix-16 butterfly in 64 registers; three CTAs (30
+// warps) per SM hide the pass latencies (measured at 2048^2: 49.5 us against
+// 54.7 us at 512 threads and two CTAs per SM, 59 us at 384 threads; earlier,
+// both columns per thread at 256 threads 90 us, that at one CTA per SM 112).
 // The column block's slice of K and the pass twiddle tables are copied into
 // shared memory (cp.async) while pass 0 runs.
 //
@@ -915,6 +917,10 @@ __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Sr
 //   back down     inverse passes, the last one writing only the Ntheta rows
 //                 back to global memory.
 // --------------------------------------------------------------------------
+// Threads of a column-pass CTA: two per butterfly of the two columns; 320 keeps
+// the radix-16 passes of the R0 * 256 lengths (144 or 160 butterflies per
+// column) 90-100 % busy, with three CTAs per SM.
+constexpr int kColThreads = 320;
 // 16-byte asynchronous copies global -> shared (cp.async; the completion
 // wait is the hardware's, no spin loop).
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -1030,25 +1036,25 @@ __device__ __forceinline__ void c1_kernel(cf* A, const FftPlan& fp, const cf* K,
 // pass's first frequency b / 16 + R0 (b mod 16) without the general digit
 // loop. Same arithmetic as the general passes.
 template <int R0>
-__device__ __forceinline__ void c1_x256(cf* A, cf* col, int Nth, const cf* Tg, const cf* Ts, const cf* K, int k1n,
-                                        int adjoint, int t, int c) {
+__device__ __forceinline__ void c1_x256(cf* A, cf* col, int Nth, const cf* Tg, const cf* T1, const cf* K, int k1n,
+                                        int adjoint, int t, int nt, int c) {
     constexpr int n = R0 * 256, nb = R0 * 16;
-    c1_first<R0>(A, col, Nth, 256, Tg, t, 256, c);
+    c1_first<R0>(A, col, Nth, 256, Tg, t, nt, c);
     cp_async_wait_all();
     __syncthreads();
-    const cf* T1 = Ts + 256 * (R0 - 1);
-    const int q = t >> 4, m = t & 15;
-    if (t < nb) {
+    for (int b = t; b < nb; b += nt) {
+        const int q = b >> 4, m = b & 15;
         cf x[16];
         c1_ld<16>(A, q * 256 + m, 16, c, x);
         c1_fwd<16>(x, T1, 16, m);
         c1_st<16>(A, q * 256 + m, 16, c, x);
     }
     __syncthreads();
-    if (t < nb) {
+    for (int b = t; b < nb; b += nt) {
+        const int q = b >> 4, m = b & 15;
         const int fb = q + R0 * m;
         cf x[16];
-        c1_ld<16>(A, t * 16, 1, c, x);
+        c1_ld<16>(A, b * 16, 1, c, x);
         // forward DFT, product with K, inverse DFT as conj(DFT(conj(.))):
         // one DFT body run twice (half the code of the pass)
 #pragma unroll 1
@@ -1071,32 +1077,47 @@ __device__ __forceinline__ void c1_x256(cf* A, cf* col, int Nth, const cf* Tg, c
                 for (int k = 0; k < 16; ++k) x[k] = cconj(x[k]);
             }
         }
-        c1_st<16>(A, t * 16, 1, c, x);
+        c1_st<16>(A, b * 16, 1, c, x);
     }
     __syncthreads();
-    if (t < nb) {
+    for (int b = t; b < nb; b += nt) {
+        const int q = b >> 4, m = b & 15;
         cf x[16];
         c1_ld<16>(A, q * 256 + m, 16, c, x);
         c1_inv<16>(x, T1, 16, m);
         c1_st<16>(A, q * 256 + m, 16, c, x);
     }
     __syncthreads();
-    c1_last<R0>(A, col, Nth, 256, Ts, t, 256, c);
+    c1_last<R0>(A, col, Nth, 256, Tg, t, nt, c);
+}
+
+// R0 of a column plan that the compile-time pair c1_x256 serves, else 0.
+__host__ __device__ __forceinline__ int colconv_x256(const FftPlan& fp) {
+    if (fp.nst != 3 || fp.st[0] != 256 || fp.rad[1] != 16 || fp.rad[2] != 16) return 0;
+    const int r = fp.rad[0];
+    return (r == 5 || r == 6 || r == 8 || r == 9 || r == 10 || r == 12) ? r : 0;
 }
 
 // Shared memory of the column kernel: the column block [Ptheta] (16-byte
 // elements), its slice of K [k1max + 1] (16 bytes each), the twiddle tables
-// (twlen complex, a multiple of 2).
+// (twlen complex, a multiple of 2): all passes' tables, or for the
+// compile-time pair only the stride-16 pass's 240 (the first pass reads its
+// own from global memory), which lets three CTAs share an SM.
+constexpr int kX256Twiddles = 16 * 15;
 __host__ __device__ __forceinline__ size_t colconv_smem(int Pt, int k1n, int twlen) {
     return ((size_t)Pt + k1n) * 16 + (size_t)twlen * 8;
 }
+__host__ __device__ __forceinline__ size_t colconv_smem(const PieceDev& P) {
+    return colconv_smem(P.Ptheta, P.k1max + 1, colconv_x256(P.fftT) ? kX256Twiddles : P.twT_len);
+}
 
 template <class Src>
-__global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src B, int adjoint) {
+__global__ void __launch_bounds__(kColThreads, 3) k_colconv(const __grid_constant__ Src B, int adjoint) {
     int kb;
     const PieceDev& P = piece_of(B, kb);
     const int Pt = P.Ptheta, Nth = P.Ntheta, k1n = P.k1max + 1;
-    if (P.CB != 2 || (P.twT_len & 1) || colconv_smem(Pt, k1n, P.twT_len) > dyn_smem_bytes()) return;
+    if (P.CB != 2 || (P.twT_len & 1) || colconv_smem(P) > dyn_smem_bytes()) return;
+    const int x256 = colconv_x256(P.fftT);
     float4* A4 = reinterpret_cast<float4*>(smem_f);
     float4* Ks4 = A4 + Pt;
     cf* Ts = reinterpret_cast<cf*>(Ks4 + k1n);
@@ -1106,9 +1127,10 @@ __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src 
     {
         const float4* Kg = reinterpret_cast<const float4*>(P.K) + (size_t)kb * k1n;
         for (int i = threadIdx.x; i < k1n; i += blockDim.x) cp_async16(Ks4 + i, Kg + i);
-        const float4* Tg = reinterpret_cast<const float4*>(P.twT);
+        const float4* Tg = reinterpret_cast<const float4*>(P.twT + (x256 ? P.fftT.tw[1] : 0));
         float4* T4 = reinterpret_cast<float4*>(Ts);
-        for (int i = threadIdx.x; i < P.twT_len / 2; i += blockDim.x) cp_async16(T4 + i, Tg + i);
+        const int n4 = (x256 ? kX256Twiddles : P.twT_len) / 2;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) cp_async16(T4 + i, Tg + i);
     }
     const int c = threadIdx.x & 1, t = threadIdx.x >> 1, nt = blockDim.x >> 1;
     const FftPlan& fp = P.fftT;
@@ -1126,16 +1148,14 @@ __global__ void __launch_bounds__(512, 2) k_colconv(const __grid_constant__ Src 
         for (int m = threadIdx.x; m < Nth; m += blockDim.x) reinterpret_cast<float4*>(col)[m] = A4[swc(m)];
         return;
     }
-    if (s == 3 && S0 == 256 && fp.rad[1] == 16 && fp.rad[2] == 16 && blockDim.x == 512) {
-        switch (R0) {
-            case 5: c1_x256<5>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
-            case 6: c1_x256<6>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
-            case 8: c1_x256<8>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
-            case 9: c1_x256<9>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
-            case 10: c1_x256<10>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
-            case 12: c1_x256<12>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, c); return;
-            default: break;
-        }
+    switch (x256) {
+        case 5: c1_x256<5>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, nt, c); return;
+        case 6: c1_x256<6>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, nt, c); return;
+        case 8: c1_x256<8>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, nt, c); return;
+        case 9: c1_x256<9>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, nt, c); return;
+        case 10: c1_x256<10>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, nt, c); return;
+        case 12: c1_x256<12>(A, col, Nth, P.twT, T, K, k1n, adjoint, t, nt, c); return;
+        default: break;
     }
 #define HR_FIRST(RR) c1_first<RR>(A, col, Nth, S0, P.twT, t, nt, c)
     switch (R0) { HR_RADIX_CASES(HR_FIRST) }
@@ -1538,7 +1558,7 @@ static int check_launch() {
 
 size_t scatter_smem_bytes(const PieceDev& P) { return rows_smem(P); }
 
-size_t colconv_smem_bytes(const PieceDev& P) { return colconv_smem(P.Ptheta, P.k1max + 1, P.twT_len); }
+size_t colconv_smem_bytes(const PieceDev& P) { return colconv_smem(P); }
 
 int max_smem_optin() {
     int dev = 0, v = 0;
@@ -1647,7 +1667,7 @@ int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream) {
     if (int e = set_smem((const void*)k_colconv<PieceBatch>, sm)) return e;
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nkb; });
-    if (nb > 0) k_colconv<PieceBatch><<<nb, 512, sm, (cudaStream_t)stream>>>(B, adjoint);
+    if (nb > 0) k_colconv<PieceBatch><<<nb, kColThreads, sm, (cudaStream_t)stream>>>(B, adjoint);
     return check_launch();
 }
 
@@ -1681,7 +1701,7 @@ int launch_band_rows_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem,
 
 int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream) {
     if (int e = set_smem((const void*)k_colconv<DevBatch>, smem)) return e;
-    if (nblocks > 0) k_colconv<DevBatch><<<nblocks, 512, smem, (cudaStream_t)stream>>>(S, adjoint);
+    if (nblocks > 0) k_colconv<DevBatch><<<nblocks, kColThreads, smem, (cudaStream_t)stream>>>(S, adjoint);
     return check_launch();
 }
 
