@@ -143,14 +143,14 @@ PROFILE_EVERY = 4   # eager steps with per-stage kernel events: one per PROFILE_
 
 MEASURED_TRAFFIC = {
     # kernel: (kernel_source_digest() when measured, bytes per launch averaged over a step's launches)
-    "k_grid_tiles": ("5c19689cba1cd2d2", 123.59e6),
-    "k_rows_r2c": ("5c19689cba1cd2d2", 22.00e6),
-    "k_colconv": ("5c19689cba1cd2d2", 47.70e6),
-    "k_rows_c2r": ("5c19689cba1cd2d2", 25.81e6),
-    "k_interp_columns": ("5c19689cba1cd2d2", 94.85e6),
-    "k_col_profiles_cols": ("5c19689cba1cd2d2", 93.90e6),
-    "k_band_rows": ("5c19689cba1cd2d2", 40.38e6),
-    "k_gather_samples": ("5c19689cba1cd2d2", 104.43e6),
+    "k_grid_tiles": ("0c07c8cc1993e35e", 123.61e6),
+    "k_rows_r2c": ("0c07c8cc1993e35e", 22.00e6),
+    "k_colconv": ("0c07c8cc1993e35e", 47.70e6),
+    "k_rows_c2r": ("0c07c8cc1993e35e", 25.81e6),
+    "k_interp_columns": ("0c07c8cc1993e35e", 94.79e6),
+    "k_col_profiles_cols": ("0c07c8cc1993e35e", 93.55e6),
+    "k_band_rows": ("0c07c8cc1993e35e", 40.35e6),
+    "k_gather_samples": ("0c07c8cc1993e35e", 104.29e6),
 }
 
 # FFT kernels run out of shared memory and are limited by instruction issue,

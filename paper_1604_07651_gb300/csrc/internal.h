@@ -138,7 +138,10 @@ int launch_rows_c2r(const PieceDev* P, int n, void* stream);
 int launch_grid_tiles_dev(const DevBatch& S, int nblocks, int ntaps, const void* f, int in_type, void* stream);
 int launch_rows_r2c_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
 int launch_band_rows_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem, void* stream);
-int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream);
+// x256: every piece of the launch takes the compile-time column pass
+// (colconv_all_x256), which runs at fewer threads per CTA.
+int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, bool x256, int adjoint, void* stream);
+bool colconv_all_x256(const PieceDev* P, int n);
 int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* stream);
 // Output interpolation: one CTA per output column; cmap[b] = (first piece,
 // number of time pieces, column l, 0) in `pieces` (device), or, when

@@ -917,10 +917,13 @@ __global__ void __launch_bounds__(512, 2) k_band_rows(const __grid_constant__ Sr
 //   back down     inverse passes, the last one writing only the Ntheta rows
 //                 back to global memory.
 // --------------------------------------------------------------------------
-// Threads of a column-pass CTA: two per butterfly of the two columns; 320 keeps
-// the radix-16 passes of the R0 * 256 lengths (144 or 160 butterflies per
-// column) 90-100 % busy, with three CTAs per SM.
+// Threads of a column-pass CTA: two per butterfly of the two columns. 320
+// keeps the radix-16 passes of the R0 * 256 lengths (144 or 160 butterflies
+// per column) 90-100 % busy, with three CTAs per SM; launches with a piece of
+// another length (the general passes, all twiddle tables in shared memory)
+// take 512 threads and two CTAs per SM.
 constexpr int kColThreads = 320;
+constexpr int kColThreadsGeneral = 512;
 // 16-byte asynchronous copies global -> shared (cp.async; the completion
 // wait is the hardware's, no spin loop).
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -1111,8 +1114,8 @@ __host__ __device__ __forceinline__ size_t colconv_smem(const PieceDev& P) {
     return colconv_smem(P.Ptheta, P.k1max + 1, colconv_x256(P.fftT) ? kX256Twiddles : P.twT_len);
 }
 
-template <class Src>
-__global__ void __launch_bounds__(kColThreads, 3) k_colconv(const __grid_constant__ Src B, int adjoint) {
+template <class Src, int TPB>
+__global__ void __launch_bounds__(TPB, TPB == kColThreads ? 3 : 2) k_colconv(const __grid_constant__ Src B, int adjoint) {
     int kb;
     const PieceDev& P = piece_of(B, kb);
     const int Pt = P.Ptheta, Nth = P.Ntheta, k1n = P.k1max + 1;
@@ -1662,13 +1665,30 @@ int launch_band_rows(const PieceDev* P, int n, void* stream) {
     return (int)cudaErrorInvalidValue;
 }
 
+bool colconv_all_x256(const PieceDev* P, int n) {
+    for (int k = 0; k < n; ++k)
+        if (!colconv_x256(P[k].fftT)) return false;
+    return true;
+}
+
+template <class Src>
+static int launch_colconv_as(const Src& B, int nb, size_t sm, bool x256, int adjoint, void* stream) {
+    if (x256) {
+        if (int e = set_smem((const void*)k_colconv<Src, kColThreads>, sm)) return e;
+        if (nb > 0) k_colconv<Src, kColThreads><<<nb, kColThreads, sm, (cudaStream_t)stream>>>(B, adjoint);
+    } else {
+        if (int e = set_smem((const void*)k_colconv<Src, kColThreadsGeneral>, sm)) return e;
+        if (nb > 0)
+            k_colconv<Src, kColThreadsGeneral><<<nb, kColThreadsGeneral, sm, (cudaStream_t)stream>>>(B, adjoint);
+    }
+    return check_launch();
+}
+
 int launch_colconv(const PieceDev* P, int n, int adjoint, void* stream) {
     const size_t sm = max_over(P, n, colconv_smem_bytes);
-    if (int e = set_smem((const void*)k_colconv<PieceBatch>, sm)) return e;
     PieceBatch B;
     const int nb = make_batch(P, n, B, [](const PieceDev& q) { return q.nkb; });
-    if (nb > 0) k_colconv<PieceBatch><<<nb, kColThreads, sm, (cudaStream_t)stream>>>(B, adjoint);
-    return check_launch();
+    return launch_colconv_as(B, nb, sm, colconv_all_x256(P, n), adjoint, stream);
 }
 
 int launch_rows_c2r(const PieceDev* P, int n, void* stream) {
@@ -1699,10 +1719,8 @@ int launch_band_rows_dev(const DevBatch& S, int nblocks, int ntaps, size_t smem,
     return (int)cudaErrorInvalidValue;
 }
 
-int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, int adjoint, void* stream) {
-    if (int e = set_smem((const void*)k_colconv<DevBatch>, smem)) return e;
-    if (nblocks > 0) k_colconv<DevBatch><<<nblocks, kColThreads, smem, (cudaStream_t)stream>>>(S, adjoint);
-    return check_launch();
+int launch_colconv_dev(const DevBatch& S, int nblocks, size_t smem, bool x256, int adjoint, void* stream) {
+    return launch_colconv_as(S, nblocks, smem, x256, adjoint, stream);
 }
 
 int launch_rows_c2r_dev(const DevBatch& S, int nblocks, size_t smem, void* stream) {

@@ -1610,6 +1610,7 @@ struct radon_batch_s {
     size_t smem_rows = 0, smem_cols = 0;
     int nrho_max = 0;
     int ntaps = 4;                             // B-spline taps per axis of every gather
+    bool col_x256 = false;                     // every piece takes the compile-time column pass
     float* lat_all = nullptr;
     size_t lat_bytes = 0;
 };
@@ -1728,6 +1729,7 @@ extern "C" radon_status radon_batch_create_grid(radon_batch* out, int n, const r
         b->smem_cols = std::max(b->smem_cols, colconv_smem_bytes(P));
         b->nrho_max = std::max(b->nrho_max, P.Nrho);
     }
+    b->col_x256 = colconv_all_x256(host.data(), (int)host.size());
     // block maps of the stage launches and the maps of the two gathers
     std::vector<int2> mu, mb, mk;
     for (int gi = 0; gi < (int)host.size(); ++gi) {
@@ -1854,7 +1856,7 @@ extern "C" radon_status radon_batch_fwd(radon_batch b, const void* f, int in_typ
         return cuda_status((int)e, "clearing the lattices");
     if (radon_status s = cuda_status(launch_grid_tiles_dev(U, b->n_units, b->ntaps, f, in_type, stream), "gridding")) return s;
     if (radon_status s = cuda_status(launch_rows_r2c_dev(Bd, b->n_bands, b->smem_rows, stream), "row FFT")) return s;
-    if (radon_status s = cuda_status(launch_colconv_dev(K, b->n_kb, b->smem_cols, 0, stream), "convolution"))
+    if (radon_status s = cuda_status(launch_colconv_dev(K, b->n_kb, b->smem_cols, b->col_x256, 0, stream), "convolution"))
         return s;
     if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
         return s;
@@ -1874,7 +1876,7 @@ extern "C" radon_status radon_batch_adj(radon_batch b, const float* g, float* f,
     if (radon_status s = cuda_status(launch_band_rows_dev(Bd, b->n_bands, b->ntaps, b->smem_rows, stream),
                                      "adjoint interpolation (bands)"))
         return s;
-    if (radon_status s = cuda_status(launch_colconv_dev(K, b->n_kb, b->smem_cols, 1, stream), "adjoint convolution"))
+    if (radon_status s = cuda_status(launch_colconv_dev(K, b->n_kb, b->smem_cols, b->col_x256, 1, stream), "adjoint convolution"))
         return s;
     if (radon_status s = cuda_status(launch_rows_c2r_dev(Bd, b->n_bands, b->smem_rows, stream), "inverse row FFT"))
         return s;
