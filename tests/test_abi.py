@@ -74,3 +74,9 @@ def test_host_side_argument_checks(lib):
     assert L.radon_fwd(None, None, None, None) == 1
     assert L.radon_adj(None, None, None, None) == 1
     assert L.radon_direct_fwd(None, None, 4, 4, 4, 4, 1.0, 1.0, 0.0, 1.0, 0.0, 0.1, None) == 1
+    # a batch must share one B-spline order: refused before any device work
+    pair = (_lib.RadonDesc * 2)(_lib.RadonDesc.from_buffer_copy(d), _lib.RadonDesc.from_buffer_copy(d))
+    pair[1].spline_order = 5
+    b = ctypes.c_void_p()
+    assert L.radon_batch_create(ctypes.byref(b), 2, pair) == 4 and not b.value
+    assert "order" in L.radon_last_error().decode()
