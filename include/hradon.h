@@ -29,7 +29,8 @@
  * stream (a cudaStream_t passed as void*, NULL = the legacy default
  * stream). The transform calls (radon_fwd, radon_adj, the batch, solver and
  * no-alloc calls) never make the host wait; plan and batch creation and
- * destruction, and radon_plan_profile_read, synchronise. A plan may be used
+ * destruction, radon_plan_profile_read and the two inspection calls
+ * (radon_plan_piece_lattice, radon_plan_piece_samples) synchronise. A plan may be used
  * by one stream at a time.
  *
  * Errors: every function returns a radon_status and never aborts;
