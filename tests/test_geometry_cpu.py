@@ -107,3 +107,10 @@ def test_host_geometry_on_given_grids_equals_oracle(i):
     same range."""
     c, x, q = _given_grid_cases()[i]
     _check(c, x, q)
+
+
+def test_host_geometry_quintic_on_given_grids_equals_oracle():
+    """Quintic B-splines (three guard cells) on unequal offsets and
+    slownesses, two slowness pieces."""
+    c, x, q = _given_grid_cases()[1]
+    _check(dict(c, order=5), x, q)
